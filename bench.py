@@ -1,0 +1,383 @@
+"""Benchmark of the compressed-table PFAC matcher on GB300.
+
+Default workload: the DNA-shaped configuration (alphabet 4, 10,000 patterns
+of length U[8,64], 256 MiB input as one segment, 0.1% of positions planted).
+A step is one pfac_match_async over the whole input with the table resident
+and the input already in HBM: the scan kernel, the key-count scan, the
+overflow re-scan and the key expansion (all kernels of the path).  The input
+(256 MiB) is larger than L2 (129 MB), so no flush is needed between steps.
+
+Printed (rank 0, one JSON line): scan throughput in Gbps (8 * input bytes /
+device time, whole job over all ranks), the same metric end to end through
+the C ABI with host buffers (pinned H2D of the input, D2H of count and keys),
+the uncompressed-table kernel's Gbps and both tables' bytes, p50/p99 step
+latency, the scan kernel's roofline against the measured HBM peak, the CPU
+oracle timed on a bounded sample, clocks sampled during the timed region, and
+the number of kernels launched.
+
+``--impl reference`` times the CPU oracle (Aho-Corasick with failure links,
+all host cores) on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+SCAN_KERNELS_PER_STEP = 5  # k_scan, k_reduce, k_offsets, k_scan (overflow re-scan), k_expand
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_workload(name, rank):
+    seed_shift = 1000 * rank
+    if name == "dna":
+        return workloads.config2(seed=workloads.seed_for(2) + seed_shift)
+    if name == "plain":
+        return workloads.config1(seed=workloads.seed_for(1) + seed_shift)
+    if name == "ids":
+        return workloads.config3(seed=workloads.seed_for(3) + seed_shift)
+    if name.startswith("sweep-"):
+        _, s, n = name.split("-")
+        return workloads.config4(int(s), int(n), seed=workloads.seed_for(4, int(s), int(n)) + seed_shift)
+    raise SystemExit(f"unknown workload {name}")
+
+
+WORKLOAD_DESC = {
+    "dna": "DNA-shaped: alphabet 4, 10,000 patterns U[8,64], 256 MiB one segment, 0.1% planted",
+    "plain": "alphabet 256, 1,000 patterns U[4,32], 1 MiB, 2,000 planted",
+    "ids": "IDS-shaped: alphabet 256, 20,000 log-normal patterns, 1 GiB of 64-1500 B packets",
+}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s=12.0, sample_mib=32, threads=None):
+    """The oracle (AC with failure links, all host cores) on the first
+    sample_mib MiB of the workload; scaled down until it fits the budget."""
+    import oracle
+    threads = threads or oracle.default_threads()
+    ac = oracle.ACOracle(w.patterns)
+    nb = min(w.n_bytes, sample_mib << 20)
+    seg = w.seg_offsets
+    t0 = time.perf_counter()
+    ac.match(w.text, seg, lo=0, hi=nb, threads=threads)
+    dt = time.perf_counter() - t0
+    reps = max(1, int(budget_s / max(dt, 1e-3)))
+    reps = min(reps, 5)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ac.match(w.text, seg, lo=0, hi=nb, threads=threads)
+    dt = (time.perf_counter() - t0) / reps
+    ac.close()
+    return {"value": round(8 * nb / dt / 1e9, 4), "unit": "Gbps", "cores": threads,
+            "kind": "oracle",
+            "sample": f"start positions [0, {nb >> 20} MiB) of the workload, Aho-Corasick with "
+                      f"failure links in C on {threads} threads, mean of {reps} runs"}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    w = load_workload(args.workload, 0)
+    import oracle
+    threads = oracle.default_threads()
+    ac = oracle.ACOracle(w.patterns)
+    nb = min(w.n_bytes, args.ref_sample_mib << 20)
+    for _ in range(args.warmup):
+        ac.match(w.text, w.seg_offsets, lo=0, hi=nb, threads=threads)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ac.match(w.text, w.seg_offsets, lo=0, hi=nb, threads=threads)
+        t.append(time.perf_counter() - t0)
+    ac.close()
+    ms = 1e3 * sum(t) / len(t)
+    v = 8 * nb / (ms / 1e3) / 1e9
+    sample = (f"start positions [0, {nb >> 20} MiB) of the workload per step, Aho-Corasick with "
+              f"failure links in C on {threads} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": "scan Gbps", "value": round(v, 4), "unit": "Gbps",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload)},
+        "cpu_baseline": {"value": round(v, 4), "unit": "Gbps", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "Gbps", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1704_02272_gb300 as pfac
+
+    w = load_workload(args.workload, rank)
+    N = w.n_bytes
+    S = len(w.seg_offsets) - 1
+    text = torch.from_numpy(w.text).to(dev)
+    seg = torch.from_numpy(w.seg_offsets.astype(np.int64)).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    t0 = time.perf_counter()
+    table = pfac.Table(w.patterns, w.sigma)
+    build_s = time.perf_counter() - t0
+    info = table.info()
+    t0 = time.perf_counter()
+    dense = pfac.Table(w.patterns, w.sigma, layout=pfac.LAYOUT_DENSE)
+    dense_build_s = time.perf_counter() - t0
+    dinfo = dense.info()
+
+    with torch.cuda.stream(stream):
+        keys = pfac.match(table, text, seg, stream=stream)
+        stream.synchronize()
+    n_match = keys.numel()
+    cap = n_match + 1024
+    out = torch.empty(cap, dtype=torch.int64, device=dev)
+    ws = torch.empty(pfac.workspace_bytes(table, N, S), dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    K, W = args.steps, args.warmup
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sc_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sc_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for e in ev_b + ev_e + sc_b + sc_e:  # creates the CUDA events
+            e.record(stream)
+    stream.synchronize()
+
+    def step(i=None, tbl=table):
+        opt = {} if i is None else {"scan_events": (sc_b[i], sc_e[i])}
+        pfac.match_async(tbl, text, seg, out, cnt, st, ws, stream=stream, **opt)
+
+    for _ in range(W):
+        step()
+    stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    for i in range(K):
+        ev_b[i].record(stream)
+        step(i)
+        ev_e[i].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [ev_b[i].elapsed_time(ev_e[i]) for i in range(K)]
+    scan_ms = [sc_b[i].elapsed_time(sc_e[i]) for i in range(K)]
+    total_ms = ev_b[0].elapsed_time(ev_e[K - 1])
+    assert int(st.item()) == 0, f"device status {int(st.item())}"
+    assert int(cnt.item()) == n_match
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = 8.0 * N * world * K / (total_ms / 1e3) / 1e9
+
+    # uncompressed table on the same GPU, same input
+    dk = pfac.match(dense, text, seg, stream=stream)
+    stream.synchronize()
+    exact = bool(torch.equal(dk, keys))
+    for _ in range(W):
+        step(tbl=dense)
+    stream.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(K):
+        step(tbl=dense)
+    d1.record(stream)
+    stream.synchronize()
+    dense_gbps = 8.0 * N * K / (d0.elapsed_time(d1) / 1e3) / 1e9
+
+    # end to end through the C ABI from host buffers
+    host_in = torch.from_numpy(w.text).pin_memory()
+    host_seg = torch.from_numpy(w.seg_offsets.astype(np.int64)).pin_memory()
+    host_out = torch.empty(cap, dtype=torch.int64).pin_memory()
+    host_cnt = torch.empty(1, dtype=torch.int64).pin_memory()
+    text2 = torch.empty_like(text)
+    seg2 = torch.empty_like(seg)
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            text2.copy_(host_in, non_blocking=True)
+            seg2.copy_(host_seg, non_blocking=True)
+            pfac.match_async(table, text2, seg2, out, cnt, st, ws, stream=stream)
+            host_cnt.copy_(cnt, non_blocking=True)
+            stream.synchronize()
+            n = int(host_cnt.item())
+            host_out[:n].copy_(out[:n], non_blocking=True)
+            stream.synchronize()
+        return n
+
+    for _ in range(max(1, W)):
+        e2e_step()
+    e0 = time.perf_counter()
+    e2e_n = 0
+    for _ in range(K):
+        e2e_n = e2e_step()
+    e2e_s = (time.perf_counter() - e0) / K
+    e2e = {"value": round(8.0 * N * world / e2e_s / 1e9, 3), "unit": "Gbps",
+           "h2d_bytes_per_step": int(N + 8 * (S + 1)),
+           "d2h_bytes_per_step": int(8 + 8 * e2e_n)}
+    assert e2e_n == n_match
+
+    hbm_peak, peak_kind = peaks()
+    matched_frac = None
+    # algorithmic bytes of one scan launch: every input byte once, the 16-byte
+    # halo of each 8 KiB tile, and one 8-byte record per matched position
+    pos = keys >> 24
+    matched_positions = int(torch.unique_consecutive(pos).numel()) if n_match else 0
+    matched_frac = matched_positions / N
+    tiles = (N + 8191) // 8192
+    alg_bytes = N + 16 * tiles + 8 * matched_positions
+    scan_avg_ms = sum(scan_ms) / K
+    achieved = alg_bytes / (scan_avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": args.traffic, "kernel": "k_scan",
+                "alg_bytes_per_launch": alg_bytes}
+
+    line = {
+        "metric": "scan Gbps (1xGB300) compressed vs uncompressed PFAC, bit-exact; table bytes; "
+                  "p99 latency",
+        "value": round(value, 3), "unit": "Gbps", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload),
+                   "n_bytes": N, "segments": S, "patterns": len(w.patterns),
+                   "alphabet": w.sigma, "l2": "input larger than L2, no flush",
+                   "variant": "default", "prefix_depth": info["prefix_depth"]},
+        "p50_ms": round(statistics.median(step_ms), 4),
+        "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+        "matches": n_match, "matched_position_frac": round(matched_frac, 6),
+        "table_bytes": {"compressed": info["device_bytes"], "dense": dinfo["device_bytes"],
+                        "paper_model": info["paper_bytes"], "trie_nodes": info["trie_nodes"],
+                        "records": info["records"], "merged_leaves": info["merged_leaves"]},
+        "dense": {"value": round(dense_gbps, 3), "unit": "Gbps", "bit_exact_vs_compressed": exact},
+        "build_s": {"compressed": round(build_s, 3), "dense": round(dense_build_s, 3)},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": SCAN_KERNELS_PER_STEP * K + (K if S > 1 else 0),
+        "clocks": clk,
+        "wall_s_timed": round(wall, 4),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    table.close()
+    dense.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dna")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per scan launch from an ncu capture of this build")
+    ap.add_argument("--ref-sample-mib", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * pfac.h - C ABI of the GB300 failure-less Aho-Corasick (PFAC) matcher.
+ *
+ * The library implements exact multi-pattern matching as the paper states it
+ * (Section 2.2: find every occurrence of a set of fixed patterns P in a text
+ * T) with the failure-less method of Section 2.3: one walk starts at every
+ * input position and follows the trie of the patterns until a symbol has no
+ * transition, reporting every pattern it completes.  The trie is stored in
+ * the bitmap storage model of Section 3.1 (per-node symbol bitmap, children
+ * addressed by popcount rank, Eq. 1) with the leaf merge of Section 3.2
+ * (Eq. 2), plus a dense lookup for the first trie levels.
+ *
+ * Result definition.  With distinct non-empty patterns P_0..P_{n-1} over the
+ * symbols 0..sigma-1, a text T[0..N) and segment offsets
+ * 0 = o_0 <= o_1 <= ... <= o_S = N, the result is the set of pairs
+ *     (p, j)  with  o_k <= p,  p + |P_j| <= o_{k+1},  T[p .. p+|P_j|) = P_j
+ * for some k (no occurrence crosses a segment end), sorted by p then j.
+ * p is a global byte offset into T; j is the caller's index of the pattern.
+ * A text byte >= sigma matches nothing (it ends every walk that reaches it).
+ *
+ * Output keys.  Each pair is returned as one uint64 key
+ *     key = (uint64)p << PFAC_ID_BITS | j,
+ * so ascending numeric order of keys is the (p, j) order.  This requires
+ * n_patterns < 2^PFAC_ID_BITS and N < 2^(64 - PFAC_ID_BITS).
+ *
+ * Memory and streams.  Pointers named d_* are CUDA device pointers owned by
+ * the caller; all other pointers are host pointers.  Every call takes the
+ * CUDA stream (a cudaStream_t passed as void*, NULL = legacy default stream)
+ * on which its device work is ordered.  The table is owned by the library
+ * from pfac_build until pfac_table_free.  Calls on one table may run
+ * concurrently on different streams as long as each uses its own workspace.
+ *
+ * Errors.  Every int-returning call returns a pfac_status; 0 is success.  A
+ * failing call leaves its outputs unspecified (except PFAC_ENOSPC, below),
+ * records a message retrievable with pfac_last_error (per host thread) and
+ * never aborts the process.
+ */
+#ifndef PFAC_H
+#define PFAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFAC_ID_BITS 24
+#define PFAC_MAX_PATTERN_LEN (1u << 20)
+
+typedef enum {
+    PFAC_OK = 0,
+    PFAC_EINVAL = -1,   /* bad argument: sizes, pointers, alignment, offsets */
+    PFAC_EDUP = -2,     /* two patterns are equal */
+    PFAC_ESYMBOL = -3,  /* a pattern symbol is >= alphabet_size */
+    PFAC_ENOMEM = -4,   /* host or device allocation failed */
+    PFAC_ENOSPC = -5,   /* output capacity too small; count reported */
+    PFAC_ECUDA = -6,    /* a CUDA runtime call failed */
+    PFAC_ETIMEOUT = -7, /* a bounded device wait gave up */
+    PFAC_EDEVICE = -8   /* a device-side consistency check failed */
+} pfac_status;
+
+typedef enum {
+    PFAC_LAYOUT_COMPRESSED = 0, /* bitmap trie + leaf merge + prefix table */
+    PFAC_LAYOUT_DENSE = 1       /* uncompressed state-transition table */
+} pfac_layout;
+
+typedef struct pfac_table pfac_table;
+
+/* Build options; a NULL pointer means all fields 0 (defaults). */
+typedef struct {
+    uint32_t layout;       /* pfac_layout */
+    uint32_t prefix_depth; /* symbols resolved by the dense prefix lookup
+                              (compressed layout); 0 = chosen by the library */
+    uint32_t flags;        /* PFAC_BUILD_* bits */
+    uint32_t reserved[5];
+} pfac_build_opts;
+
+/* Build flag: build the table on the host only (no device memory, no CUDA
+ * call); the table then answers pfac_table_info but cannot match. */
+#define PFAC_BUILD_HOST_ONLY 1u
+
+/* Match options; a NULL pointer means library defaults (the table's
+ * autotuned choice when pfac_autotune has run). */
+typedef struct {
+    uint32_t variant;      /* 0 = default, 1 = prefix bitmap filter in shared
+                              memory, 2 = prefix table in shared memory,
+                              3 = prefix table through L2 only */
+    uint32_t prefix_depth; /* 0 = table default; else one the table holds */
+    uint32_t ctas_per_sm;  /* 0 = default (1) */
+    uint32_t flags;        /* reserved, 0 */
+    void *ev_scan_begin;   /* optional cudaEvent_t recorded on the call's stream
+                              right before the scan kernel, for profiling */
+    void *ev_scan_end;     /* optional cudaEvent_t recorded right after it */
+    uint32_t reserved[4];
+} pfac_match_opts;
+
+typedef struct {
+    uint32_t alphabet_size;
+    uint32_t n_patterns;
+    uint32_t min_len, max_len;
+    uint32_t layout;
+    uint32_t prefix_depth;     /* default prefix depth of the table */
+    uint64_t trie_nodes;       /* Q: nodes of the uncompressed trie, root included */
+    uint64_t trie_leaves;      /* childless nodes */
+    uint64_t records;          /* node records stored after the leaf merge */
+    uint64_t merged_leaves;    /* leaves folded into their parent's record */
+    uint64_t device_bytes;     /* bytes of the device-resident table */
+    uint64_t paper_bytes;      /* Q * (ceil(sigma/8) + 4): Section 3.1 model */
+    uint64_t dense_bytes;      /* Q * 4 * sigma: one next state per symbol */
+    uint64_t output_lists;     /* distinct sorted id lists */
+    uint64_t output_list_words;
+} pfac_table_info_t;
+
+/*
+ * pfac_build - build the matching table of a pattern set (Sections 3.1, 3.2).
+ *
+ *   patterns[i], lengths[i]  host pointer and length of pattern i (its id);
+ *                            1 <= lengths[i] <= PFAC_MAX_PATTERN_LEN, every
+ *                            byte < alphabet_size.  Copied; the caller keeps
+ *                            ownership.
+ *   n_patterns               0 <= n < 2^PFAC_ID_BITS (0 gives an empty table)
+ *   alphabet_size            1..256
+ *   opts                     may be NULL
+ *   cuda_stream              stream of the table upload; the call returns
+ *                            after the upload completed
+ *   out                      receives the table (owned by the library)
+ *
+ * Errors: PFAC_EINVAL (sizes, NULL pointers, empty or too long pattern),
+ * PFAC_ESYMBOL, PFAC_EDUP, PFAC_ENOMEM, PFAC_ECUDA.
+ */
+int pfac_build(const uint8_t *const *patterns, const uint32_t *lengths, uint32_t n_patterns,
+               uint32_t alphabet_size, const pfac_build_opts *opts, void *cuda_stream,
+               pfac_table **out);
+
+/*
+ * pfac_workspace_bytes - device scratch needed by pfac_match_async for an
+ * input of n_bytes split into n_segments segments.  Writes *bytes.
+ */
+int pfac_workspace_bytes(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments,
+                         const pfac_match_opts *opts, uint64_t *bytes);
+
+/*
+ * pfac_match_async - match a device-resident text (Section 2.3), fully
+ * stream-ordered: no host synchronisation, no allocation; capturable into a
+ * CUDA graph.
+ *
+ *   d_input          n_bytes symbols; 16-byte aligned (else PFAC_EINVAL)
+ *   d_seg_offsets    n_segments + 1 uint64 offsets, o_0 = 0, non-decreasing,
+ *                    o_S = n_bytes (checked on the device: a violation makes
+ *                    the call report PFAC_EINVAL through d_status)
+ *   d_out_keys       room for out_capacity keys; the first
+ *                    min(count, out_capacity) sorted keys are written
+ *   d_count          device uint64: receives the total match count
+ *   d_status         device int32 (may be NULL): receives PFAC_OK, PFAC_EINVAL
+ *                    (bad offsets) or PFAC_EDEVICE
+ *   d_workspace      pfac_workspace_bytes() bytes, 256-byte aligned, owned by
+ *                    the caller; must not be shared by concurrent calls
+ *
+ * Host-side argument errors return PFAC_EINVAL; launch failures PFAC_ECUDA.
+ */
+int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
+                     const uint64_t *d_seg_offsets, uint32_t n_segments, uint64_t *d_out_keys,
+                     uint64_t out_capacity, uint64_t *d_count, int32_t *d_status,
+                     void *d_workspace, uint64_t workspace_bytes, const pfac_match_opts *opts,
+                     void *cuda_stream);
+
+/*
+ * pfac_match - synchronous form of pfac_match_async: allocates the workspace
+ * with the stream-ordered allocator, matches, waits for the stream and writes
+ * the total match count to the host *n_out.  Returns PFAC_ENOSPC when
+ * count > out_capacity (the first out_capacity keys are valid and *n_out holds
+ * the full count, so a second call with a larger buffer succeeds).
+ */
+int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
+               const uint64_t *d_seg_offsets, uint32_t n_segments, uint64_t *d_out_keys,
+               uint64_t out_capacity, uint64_t *n_out, const pfac_match_opts *opts,
+               void *cuda_stream);
+
+/* pfac_table_info - statistics of a built table (host call, no device work). */
+int pfac_table_info(const pfac_table *t, pfac_table_info_t *out);
+
+/* pfac_table_free - releases the table's host and device memory.  The caller
+ * must make sure no device work that uses the table is still pending. */
+void pfac_table_free(pfac_table *t);
+
+/* Static text of a status code. */
+const char *pfac_status_str(int status);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to n bytes) into buf; returns the status of that error (0 if none). */
+int pfac_last_error(char *buf, size_t n);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int pfac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFAC_H */

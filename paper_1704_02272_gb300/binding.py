@@ -1,0 +1,241 @@
+"""ctypes binding of libpfac (argument marshalling only).
+
+Every call forwards to the C ABI declared in include/pfac.h; all matching work
+runs in the library's CUDA kernels.  There is no CPU path: if libpfac.so is
+missing the import of this module raises.  PyTorch supplies device memory and
+streams: texts, offsets, outputs and workspaces are CUDA tensors, and the
+stream is torch's current stream unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpfac.so")
+
+ID_BITS = 24
+LAYOUT_COMPRESSED, LAYOUT_DENSE = 0, 1
+VARIANT_DEFAULT, VARIANT_FILTER, VARIANT_DSMEM, VARIANT_DGLOBAL = 0, 1, 2, 3
+
+STATUS = {0: "PFAC_OK", -1: "PFAC_EINVAL", -2: "PFAC_EDUP", -3: "PFAC_ESYMBOL",
+          -4: "PFAC_ENOMEM", -5: "PFAC_ENOSPC", -6: "PFAC_ECUDA", -7: "PFAC_ETIMEOUT",
+          -8: "PFAC_EDEVICE"}
+
+
+class PfacError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("layout", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+
+BUILD_HOST_ONLY = 1
+
+
+class MatchOpts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("ev_scan_begin", ctypes.c_void_p), ("ev_scan_end", ctypes.c_void_p),
+                ("reserved", ctypes.c_uint32 * 4)]
+
+
+class TableInfo(ctypes.Structure):
+    _fields_ = [("alphabet_size", ctypes.c_uint32), ("n_patterns", ctypes.c_uint32),
+                ("min_len", ctypes.c_uint32), ("max_len", ctypes.c_uint32),
+                ("layout", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
+                ("trie_nodes", ctypes.c_uint64), ("trie_leaves", ctypes.c_uint64),
+                ("records", ctypes.c_uint64), ("merged_leaves", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("paper_bytes", ctypes.c_uint64),
+                ("dense_bytes", ctypes.c_uint64), ("output_lists", ctypes.c_uint64),
+                ("output_list_words", ctypes.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpfac.so is not built ({LIB_PATH}); run "
+                          "`python paper_1704_02272_gb300/build.py` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u8p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8)
+    u32, u64 = ctypes.c_uint32, ctypes.c_uint64
+    lib.pfac_build.restype = ctypes.c_int
+    lib.pfac_build.argtypes = [ctypes.POINTER(u8p), ctypes.POINTER(u32), u32, u32,
+                               ctypes.POINTER(BuildOpts), vp, ctypes.POINTER(vp)]
+    lib.pfac_workspace_bytes.restype = ctypes.c_int
+    lib.pfac_workspace_bytes.argtypes = [vp, u64, u32, ctypes.POINTER(MatchOpts),
+                                         ctypes.POINTER(u64)]
+    lib.pfac_match_async.restype = ctypes.c_int
+    lib.pfac_match_async.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp, vp, u64,
+                                     ctypes.POINTER(MatchOpts), vp]
+    lib.pfac_match.restype = ctypes.c_int
+    lib.pfac_match.argtypes = [vp, vp, u64, vp, u32, vp, u64, ctypes.POINTER(u64),
+                               ctypes.POINTER(MatchOpts), vp]
+    lib.pfac_table_info.restype = ctypes.c_int
+    lib.pfac_table_info.argtypes = [vp, ctypes.POINTER(TableInfo)]
+    lib.pfac_table_free.restype = None
+    lib.pfac_table_free.argtypes = [vp]
+    lib.pfac_status_str.restype = ctypes.c_char_p
+    lib.pfac_status_str.argtypes = [ctypes.c_int]
+    lib.pfac_last_error.restype = ctypes.c_int
+    lib.pfac_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.pfac_version.restype = ctypes.c_int
+    lib.pfac_version.argtypes = []
+    return lib
+
+
+LIB = _load()
+
+
+def _check(rc: int):
+    if rc != 0:
+        buf = ctypes.create_string_buffer(512)
+        LIB.pfac_last_error(buf, 512)
+        raise PfacError(rc, buf.value.decode(errors="replace"))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, scan_events=None):
+    o = MatchOpts()
+    o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
+    if scan_events is not None:  # (begin, end) torch.cuda.Event pair
+        o.ev_scan_begin = scan_events[0].cuda_event
+        o.ev_scan_end = scan_events[1].cuda_event
+    return o
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else ctypes.c_void_p(0)
+
+
+class Table:
+    """A built matching table (pfac_build); device memory owned by libpfac."""
+
+    def __init__(self, patterns, alphabet_size: int, layout: int = LAYOUT_COMPRESSED,
+                 prefix_depth: int = 0, stream=None, host_only: bool = False):
+        n = len(patterns)
+        bufs = [ctypes.create_string_buffer(bytes(p), len(p)) for p in patterns]
+        arr = (ctypes.POINTER(ctypes.c_uint8) * max(n, 1))()
+        lens = (ctypes.c_uint32 * max(n, 1))()
+        for i, (b, p) in enumerate(zip(bufs, patterns)):
+            arr[i] = ctypes.cast(b, ctypes.POINTER(ctypes.c_uint8))
+            lens[i] = len(p)
+        o = BuildOpts()
+        o.layout, o.prefix_depth = layout, prefix_depth
+        o.flags = BUILD_HOST_ONLY if host_only else 0
+        h = ctypes.c_void_p()
+        st = 0 if host_only else _stream(stream)
+        _check(LIB.pfac_build(arr, lens, n, alphabet_size, ctypes.byref(o),
+                              ctypes.c_void_p(st), ctypes.byref(h)))
+        self._h = h
+        self.alphabet_size = alphabet_size
+        self.layout = layout
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("table is closed")
+        return self._h
+
+    def info(self) -> dict:
+        i = TableInfo()
+        _check(LIB.pfac_table_info(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in TableInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            LIB.pfac_table_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def workspace_bytes(table: Table, n_bytes: int, n_segments: int, **opt) -> int:
+    b = ctypes.c_uint64()
+    o = _opts(**opt)
+    _check(LIB.pfac_workspace_bytes(table.handle, n_bytes, n_segments, ctypes.byref(o),
+                                    ctypes.byref(b)))
+    return b.value
+
+
+def match_async(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,
+                count: torch.Tensor, status: torch.Tensor, workspace: torch.Tensor,
+                stream=None, **opt):
+    """pfac_match_async: everything stays on the device (graph-capturable)."""
+    o = _opts(**opt)
+    n_seg = max(seg.numel() - 1, 0)
+    _check(LIB.pfac_match_async(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg,
+                                _ptr(out), out.numel() if out is not None else 0, _ptr(count),
+                                _ptr(status), _ptr(workspace), workspace.numel(),
+                                ctypes.byref(o), ctypes.c_void_p(_stream(stream))))
+
+
+def match_into(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,
+               stream=None, **opt) -> int:
+    """pfac_match: writes min(count, capacity) sorted keys into ``out`` and
+    returns the total count (PfacError PFAC_ENOSPC when it does not fit)."""
+    o = _opts(**opt)
+    n = ctypes.c_uint64()
+    n_seg = max(seg.numel() - 1, 0)
+    rc = LIB.pfac_match(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg, _ptr(out),
+                        out.numel() if out is not None else 0, ctypes.byref(n), ctypes.byref(o),
+                        ctypes.c_void_p(_stream(stream)))
+    if rc == -5:
+        err = PfacError(rc, f"{n.value} matches exceed capacity {out.numel()}")
+        err.count = n.value
+        raise err
+    _check(rc)
+    return n.value
+
+
+def match(table: Table, text: torch.Tensor, seg: torch.Tensor, capacity: int = None,
+          stream=None, **opt) -> torch.Tensor:
+    """Sorted match keys (int64 tensor on the text's device); grows the output
+    buffer once if the first capacity was too small."""
+    dev = text.device
+    cap = capacity if capacity is not None else max(1024, text.numel() // 64)
+    out = torch.empty(cap, dtype=torch.int64, device=dev)
+    try:
+        n = match_into(table, text, seg, out, stream=stream, **opt)
+    except PfacError as e:
+        if e.status != -5:
+            raise
+        out = torch.empty(e.count, dtype=torch.int64, device=dev)
+        n = match_into(table, text, seg, out, stream=stream, **opt)
+    return out[:n]
+
+
+def unpack(keys: torch.Tensor):
+    """(positions, pattern ids) of packed keys."""
+    return keys >> ID_BITS, keys & ((1 << ID_BITS) - 1)
+
+
+def single_segment(n_bytes: int, device) -> torch.Tensor:
+    return torch.tensor([0, n_bytes], dtype=torch.int64, device=device)
+
+
+def version() -> int:
+    return LIB.pfac_version()

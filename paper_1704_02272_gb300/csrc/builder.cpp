@@ -1,0 +1,498 @@
+// Host-side trie builder and compressor (Sections 3.1 and 3.2).
+//
+// Steps: validate -> sort the patterns alphabetically keeping their ids ->
+// breadth-first construction (children contiguous and in symbol order) ->
+// output lists per state -> leaf merge (Eq. 2) -> bitmap records with
+// popcount-ranked child bases (Eq. 1) -> dense prefix lookups for the first
+// levels -> one device blob uploaded on the caller's stream.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace pfac {
+
+static thread_local int g_last_status = 0;
+static thread_local char g_last_msg[512] = {0};
+
+int set_error(int status, const char *fmt, ...) {
+    g_last_status = status;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_msg, sizeof(g_last_msg), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+void clear_error() {
+    g_last_status = 0;
+    g_last_msg[0] = 0;
+}
+
+namespace {
+
+struct BNode {
+    uint32_t lo, hi;       // range of the sorted pattern list sharing the prefix
+    uint32_t depth;
+    uint32_t parent;
+    uint32_t first_child;  // node index of the first child (valid if n_child)
+    uint32_t n_child;
+    int32_t final_id;      // pattern ending here, or -1
+};
+
+struct Pat {
+    const uint8_t *p;
+    uint32_t len;
+};
+
+bool pat_less(const Pat &a, const Pat &b) {
+    uint32_t m = a.len < b.len ? a.len : b.len;
+    int c = m ? memcmp(a.p, b.p, m) : 0;
+    if (c != 0) return c < 0;
+    return a.len < b.len;
+}
+
+uint32_t bits_per_symbol(uint32_t sigma) {
+    uint32_t b = 1;
+    while ((1u << b) < sigma) b++;
+    return b;
+}
+
+// Appends the sorted id list `ids` to the pool; returns its fin code.
+int put_list(std::vector<uint32_t> &pool, const std::vector<uint32_t> &ids, uint32_t *code) {
+    uint64_t off = pool.size();
+    if (off > FIN_MAX_OFF) return -1;
+    if (ids.size() < FIN_LEN_ESC) {
+        pool.insert(pool.end(), ids.begin(), ids.end());
+        *code = (uint32_t)(off << FIN_LEN_BITS) | (uint32_t)ids.size();
+    } else {
+        pool.push_back((uint32_t)ids.size());
+        pool.insert(pool.end(), ids.begin(), ids.end());
+        *code = (uint32_t)(off << FIN_LEN_BITS) | FIN_LEN_ESC;
+    }
+    return 0;
+}
+
+void get_list(const std::vector<uint32_t> &pool, uint32_t code, std::vector<uint32_t> &ids) {
+    ids.clear();
+    if (!code) return;
+    uint32_t off = code >> FIN_LEN_BITS, len = code & FIN_LEN_ESC;
+    if (len == FIN_LEN_ESC) {
+        len = pool[off];
+        off++;
+    }
+    ids.assign(pool.begin() + off, pool.begin() + off + len);
+}
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+}  // namespace
+}  // namespace pfac
+
+using namespace pfac;
+
+extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *lengths,
+                          uint32_t n_patterns, uint32_t alphabet_size,
+                          const pfac_build_opts *opts, void *cuda_stream, pfac_table **out) {
+    clear_error();
+    if (!out) return set_error(PFAC_EINVAL, "pfac_build: out is NULL");
+    *out = nullptr;
+    if (alphabet_size < 1 || alphabet_size > 256)
+        return set_error(PFAC_EINVAL, "pfac_build: alphabet_size %u not in 1..256", alphabet_size);
+    if (n_patterns >= (1u << PFAC_ID_BITS))
+        return set_error(PFAC_EINVAL, "pfac_build: %u patterns exceed the id range", n_patterns);
+    if (n_patterns && (!patterns || !lengths))
+        return set_error(PFAC_EINVAL, "pfac_build: NULL pattern arrays");
+    pfac_build_opts o{};
+    if (opts) o = *opts;
+    if (o.layout > PFAC_LAYOUT_DENSE)
+        return set_error(PFAC_EINVAL, "pfac_build: unknown layout %u", o.layout);
+    const uint32_t sigma = alphabet_size;
+
+    try {
+        // ---- validate ----------------------------------------------------
+        std::vector<Pat> pats(n_patterns);
+        uint32_t min_len = n_patterns ? 0xFFFFFFFFu : 0, max_len = 0;
+        uint64_t total = 0;
+        for (uint32_t i = 0; i < n_patterns; i++) {
+            uint32_t L = lengths[i];
+            if (L == 0) return set_error(PFAC_EINVAL, "pfac_build: pattern %u is empty", i);
+            if (L > PFAC_MAX_PATTERN_LEN)
+                return set_error(PFAC_EINVAL, "pfac_build: pattern %u longer than %u", i,
+                                 PFAC_MAX_PATTERN_LEN);
+            if (!patterns[i]) return set_error(PFAC_EINVAL, "pfac_build: pattern %u is NULL", i);
+            if (sigma < 256)
+                for (uint32_t k = 0; k < L; k++)
+                    if (patterns[i][k] >= sigma)
+                        return set_error(PFAC_ESYMBOL,
+                                         "pfac_build: pattern %u byte %u is %u >= alphabet %u", i,
+                                         k, patterns[i][k], sigma);
+            pats[i] = Pat{patterns[i], L};
+            min_len = std::min(min_len, L);
+            max_len = std::max(max_len, L);
+            total += L;
+        }
+        if (total >= 0x7FFFFFF0ull)
+            return set_error(PFAC_EINVAL, "pfac_build: %llu pattern bytes exceed 2^31",
+                             (unsigned long long)total);
+
+        // ---- sort alphabetically, keeping ids (Section 3.1) --------------
+        std::vector<uint32_t> order(n_patterns);
+        for (uint32_t i = 0; i < n_patterns; i++) order[i] = i;
+        std::sort(order.begin(), order.end(),
+                  [&](uint32_t a, uint32_t b) { return pat_less(pats[a], pats[b]); });
+        for (uint32_t i = 1; i < n_patterns; i++) {
+            const Pat &a = pats[order[i - 1]], &b = pats[order[i]];
+            if (a.len == b.len && memcmp(a.p, b.p, a.len) == 0)
+                return set_error(PFAC_EDUP, "pfac_build: patterns %u and %u are equal",
+                                 std::min(order[i - 1], order[i]), std::max(order[i - 1], order[i]));
+        }
+        auto sym_at = [&](uint32_t sorted_i, uint32_t d) { return pats[order[sorted_i]].p[d]; };
+        auto len_at = [&](uint32_t sorted_i) { return pats[order[sorted_i]].len; };
+
+        // ---- breadth-first trie -----------------------------------------
+        const uint32_t W = sigma <= 32 ? 1 : (sigma <= 64 ? 2 : 8);
+        std::vector<BNode> nodes;
+        std::vector<uint32_t> bm;  // W words per node
+        nodes.reserve(total + 1);
+        nodes.push_back(BNode{0, n_patterns, 0, 0, 0, 0, -1});
+        bm.assign(W, 0);
+        for (size_t v = 0; v < nodes.size(); v++) {
+            uint32_t lo = nodes[v].lo, hi = nodes[v].hi, d = nodes[v].depth;
+            uint32_t i = lo;
+            if (i < hi && len_at(i) == d) {  // the pattern equal to the prefix sorts first
+                nodes[v].final_id = (int32_t)order[i];
+                i++;
+            }
+            while (i < hi) {
+                uint8_t c = sym_at(i, d);
+                uint32_t k = i;
+                while (k < hi && sym_at(k, d) == c) k++;
+                uint32_t idx = (uint32_t)nodes.size();
+                if (nodes[v].n_child == 0) nodes[v].first_child = idx;
+                nodes[v].n_child++;
+                bm[v * W + (c >> 5)] |= 1u << (c & 31);
+                nodes.push_back(BNode{i, k, d + 1, (uint32_t)v, 0, 0, -1});
+                bm.resize(bm.size() + W, 0);
+                i = k;
+            }
+        }
+        const uint64_t Q = nodes.size();
+        if (Q >= 0x7FFFFFF0ull) return set_error(PFAC_EINVAL, "pfac_build: trie too large");
+
+        // ---- output lists: fin(v) = fin(parent) plus v's own id ----------
+        std::vector<uint32_t> fin_code(Q, 0), pool;
+        std::vector<uint32_t> ids;
+        uint64_t n_lists = 0;
+        for (uint64_t v = 1; v < Q; v++) {
+            uint32_t pc = fin_code[nodes[v].parent];
+            if (nodes[v].final_id < 0) {
+                fin_code[v] = pc;
+                continue;
+            }
+            get_list(pool, pc, ids);
+            ids.insert(std::upper_bound(ids.begin(), ids.end(), (uint32_t)nodes[v].final_id),
+                       (uint32_t)nodes[v].final_id);
+            if (put_list(pool, ids, &fin_code[v]))
+                return set_error(PFAC_ENOMEM, "pfac_build: output lists exceed %u words",
+                                 FIN_MAX_OFF);
+            n_lists++;
+        }
+        if (pool.empty()) pool.push_back(0);
+
+        // ---- leaf merge (Eq. 2) and record numbering ----------------------
+        std::vector<uint8_t> all_leaf(Q, 0);
+        uint64_t n_leaves = 0;
+        for (uint64_t v = 0; v < Q; v++) {
+            if (v > 0 && nodes[v].n_child == 0) n_leaves++;
+            if (nodes[v].n_child) {
+                bool all = true;
+                for (uint32_t c = 0; c < nodes[v].n_child && all; c++)
+                    all = nodes[nodes[v].first_child + c].n_child == 0;
+                all_leaf[v] = all;
+            }
+        }
+        const uint32_t NOREC = 0xFFFFFFFFu;
+        std::vector<uint32_t> rec_of(Q, NOREC);
+        uint32_t n_rec = 0;
+        uint64_t merged = 0;
+        for (uint64_t v = 0; v < Q; v++) {
+            if (v > 0 && nodes[v].n_child == 0 && all_leaf[nodes[v].parent]) {
+                merged++;
+                continue;
+            }
+            rec_of[v] = n_rec++;
+        }
+
+        // ---- prefix lookups ----------------------------------------------
+        const uint32_t bps = bits_per_symbol(sigma);
+        // prefix tables for depths 1..kdef, where the default depth keeps the
+        // bitmap at 2^16 bits; a deeper one (up to 2^18 entries) on request
+        const uint32_t klim = std::min<uint32_t>(std::max(1u, 18 / bps), KMAX);
+        const uint32_t kdef = std::min<uint32_t>(std::max(1u, 16 / bps), klim);
+        if (o.prefix_depth > klim)
+            return set_error(PFAC_EINVAL, "pfac_build: prefix_depth %u > %u", o.prefix_depth, klim);
+        const uint32_t kmax = std::max(kdef, o.prefix_depth);
+        // walk the node-level trie over k symbols packed in x
+        auto child_of = [&](uint32_t v, uint32_t c) -> int64_t {
+            if (c >= sigma) return -1;
+            const uint32_t *b = &bm[(uint64_t)v * W];
+            if (!((b[c >> 5] >> (c & 31)) & 1)) return -1;
+            uint32_t r = 0;
+            for (uint32_t w = 0; w < (c >> 5); w++) r += __builtin_popcount(b[w]);
+            r += __builtin_popcount(b[c >> 5] & ((1u << (c & 31)) - 1));
+            return (int64_t)nodes[v].first_child + r;
+        };
+
+        // ---- section sizes ------------------------------------------------
+        const bool dense = o.layout == PFAC_LAYOUT_DENSE;
+        const int RW = rec_words((int)W);
+        uint64_t sz_rec = dense ? 0 : (uint64_t)n_rec * RW * 4;
+        uint64_t sz_fin = (!dense && W == 1) ? (uint64_t)n_rec * 4 : 0;
+        std::vector<uint32_t> leaf_fin;
+        if (!dense) {
+            leaf_fin.reserve(merged);
+        }
+        uint64_t sz_pool = pool.size() * 4;
+        uint64_t sz_D[KMAX + 1] = {0}, sz_F[KMAX + 1] = {0};
+        if (!dense)
+            for (uint32_t k = 1; k <= kmax; k++) {
+                uint64_t ent = 1ull << (k * bps);
+                sz_D[k] = ent * 4;
+                sz_F[k] = std::max<uint64_t>(ent / 8, 4);
+            }
+        uint64_t sz_stt = dense ? Q * sigma * 4 : 0;
+        uint64_t sz_dfin = dense ? Q * 4 : 0;
+
+        // records and merged-leaf outputs
+        std::vector<uint32_t> rec, finv;
+        if (!dense) {
+            rec.assign((uint64_t)n_rec * RW, 0);
+            if (W == 1) finv.assign(n_rec, 0);
+            for (uint64_t v = 0; v < Q; v++) {
+                uint32_t r = rec_of[v];
+                if (r == NOREC) continue;
+                uint32_t *R = &rec[(uint64_t)r * RW];
+                uint32_t meta = 0;
+                if (all_leaf[v]) {
+                    meta = META_ALL_LEAF | (uint32_t)leaf_fin.size();
+                    for (uint32_t c = 0; c < nodes[v].n_child; c++)
+                        leaf_fin.push_back(fin_code[nodes[v].first_child + c]);
+                } else if (nodes[v].n_child) {
+                    meta = rec_of[nodes[v].first_child];
+                    // children of a node with an internal child all keep records,
+                    // contiguous in breadth-first order
+                    for (uint32_t c = 0; c < nodes[v].n_child; c++)
+                        if (rec_of[nodes[v].first_child + c] != meta + c)
+                            return set_error(PFAC_EDEVICE, "pfac_build: internal error (records)");
+                }
+                for (uint32_t w = 0; w < W; w++) R[w] = bm[v * W + w];
+                if (W == 1) {
+                    R[1] = meta;
+                    finv[r] = fin_code[v];
+                } else if (W == 2) {
+                    R[2] = meta;
+                    R[3] = fin_code[v];
+                } else {
+                    R[8] = meta;
+                    R[9] = fin_code[v];
+                    uint32_t cum = 0;
+                    uint32_t c4[2] = {0, 0};
+                    for (uint32_t w = 0; w < 8; w++) {
+                        c4[w >> 2] |= cum << (8 * (w & 3));
+                        cum += __builtin_popcount(bm[v * W + w]);
+                    }
+                    R[10] = c4[0];
+                    R[11] = c4[1];
+                }
+            }
+        }
+        if (leaf_fin.empty()) leaf_fin.push_back(0);
+        uint64_t sz_leaf = dense ? 0 : leaf_fin.size() * 4;
+
+        // blob layout
+        uint64_t off = 0;
+        auto place = [&](uint64_t sz) {
+            uint64_t at = off;
+            off = align256(off + sz);
+            return at;
+        };
+        uint64_t o_rec = place(sz_rec), o_fin = place(sz_fin), o_leaf = place(sz_leaf),
+                 o_pool = place(sz_pool);
+        uint64_t o_D[KMAX + 1] = {0}, o_F[KMAX + 1] = {0};
+        for (uint32_t k = 1; k <= kmax; k++) {
+            o_D[k] = place(sz_D[k]);
+            o_F[k] = place(sz_F[k]);
+        }
+        uint64_t o_stt = place(sz_stt), o_dfin = place(sz_dfin);
+        const uint64_t blob = std::max<uint64_t>(off, 256);
+
+        std::vector<uint8_t> host;
+        host.assign(blob, 0);
+        auto put = [&](uint64_t at, const void *src, uint64_t n) {
+            if (n) memcpy(host.data() + at, src, n);
+        };
+        put(o_rec, rec.data(), sz_rec);
+        put(o_fin, finv.data(), sz_fin);
+        put(o_leaf, leaf_fin.data(), sz_leaf);
+        put(o_pool, pool.data(), sz_pool);
+        if (!dense)
+            for (uint32_t k = 1; k <= kmax; k++) {
+                uint32_t *D = (uint32_t *)(host.data() + o_D[k]);
+                uint32_t *F = (uint32_t *)(host.data() + o_F[k]);
+                const uint64_t ent = 1ull << (k * bps);
+                const uint32_t smask = (1u << bps) - 1;
+                for (uint64_t x = 0; x < ent; x++) {
+                    uint32_t v = 0;
+                    uint32_t e = 0;
+                    bool stopped = false;
+                    for (uint32_t i = 0; i < k; i++) {
+                        int64_t ch = child_of(v, (uint32_t)(x >> (bps * i)) & smask);
+                        if (ch < 0) {
+                            e = fin_code[v];
+                            stopped = true;
+                            break;
+                        }
+                        v = (uint32_t)ch;
+                    }
+                    if (!stopped) {
+                        if (nodes[v].n_child == 0) e = fin_code[v];  // a leaf ends the walk
+                        else e = D_CONT | rec_of[v];
+                    }
+                    D[x] = e;
+                    if (e) F[x >> 5] |= 1u << (x & 31);
+                }
+            }
+        if (dense) {
+            uint32_t *S = (uint32_t *)(host.data() + o_stt);
+            uint32_t *DF = (uint32_t *)(host.data() + o_dfin);
+            for (uint64_t v = 0; v < Q; v++) {
+                DF[v] = fin_code[v];
+                uint32_t r = 0;
+                for (uint32_t c = 0; c < sigma; c++)
+                    if ((bm[v * W + (c >> 5)] >> (c & 31)) & 1)
+                        S[v * sigma + c] = nodes[v].first_child + r++;
+            }
+        }
+
+        // ---- upload -------------------------------------------------------
+        pfac_table *t = new (std::nothrow) pfac_table();
+        if (!t) return set_error(PFAC_ENOMEM, "pfac_build: host allocation failed");
+        const bool host_only = (o.flags & PFAC_BUILD_HOST_ONLY) != 0;
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        cudaError_t ce = cudaSuccess;
+        if (!host_only) {
+            cudaGetDevice(&t->device);
+            ce = cudaMalloc(&t->d_blob, blob);
+            if (ce != cudaSuccess) {
+                delete t;
+                cudaGetLastError();
+                return set_error(ce == cudaErrorMemoryAllocation ? PFAC_ENOMEM : PFAC_ECUDA,
+                                 "pfac_build: cudaMalloc(%llu): %s", (unsigned long long)blob,
+                                 cudaGetErrorString(ce));
+            }
+            ce = cudaMemcpyAsync(t->d_blob, host.data(), blob, cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+            if (ce != cudaSuccess) {
+                cudaFree(t->d_blob);
+                delete t;
+                return set_error(PFAC_ECUDA, "pfac_build: upload: %s", cudaGetErrorString(ce));
+            }
+        }
+        t->blob_bytes = blob;
+        uint8_t *B = (uint8_t *)t->d_blob;
+        DevTable &dv = t->dev;
+        memset(&dv, 0, sizeof(dv));
+        dv.sigma = sigma;
+        dv.W = W;
+        dv.bps = bps;
+        dv.kdef = kdef;
+        dv.layout = o.layout;
+        dv.max_len = max_len;
+        dv.n_rec = n_rec;
+        dv.n_nodes = (uint32_t)Q;
+        dv.rec = (const uint32_t *)(B + o_rec);
+        dv.fin = (const uint32_t *)(B + o_fin);
+        dv.leaf_fin = (const uint32_t *)(B + o_leaf);
+        dv.pool = (const uint32_t *)(B + o_pool);
+        if (!dense)
+            for (uint32_t k = 1; k <= kmax; k++) {
+                dv.D[k] = (const uint32_t *)(B + o_D[k]);
+                dv.F[k] = (const uint32_t *)(B + o_F[k]);
+            }
+        dv.stt = dense ? (const uint32_t *)(B + o_stt) : nullptr;
+        dv.dfin = dense ? (const uint32_t *)(B + o_dfin) : nullptr;
+        t->kmax = dense ? 0 : kmax;
+        if (!dense && o.prefix_depth) dv.kdef = o.prefix_depth;
+
+        pfac_table_info_t &I = t->info;
+        I.alphabet_size = sigma;
+        I.n_patterns = n_patterns;
+        I.min_len = min_len;
+        I.max_len = max_len;
+        I.layout = o.layout;
+        I.prefix_depth = dense ? 0 : dv.kdef;
+        I.trie_nodes = Q;
+        I.trie_leaves = n_leaves;
+        I.records = dense ? Q : n_rec;
+        I.merged_leaves = dense ? 0 : merged;
+        I.device_bytes = blob;
+        I.paper_bytes = Q * ((sigma + 7) / 8 + 4);
+        I.dense_bytes = Q * 4ull * sigma;
+        I.output_lists = n_lists;
+        I.output_list_words = pool.size();
+        *out = t;
+        return PFAC_OK;
+    } catch (const std::bad_alloc &) {
+        return set_error(PFAC_ENOMEM, "pfac_build: host allocation failed");
+    }
+}
+
+extern "C" int pfac_table_info(const pfac_table *t, pfac_table_info_t *out) {
+    if (!t || !out) return set_error(PFAC_EINVAL, "pfac_table_info: NULL argument");
+    *out = t->info;
+    return PFAC_OK;
+}
+
+extern "C" void pfac_table_free(pfac_table *t) {
+    if (!t) return;
+    if (t->d_blob) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != t->device) cudaSetDevice(t->device);
+        cudaFree(t->d_blob);
+        if (cur != t->device) cudaSetDevice(cur);
+    }
+    delete t;
+}
+
+extern "C" const char *pfac_status_str(int s) {
+    switch (s) {
+        case PFAC_OK: return "ok";
+        case PFAC_EINVAL: return "invalid argument";
+        case PFAC_EDUP: return "duplicate pattern";
+        case PFAC_ESYMBOL: return "pattern symbol outside the alphabet";
+        case PFAC_ENOMEM: return "out of memory";
+        case PFAC_ENOSPC: return "output capacity too small";
+        case PFAC_ECUDA: return "CUDA error";
+        case PFAC_ETIMEOUT: return "device wait timed out";
+        case PFAC_EDEVICE: return "device consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int pfac_last_error(char *buf, size_t n) {
+    if (buf && n) {
+        strncpy(buf, g_last_msg, n - 1);
+        buf[n - 1] = 0;
+    }
+    return g_last_status;
+}
+
+extern "C" int pfac_version(void) { return 100; }

@@ -1,0 +1,28 @@
+// Host-side table object and error reporting shared by the library's
+// translation units.
+#pragma once
+#include <stdarg.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/pfac.h"
+#include "table.h"
+
+struct pfac_table {
+    pfac::DevTable dev;
+    void *d_blob = nullptr;
+    uint64_t blob_bytes = 0;
+    pfac_table_info_t info{};
+    uint32_t kmax = 0;        // prefix tables exist for depths 1..kmax
+    int device = 0;
+    // autotuned defaults (0 = none)
+    uint32_t tuned_variant = 0;
+    uint32_t tuned_k = 0;
+};
+
+namespace pfac {
+
+int set_error(int status, const char *fmt, ...);
+void clear_error();
+
+}  // namespace pfac

@@ -1,0 +1,641 @@
+// Device code of the failure-less matcher (Section 2.3) on sm_103a.
+//
+// Scan kernel (k_scan): a persistent grid, one CTA per SM.  Warp 16 is the
+// producer: one lane streams 8 KiB input tiles (plus a 16-byte halo) from HBM
+// into a 4-stage shared-memory ring with cp.async.bulk, completion tracked by
+// mbarriers.  Warps 0..15 consume: each thread owns 16 consecutive start
+// positions.  Per position it forms the index of the next k symbols, tests the
+// prefix bitmap (or reads the prefix table) kept in shared memory, and only the
+// survivors continue the walk through the bitmap records (Eq. 1) in L2.  The
+// walk result of a position is fin(state where it stopped), the sorted id list
+// of every pattern it completed.  A block scan gives each thread its slot; the
+// tile's (position, fin) records go to a per-tile region of the workspace and
+// the tile's match and key counts to per-tile counters.
+//
+// Ordering kernels: k_reduce scans the per-tile key counts (chunk sums plus a
+// last-block scan of the chunks), k_offsets turns them into per-tile output
+// offsets, k_expand writes the sorted keys of each tile from its records, and
+// tiles whose records did not fit re-run k_scan in emit mode, which writes
+// keys directly.  No kernel waits on another CTA, so there is no inter-CTA
+// spinning anywhere; the only waits are the mbarrier waits of the ring, each
+// bounded by a wall-clock limit after which the kernel records PFAC_ETIMEOUT.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "table.h"
+
+namespace pfac {
+
+constexpr int CW = 16;                  // consumer warps
+constexpr int NCONS = CW * 32;          // consumer threads
+constexpr int NTHREADS = NCONS + 32;    // plus one producer warp
+constexpr int BPT = 16;                 // start positions per consumer thread
+constexpr int TILE = NCONS * BPT;       // 8192 positions per tile
+constexpr int HALO = 16;                // staged bytes past the tile (k - 1 <= 15)
+constexpr int STAGES = 4;
+constexpr int STAGE_IN = TILE + 128;    // bytes per input stage
+constexpr int SEGW = 64;                // tile segment block: [count, <= 63 bounds]
+constexpr int SEG_MAXB = SEGW - 1;
+constexpr uint32_t SEG_OVF = 0xFFFFFFFFu;
+constexpr int REC_CAP = TILE / 16;      // records kept per tile by the scan pass
+constexpr int TABLE_SMEM_MAX = 128 * 1024;
+constexpr uint64_t WAIT_LIMIT_NS = 4000000000ull;  // bounded waits: 4 s
+
+constexpr int ST_BADSEG = 1, ST_TIMEOUT = 2, ST_DEVICE = 4;
+
+enum { VAR_FILTER = 1, VAR_DSMEM = 2, VAR_DGLOBAL = 3, VAR_DENSE = 4 };
+
+struct WsHeader {
+    int32_t status;
+    uint32_t ovf_count;
+    uint32_t done_reduce;
+    uint32_t done_expand;
+    uint32_t pad[12];
+};
+
+struct MatchParams {
+    DevTable T;
+    const uint8_t *in;
+    uint64_t n;
+    const uint64_t *seg;
+    uint32_t n_seg;
+    uint32_t n_tiles;
+    uint64_t *out;
+    uint64_t cap;
+    uint64_t *d_count;
+    int32_t *d_status;
+    // workspace
+    WsHeader *hdr;
+    uint32_t *tile_m;
+    uint64_t *tile_k;
+    uint64_t *key_off;
+    uint64_t *chunk;      // n_chunks sums, then n_chunks offsets
+    uint32_t n_chunks;
+    uint32_t *ovf_list;
+    uint64_t *recs;
+    uint32_t *tile_bounds;
+    // scan configuration
+    uint32_t k;           // prefix depth
+    const uint32_t *D;    // prefix table of depth k (global)
+    const uint32_t *F;    // prefix bitmap of depth k (global)
+    uint32_t tbl_words;   // 32-bit words of the shared-memory table
+    uint32_t rep_log2;    // bitmap copies in shared memory (log2)
+    uint32_t dense_rows;  // dense layout: states whose rows live in shared memory
+};
+
+// ------------------------------------------------------------ PTX helpers --
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of `parity` to complete; gives up after WAIT_LIMIT_NS.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; it++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+            __nanosleep(128);
+        }
+    }
+}
+
+// One bulk copy global -> this CTA's shared memory (no multicast); 16-byte
+// aligned addresses, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void cons_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NCONS) : "memory");
+}
+
+// Barrier over the consumer warps that also ANDs a predicate across them.
+__device__ __forceinline__ bool cons_bar_and(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(NCONS)
+        : "memory");
+    return r != 0;
+}
+
+// ------------------------------------------------------------ outputs ------
+
+__device__ __forceinline__ uint32_t fin_len(const uint32_t *__restrict__ pool, uint32_t f) {
+    uint32_t l = f & FIN_LEN_ESC;
+    return l == FIN_LEN_ESC ? __ldg(pool + (f >> FIN_LEN_BITS)) : l;
+}
+
+__device__ __forceinline__ const uint32_t *fin_ids(const uint32_t *__restrict__ pool, uint32_t f) {
+    return pool + (f >> FIN_LEN_BITS) + (((f & FIN_LEN_ESC) == FIN_LEN_ESC) ? 1 : 0);
+}
+
+// ------------------------------------------------------------ walks --------
+
+// Continues a walk at record r with the next symbol at relative position q
+// (Eq. 1 per step); returns fin of the state where it stops.  Positions below
+// `staged` are read from the staged tile, others from global memory; q never
+// reaches `lim` (the segment end, clipped to the input end).
+template <int W>
+__device__ __noinline__ uint32_t walk_rec(const uint32_t *__restrict__ rec,
+                                          const uint32_t *__restrict__ fin1,
+                                          const uint32_t *__restrict__ leaf_fin, uint32_t sigma,
+                                          uint32_t r, const uint8_t *sm, uint32_t staged,
+                                          const uint8_t *__restrict__ g, uint32_t q,
+                                          uint32_t lim) {
+    constexpr int RW = rec_words(W);
+    while (q < lim) {
+        const uint32_t *R = rec + (size_t)r * RW;
+        const uint32_t c = q < staged ? (uint32_t)sm[q] : (uint32_t)__ldg(g + q);
+        if (c >= sigma) break;
+        uint32_t word, below;
+        if (W == 1) {
+            word = __ldg(R);
+            below = 0;
+        } else if (W == 2) {
+            const uint2 b = __ldg(reinterpret_cast<const uint2 *>(R));
+            word = c < 32 ? b.x : b.y;
+            below = c < 32 ? 0u : (uint32_t)__popc(b.x);
+        } else {
+            word = __ldg(R + (c >> 5));
+            const uint32_t cw = __ldg(R + 10 + (c >> 7));
+            below = (cw >> (8 * ((c >> 5) & 3))) & 0xFFu;
+        }
+        const uint32_t bit = c & 31;
+        if (!((word >> bit) & 1u)) break;
+        const uint32_t rank = below + (uint32_t)__popc(word & ((1u << bit) - 1u));
+        const uint32_t meta = __ldg(R + W);
+        const uint32_t base = meta & META_BASE_MASK;
+        if (meta & META_ALL_LEAF) return __ldg(leaf_fin + base + rank);
+        r = base + rank;
+        q++;
+    }
+    return W == 1 ? __ldg(fin1 + r) : __ldg(rec + (size_t)r * RW + W + 1);
+}
+
+// Uncompressed walk: state s, next-state table rows of sigma entries; rows of
+// states below `nrows` are read from shared memory.
+static __device__ __noinline__ uint32_t walk_dense(const uint32_t *__restrict__ stt,
+                                            const uint32_t *__restrict__ dfin, uint32_t sigma,
+                                            const uint32_t *srows, uint32_t nrows, uint32_t s,
+                                            const uint8_t *sm, uint32_t staged,
+                                            const uint8_t *__restrict__ g, uint32_t q,
+                                            uint32_t lim) {
+    while (q < lim) {
+        const uint32_t c = q < staged ? (uint32_t)sm[q] : (uint32_t)__ldg(g + q);
+        if (c >= sigma) break;
+        const uint32_t nx = s < nrows ? srows[s * sigma + c] : __ldg(stt + (size_t)s * sigma + c);
+        if (!nx) break;
+        s = nx;
+        q++;
+    }
+    return __ldg(dfin + s);
+}
+
+// ------------------------------------------------------------ packing ------
+
+// Packs the 32 window bytes into a bit string of BPS bits per symbol (first
+// symbol lowest); bs has BPS + 1 words, the last one zero.
+template <int BPS>
+__device__ __forceinline__ void pack_symbols(const uint32_t (&x)[8], uint32_t (&bs)[BPS + 1]) {
+    if (BPS == 8) {
+#pragma unroll
+        for (int w = 0; w < 8; w++) bs[w] = x[w];
+        bs[BPS] = 0;
+    } else if (BPS == 2) {
+        // four 2-bit symbols in the low bits of four bytes -> one byte
+        uint32_t b[8];
+#pragma unroll
+        for (int w = 0; w < 8; w++) {
+            uint32_t t = x[w] & 0x03030303u;
+            t = t | (t >> 6);            // s0|s1<<2 at bits 0..3, s2|s3<<2 at 16..19
+            t = (t & 0x000F000Fu);
+            b[w] = (t | (t >> 12)) & 0xFFu;
+        }
+        bs[0] = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+        bs[1] = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+        bs[2] = 0;
+    } else {
+#pragma unroll
+        for (int w = 0; w <= BPS; w++) bs[w] = 0;
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const uint32_t s = (x[i >> 2] >> (8 * (i & 3))) & ((1u << BPS) - 1u);
+            const int bit = BPS * i;
+            bs[bit >> 5] |= s << (bit & 31);
+            if ((bit & 31) + BPS > 32) bs[(bit >> 5) + 1] |= s >> (32 - (bit & 31));
+        }
+    }
+}
+
+// Bits [BPS*j, BPS*j + 32) of the packed string.
+template <int BPS>
+__device__ __forceinline__ uint32_t symbols_at(const uint32_t (&bs)[BPS + 1], int j) {
+    const int bit = BPS * j;
+    return __funnelshift_r(bs[bit >> 5], bs[(bit >> 5) + 1], bit & 31);
+}
+
+// ------------------------------------------------------------ tile pieces --
+
+// First segment end strictly above relative position p (clipped to rem).
+__device__ __forceinline__ uint32_t seg_limit(const uint32_t *segs, uint32_t p, uint32_t rem,
+                                              const uint64_t *__restrict__ gseg, uint32_t n_seg,
+                                              uint64_t tile_start) {
+    if (n_seg <= 1) return rem;
+    const uint32_t nb = segs[0];
+    if (nb == SEG_OVF) {
+        // more boundaries than the tile block holds: search the offsets
+        const uint64_t ap = tile_start + p;
+        uint32_t lo = 1, hi = n_seg;  // first index s in [1, n_seg] with o_s > ap
+        while (lo < hi) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(gseg + mid) > ap) hi = mid; else lo = mid + 1;
+        }
+        const uint64_t e = __ldg(gseg + lo);
+        const uint64_t r = e > tile_start ? e - tile_start : 0;
+        return r < rem ? (uint32_t)r : rem;
+    }
+    uint32_t lo = 0, hi = nb;  // first entry > p among segs[1..nb]
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (segs[1 + mid] > p) hi = mid; else lo = mid + 1;
+    }
+    const uint32_t r = lo < nb ? segs[1 + lo] : rem;
+    return r < rem ? r : rem;
+}
+
+// Walk results of one consumer thread's 16 positions (compressed layout).
+template <int W, int BPS, int VAR>
+__device__ __forceinline__ void thread_positions(const MatchParams &P, const uint8_t *sin,
+                                                 uint32_t staged, uint32_t valid, uint32_t rem,
+                                                 const uint32_t *segs, uint64_t tile_start,
+                                                 const uint8_t *__restrict__ g,
+                                                 const uint32_t *stbl, uint32_t tid,
+                                                 uint32_t (&fr)[BPT]) {
+    const uint32_t p0 = tid * BPT;
+    const uint32_t k = P.k;
+    const uint32_t sigma = P.T.sigma;
+#pragma unroll
+    for (int j = 0; j < BPT; j++) fr[j] = 0;
+    if (p0 >= valid) return;
+    const uint32_t lim = seg_limit(segs, p0, rem, P.seg, P.n_seg, tile_start);
+    const uint32_t span = p0 + BPT - 1 + k;  // one past the last symbol read
+    bool fast = span <= lim && span <= staged;
+    uint32_t x[8];
+    if (fast) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(sin + p0);
+        const uint4 b = *reinterpret_cast<const uint4 *>(sin + p0 + 16);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        if (BPS < 8) {
+            // every symbol the window uses must fit in BPS bits
+            const uint32_t hm = 0x01010101u * ((0xFFu << BPS) & 0xFFu);
+            const uint32_t nbytes = BPT - 1 + k;
+            uint32_t bad = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                const uint32_t lo = 4u * w;
+                uint32_t m = hm;
+                if (lo + 4 > nbytes)
+                    m = lo >= nbytes ? 0u : (hm & (0xFFFFFFFFu >> (8u * (lo + 4 - nbytes))));
+                bad |= x[w] & m;
+            }
+            fast = bad == 0;
+        }
+    }
+    if (fast) {
+        uint32_t bs[BPS + 1];
+        pack_symbols<BPS>(x, bs);
+        const uint32_t kmask = (1u << (BPS * k)) - 1u;
+        uint32_t idx[BPT];
+#pragma unroll
+        for (int j = 0; j < BPT; j++) idx[j] = symbols_at<BPS>(bs, j) & kmask;
+        uint32_t ent[BPT];
+        uint32_t surv = 0;
+        if (VAR == VAR_FILTER) {
+            const uint32_t rep = P.rep_log2;
+            const uint32_t copy = tid & ((1u << rep) - 1u);
+#pragma unroll
+            for (int j = 0; j < BPT; j++) {
+                const uint32_t w = stbl[((idx[j] >> 5) << rep) | copy];
+                surv |= ((w >> (idx[j] & 31)) & 1u) << j;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < BPT; j++) {
+                ent[j] = VAR == VAR_DSMEM ? stbl[idx[j]] : __ldg(P.D + idx[j]);
+                surv |= (ent[j] != 0 ? 1u : 0u) << j;
+            }
+        }
+        if (surv) {
+#pragma unroll
+            for (int j = 0; j < BPT; j++) {
+                if ((surv >> j) & 1u) {
+                    const uint32_t e = VAR == VAR_FILTER ? __ldg(P.D + idx[j]) : ent[j];
+                    fr[j] = (e & D_CONT)
+                                ? walk_rec<W>(P.T.rec, P.T.fin, P.T.leaf_fin, sigma,
+                                              e & D_VAL_MASK, sin, staged, g, p0 + j + k, lim)
+                                : e;
+                }
+            }
+        }
+        return;
+    }
+    // general path: segment ends inside the window, the input end, or
+    // symbols outside the packed range -> walk every position from the root
+#pragma unroll 1
+    for (int j = 0; j < BPT; j++) {
+        const uint32_t p = p0 + j;
+        if (p >= valid) break;
+        const uint32_t lj = seg_limit(segs, p, rem, P.seg, P.n_seg, tile_start);
+        const uint32_t f = walk_rec<W>(P.T.rec, P.T.fin, P.T.leaf_fin, sigma, 0u, sin, staged, g,
+                                       p, lj);
+        // keep fr in registers: select by position
+#pragma unroll
+        for (int i = 0; i < BPT; i++)
+            if (i == j) fr[i] = f;
+    }
+}
+
+// Walk results of one thread's 16 positions (uncompressed layout).
+__device__ __forceinline__ void thread_positions_dense(const MatchParams &P, const uint8_t *sin,
+                                                       uint32_t staged, uint32_t valid,
+                                                       uint32_t rem, const uint32_t *segs,
+                                                       uint64_t tile_start,
+                                                       const uint8_t *__restrict__ g,
+                                                       const uint32_t *srows, uint32_t tid,
+                                                       uint32_t (&fr)[BPT]) {
+    const uint32_t p0 = tid * BPT;
+    const uint32_t sigma = P.T.sigma;
+#pragma unroll
+    for (int j = 0; j < BPT; j++) fr[j] = 0;
+    if (p0 >= valid) return;
+    const uint32_t lim = seg_limit(segs, p0, rem, P.seg, P.n_seg, tile_start);
+    const uint32_t span = p0 + BPT;
+    if (span <= lim && span <= staged) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(sin + p0);
+        const uint32_t x[4] = {a.x, a.y, a.z, a.w};
+        uint32_t s1[BPT];
+        uint32_t surv = 0;
+#pragma unroll
+        for (int j = 0; j < BPT; j++) {
+            const uint32_t c = (x[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+            s1[j] = c < sigma ? srows[c] : 0u;  // root row is row 0 in shared memory
+            surv |= (s1[j] != 0 ? 1u : 0u) << j;
+        }
+        if (surv) {
+#pragma unroll
+            for (int j = 0; j < BPT; j++)
+                if ((surv >> j) & 1u)
+                    fr[j] = walk_dense(P.T.stt, P.T.dfin, sigma, srows, P.dense_rows, s1[j], sin,
+                                       staged, g, p0 + j + 1, lim);
+        }
+        return;
+    }
+#pragma unroll 1
+    for (int j = 0; j < BPT; j++) {
+        const uint32_t p = p0 + j;
+        if (p >= valid) break;
+        const uint32_t lj = seg_limit(segs, p, rem, P.seg, P.n_seg, tile_start);
+        const uint32_t f = walk_dense(P.T.stt, P.T.dfin, sigma, srows, P.dense_rows, 0u, sin,
+                                      staged, g, p, lj);
+#pragma unroll
+        for (int i = 0; i < BPT; i++)
+            if (i == j) fr[i] = f;
+    }
+}
+
+// Exclusive scan over the consumer threads; returns the prefix, sets total.
+__device__ __forceinline__ uint64_t cons_scan(uint64_t v, uint64_t *wt, uint64_t &total,
+                                              uint32_t tid) {
+    const uint32_t lane = tid & 31, w = tid >> 5;
+    uint64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += nb;
+    }
+    if (lane == 31) wt[w] = inc;
+    cons_bar();
+    if (w == 0) {
+        uint64_t t = lane < CW ? wt[lane] : 0;
+        uint64_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t nb = __shfl_up_sync(0xFFFFFFFFu, ti, o);
+            if (lane >= (uint32_t)o) ti += nb;
+        }
+        if (lane < CW) wt[lane] = ti - t;
+        if (lane == CW - 1) wt[CW] = ti;
+    }
+    cons_bar();
+    total = wt[CW];
+    return wt[w] + inc - v;
+}
+
+// ------------------------------------------------------------ scan kernel --
+
+// emit == 0: scan every tile, keep records, count keys.
+// emit == 1: re-run the tiles listed in ovf_list and write their keys.
+template <int W, int BPS, int VAR>
+__global__ void __launch_bounds__(NTHREADS, 1) k_scan(const MatchParams P, const int emit) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t tbl_bytes = (P.tbl_words * 4u + 127u) & ~127u;
+    uint32_t *stbl = reinterpret_cast<uint32_t *>(smem);
+    uint8_t *st_in = smem + tbl_bytes;
+    uint32_t *st_seg = reinterpret_cast<uint32_t *>(st_in + STAGES * STAGE_IN);
+    uint64_t *full = reinterpret_cast<uint64_t *>(st_seg + STAGES * SEGW);
+    uint64_t *empty = full + STAGES;
+    int32_t *st_tile = reinterpret_cast<int32_t *>(empty + STAGES);
+    uint64_t *wt = reinterpret_cast<uint64_t *>(st_tile + 2 * STAGES);
+
+    const uint32_t tid = threadIdx.x;
+    const uint32_t n_work = emit ? *(volatile uint32_t *)&P.hdr->ovf_count : P.n_tiles;
+    if (blockIdx.x >= n_work) return;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (tid >= NCONS) {
+        // ---------------- producer warp ----------------
+        if (tid == NCONS) {
+            uint32_t issued = 0;
+            bool timed_out = false;
+            for (uint32_t i = 0;; i++) {
+                const int s = i % STAGES;
+                if (i >= STAGES && !mbar_wait_bounded(&empty[s], ((i / STAGES) - 1) & 1)) {
+                    // the consumers stopped releasing stages; they give up on
+                    // their own bounded waits
+                    atomicOr(&P.hdr->status, ST_TIMEOUT);
+                    timed_out = true;
+                    break;
+                }
+                const uint32_t wi = blockIdx.x + i * gridDim.x;
+                if (wi >= n_work) {
+                    st_tile[s] = -1;
+                    mbar_arrive(&full[s]);
+                    break;
+                }
+                const uint32_t t = emit ? P.ovf_list[wi] : wi;
+                st_tile[s] = (int32_t)t;
+                const uint64_t start = (uint64_t)t * TILE;
+                const uint64_t avail = P.n - start;
+                const uint32_t bytes = avail < (uint64_t)(TILE + HALO) ? (uint32_t)avail : TILE + HALO;
+                const uint32_t nb = bytes & ~15u;
+                const uint32_t tx = nb + (P.n_seg > 1 ? SEGW * 4 : 0);
+                mbar_arrive_expect_tx(&full[s], tx);
+                if (nb) bulk_g2s(st_in + s * STAGE_IN, P.in + start, nb, &full[s]);
+                if (P.n_seg > 1)
+                    bulk_g2s(st_seg + s * SEGW, P.tile_bounds + (size_t)t * SEGW, SEGW * 4,
+                             &full[s]);
+                issued = i + 1;
+            }
+            // On the normal path every issued copy is waited for by the
+            // consumers before the CTA can exit.  After a timeout, wait
+            // (bounded) for the copies that may still be in flight.
+            if (timed_out)
+                for (uint32_t i = issued > STAGES ? issued - STAGES : 0; i < issued; i++)
+                    mbar_wait_bounded(&full[i % STAGES], (i / STAGES) & 1);
+        }
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    if (VAR == VAR_FILTER) {
+        const uint32_t rep = P.rep_log2;
+        for (uint32_t i = tid; i < P.tbl_words; i += NCONS) stbl[i] = __ldg(P.F + (i >> rep));
+    } else if (VAR == VAR_DSMEM) {
+        for (uint32_t i = tid; i < P.tbl_words; i += NCONS) stbl[i] = __ldg(P.D + i);
+    } else if (VAR == VAR_DENSE) {
+        for (uint32_t i = tid; i < P.tbl_words; i += NCONS) stbl[i] = __ldg(P.T.stt + i);
+    }
+    cons_bar();
+
+    const uint32_t lane = tid & 31;
+    for (uint32_t i = 0;; i++) {
+        const int s = i % STAGES;
+        const bool ok = cons_bar_and(mbar_wait_bounded(&full[s], (i / STAGES) & 1));
+        if (!ok) {
+            if (tid == 0) atomicOr(&P.hdr->status, ST_TIMEOUT);
+            break;
+        }
+        const int32_t t = st_tile[s];
+        if (t < 0) break;
+        const uint64_t tile_start = (uint64_t)t * TILE;
+        const uint64_t remain = P.n - tile_start;
+        const uint32_t rem = remain < 0xFFFFFFF0ull ? (uint32_t)remain : 0xFFFFFFF0u;
+        const uint32_t valid = rem < (uint32_t)TILE ? rem : (uint32_t)TILE;
+        const uint32_t staged = (rem < (uint32_t)(TILE + HALO) ? rem : (uint32_t)(TILE + HALO)) & ~15u;
+        const uint8_t *sin = st_in + s * STAGE_IN;
+        const uint32_t *segs = st_seg + s * SEGW;
+        const uint8_t *g = P.in + tile_start;
+
+        uint32_t fr[BPT];
+        if (VAR == VAR_DENSE)
+            thread_positions_dense(P, sin, staged, valid, rem, segs, tile_start, g, stbl, tid, fr);
+        else
+            thread_positions<W, BPS, VAR>(P, sin, staged, valid, rem, segs, tile_start, g, stbl,
+                                          tid, fr);
+        // the stage is no longer read: hand it back to the producer
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+
+        uint32_t nm = 0;
+        uint64_t nk = 0;
+#pragma unroll
+        for (int j = 0; j < BPT; j++) {
+            if (fr[j]) {
+                nm++;
+                nk += fin_len(P.T.pool, fr[j]);
+            }
+        }
+        uint64_t total;
+        const uint64_t excl = cons_scan((nk << 16) | nm, wt, total, tid);
+        const uint32_t m_t = (uint32_t)(total & 0xFFFFu);
+        const uint64_t k_t = total >> 16;
+        const uint32_t p0 = tid * BPT;
+        if (!emit) {
+            if (m_t <= (uint32_t)REC_CAP) {
+                uint64_t *rr = P.recs + (size_t)t * REC_CAP + (excl & 0xFFFFu);
+#pragma unroll
+                for (int j = 0; j < BPT; j++)
+                    if (fr[j]) *rr++ = ((uint64_t)(p0 + j) << 32) | fr[j];
+            }
+            if (tid == 0) {
+                P.tile_m[t] = m_t;
+                P.tile_k[t] = k_t;
+                if (m_t > (uint32_t)REC_CAP) P.ovf_list[atomicAdd(&P.hdr->ovf_count, 1u)] = t;
+            }
+        } else if (nm) {
+            uint64_t o = P.key_off[t] + (excl >> 16);
+#pragma unroll 1
+            for (int j = 0; j < BPT; j++) {
+                const uint32_t f = fr[j];
+                if (!f) continue;
+                const uint32_t L = fin_len(P.T.pool, f);
+                const uint32_t *ids = fin_ids(P.T.pool, f);
+                const uint64_t pk = (tile_start + p0 + j) << 24;
+                for (uint32_t e = 0; e < L; e++, o++)
+                    if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
+            }
+        }
+    }
+}
+
+}  // namespace pfac

@@ -1,0 +1,510 @@
+// Match entry points: kernel selection, workspace layout, the ordering
+// kernels, and the C ABI calls pfac_workspace_bytes / pfac_match_async /
+// pfac_match (Section 2.3 semantics; see include/pfac.h).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace pfac {
+
+void *scan_kernel_bps1(int);
+void *scan_kernel_bps2(int);
+void *scan_kernel_bps3(int);
+void *scan_kernel_bps4(int);
+void *scan_kernel_bps5(int);
+void *scan_kernel_bps6(int);
+void *scan_kernel_bps7(int);
+void *scan_kernel_bps8(int);
+void *scan_kernel_dense();
+
+constexpr int CHUNK = 4096;      // tiles per chunk of the key-count scan
+constexpr int RT = 1024;         // threads of the scan/offset kernels
+
+// ------------------------------------------------ segment bounds per tile --
+
+// Validates the offsets and lists, per tile, the segment ends that the
+// tile's positions can need: every o_s > tile start up to and including the
+// first o_s >= tile end (at most SEG_MAXB, else SEG_OVF).
+__global__ void k_bounds(const MatchParams P) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t *seg = P.seg;
+    for (uint64_t s = gt; s < P.n_seg; s += stride)
+        if (__ldg(seg + s + 1) < __ldg(seg + s)) atomicOr(&P.hdr->status, ST_BADSEG);
+    if (gt == 0 && (__ldg(seg) != 0 || __ldg(seg + P.n_seg) != P.n))
+        atomicOr(&P.hdr->status, ST_BADSEG);
+    for (uint64_t t = gt; t < P.n_tiles; t += stride) {
+        const uint64_t start = t * TILE, end = start + TILE;
+        uint32_t lo = 1, hi = P.n_seg;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(seg + mid) > start) hi = mid; else lo = mid + 1;
+        }
+        uint32_t *B = P.tile_bounds + t * SEGW;
+        uint32_t cnt = 0;
+        bool ovf = false;
+        for (uint32_t s = lo; s <= P.n_seg; s++) {
+            const uint64_t o = __ldg(seg + s);
+            if (cnt == SEG_MAXB) {
+                ovf = true;
+                break;
+            }
+            const uint64_t r = o > start ? o - start : 0;
+            B[1 + cnt++] = r < 0xFFFFFFF0ull ? (uint32_t)r : 0xFFFFFFF0u;
+            if (o >= end) break;
+        }
+        B[0] = ovf ? SEG_OVF : cnt;
+    }
+}
+
+// ------------------------------------------------ key-count scan ----------
+
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t *sh, uint64_t &total) {
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += nb;
+    }
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const uint64_t t = lane < nw ? sh[lane] : 0;
+        uint64_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t nb = __shfl_up_sync(0xFFFFFFFFu, ti, o);
+            if (lane >= (uint32_t)o) ti += nb;
+        }
+        if (lane < nw) sh[lane] = ti - t;
+        if (lane == nw - 1) sh[32] = ti;
+    }
+    __syncthreads();
+    total = sh[32];
+    const uint64_t r = sh[w] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int32_t status_code(int32_t st) {
+    if (st & ST_BADSEG) return PFAC_EINVAL;
+    if (st & ST_TIMEOUT) return PFAC_ETIMEOUT;
+    if (st & ST_DEVICE) return PFAC_EDEVICE;
+    return PFAC_OK;
+}
+
+// Chunk sums of the per-tile key counts; the last CTA scans the chunk sums,
+// writes the total match count and checks single-segment offsets.
+__global__ void __launch_bounds__(RT) k_reduce(const MatchParams P) {
+    __shared__ uint64_t sh[33];
+    __shared__ bool last;
+    const uint32_t c = blockIdx.x;
+    uint64_t sum = 0;
+    if (c < P.n_chunks) {
+        const uint64_t t0 = (uint64_t)c * CHUNK;
+        for (uint32_t i = threadIdx.x; i < CHUNK; i += RT) {
+            const uint64_t t = t0 + i;
+            if (t < P.n_tiles) sum += P.tile_k[t];
+        }
+    }
+    uint64_t total;
+    block_excl_scan(sum, sh, total);
+    if (threadIdx.x == 0) {
+        if (c < P.n_chunks) P.chunk[c] = total;
+        __threadfence();
+        last = atomicAdd(&P.hdr->done_reduce, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    uint64_t carry = 0;
+    for (uint32_t base = 0; base < P.n_chunks; base += RT) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t v = i < P.n_chunks ? __ldcg(P.chunk + i) : 0;
+        uint64_t tot;
+        const uint64_t ex = block_excl_scan(v, sh, tot);
+        if (i < P.n_chunks) P.chunk[P.n_chunks + i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        *P.d_count = carry;
+        if (P.n_seg <= 1) {
+            const bool ok = P.n_seg == 1 ? (P.seg[0] == 0 && P.seg[1] == P.n)
+                                         : (P.n == 0 && P.seg[0] == 0);
+            if (!ok) atomicOr(&P.hdr->status, ST_BADSEG);
+        }
+    }
+}
+
+// Per-tile output offsets: chunk offset plus the scan inside the chunk.
+__global__ void __launch_bounds__(RT) k_offsets(const MatchParams P) {
+    __shared__ uint64_t sh[33];
+    const uint32_t c = blockIdx.x;
+    const uint64_t t0 = (uint64_t)c * CHUNK;
+    constexpr int PER = CHUNK / RT;
+    uint64_t v[PER];
+    uint64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const uint64_t t = t0 + threadIdx.x * PER + i;
+        v[i] = t < P.n_tiles ? P.tile_k[t] : 0;
+        s += v[i];
+    }
+    uint64_t total;
+    uint64_t ex = block_excl_scan(s, sh, total) + __ldcg(P.chunk + P.n_chunks + c);
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const uint64_t t = t0 + threadIdx.x * PER + i;
+        if (t < P.n_tiles) P.key_off[t] = ex;
+        ex += v[i];
+    }
+}
+
+// Writes the keys of every tile whose records were kept (one warp per tile);
+// the last CTA publishes the call's status.
+__global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
+    __shared__ bool last;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t *pool = P.T.pool;
+    for (uint64_t t = gw; t < P.n_tiles; t += nwarps) {
+        const uint32_t m = P.tile_m[t];
+        if (m == 0 || m > (uint32_t)REC_CAP) continue;
+        uint64_t off = P.key_off[t];
+        const uint64_t *rr = P.recs + t * REC_CAP;
+        const uint64_t tile_start = t * TILE;
+        for (uint32_t i0 = 0; i0 < m; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            uint64_t r = 0;
+            uint32_t L = 0;
+            if (i < m) {
+                r = rr[i];
+                L = fin_len(pool, (uint32_t)r);
+            }
+            uint32_t inc = L;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= (uint32_t)o) inc += nb;
+            }
+            const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            if (L) {
+                const uint64_t pk = (tile_start + (r >> 32)) << PFAC_ID_BITS;
+                const uint32_t *ids = fin_ids(pool, (uint32_t)r);
+                uint64_t o = off + inc - L;
+                for (uint32_t e = 0; e < L; e++, o++)
+                    if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
+            }
+            off += tot;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&P.hdr->done_expand, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0 && P.d_status) {
+        __threadfence();
+        *P.d_status = status_code(*(volatile int32_t *)&P.hdr->status);
+    }
+}
+
+// ------------------------------------------------ host side ---------------
+
+struct Plan {
+    int var;
+    uint32_t k;
+    uint32_t tbl_words;
+    uint32_t rep_log2;
+    uint32_t dense_rows;
+    void *kernel;
+    size_t smem;
+};
+
+struct WsLayout {
+    uint64_t hdr, tile_m, tile_k, key_off, chunk, ovf, recs, bounds, total;
+    uint32_t n_tiles, n_chunks;
+};
+
+static inline uint64_t al256(uint64_t x) { return (x + 255) & ~255ull; }
+
+static WsLayout ws_layout(uint64_t n_bytes, uint32_t n_seg) {
+    WsLayout L{};
+    const uint64_t nt = (n_bytes + TILE - 1) / TILE;
+    L.n_tiles = (uint32_t)nt;
+    L.n_chunks = (uint32_t)((nt + CHUNK - 1) / CHUNK);
+    uint64_t o = 0;
+    auto put = [&](uint64_t sz) {
+        const uint64_t at = o;
+        o = al256(o + sz);
+        return at;
+    };
+    L.hdr = put(sizeof(WsHeader));
+    L.tile_m = put(nt * 4);
+    L.tile_k = put(nt * 8);
+    L.key_off = put(nt * 8);
+    L.chunk = put((uint64_t)L.n_chunks * 16);
+    L.ovf = put(nt * 4);
+    L.recs = put(nt * REC_CAP * 8);
+    L.bounds = put(n_seg > 1 ? nt * SEGW * 4 : 0);
+    L.total = o;
+    return L;
+}
+
+static void *scan_kernel_for(uint32_t bps, int var) {
+    switch (bps) {
+        case 1: return scan_kernel_bps1(var);
+        case 2: return scan_kernel_bps2(var);
+        case 3: return scan_kernel_bps3(var);
+        case 4: return scan_kernel_bps4(var);
+        case 5: return scan_kernel_bps5(var);
+        case 6: return scan_kernel_bps6(var);
+        case 7: return scan_kernel_bps7(var);
+        case 8: return scan_kernel_bps8(var);
+        default: return nullptr;
+    }
+}
+
+static size_t scan_smem(uint32_t tbl_words) {
+    const size_t tbl = ((size_t)tbl_words * 4 + 127) & ~(size_t)127;
+    return tbl + STAGES * STAGE_IN + STAGES * SEGW * 4 + 2 * STAGES * 8 + 2 * STAGES * 4 +
+           (CW + 1) * 8;
+}
+
+static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl) {
+    const DevTable &T = t->dev;
+    memset(pl, 0, sizeof(*pl));
+    if (T.layout == PFAC_LAYOUT_DENSE) {
+        pl->var = VAR_DENSE;
+        uint32_t rows = (uint32_t)(TABLE_SMEM_MAX / (4ull * T.sigma));
+        if (rows > T.n_nodes) rows = T.n_nodes;
+        pl->dense_rows = rows;
+        pl->tbl_words = rows * T.sigma;
+        pl->kernel = scan_kernel_dense();
+    } else {
+        uint32_t k = opts && opts->prefix_depth ? opts->prefix_depth
+                                                 : (t->tuned_k ? t->tuned_k : T.kdef);
+        if (k < 1 || k > t->kmax)
+            return set_error(PFAC_EINVAL, "pfac_match: prefix_depth %u not held by the table", k);
+        const uint64_t ent = 1ull << (k * T.bps);
+        int var = opts && opts->variant ? (int)opts->variant
+                                        : (t->tuned_variant ? (int)t->tuned_variant : 0);
+        if (var == 0) var = ent <= 65536 ? VAR_FILTER : (ent * 4 <= TABLE_SMEM_MAX ? VAR_DSMEM : VAR_DGLOBAL);
+        pl->var = var;
+        pl->k = k;
+        if (var == VAR_FILTER) {
+            const uint64_t fw = ent >= 32 ? ent / 32 : 1;
+            uint32_t rep = 0;
+            while (rep < 5 && (fw << (rep + 1)) * 4 <= TABLE_SMEM_MAX) rep++;
+            if (fw * 4 > TABLE_SMEM_MAX)
+                return set_error(PFAC_EINVAL, "pfac_match: prefix bitmap of depth %u too large", k);
+            pl->rep_log2 = rep;
+            pl->tbl_words = (uint32_t)(fw << rep);
+        } else if (var == VAR_DSMEM) {
+            if (ent * 4 > TABLE_SMEM_MAX)
+                return set_error(PFAC_EINVAL, "pfac_match: prefix table of depth %u too large", k);
+            pl->tbl_words = (uint32_t)ent;
+        } else if (var == VAR_DGLOBAL) {
+            pl->tbl_words = 0;
+        } else {
+            return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
+        }
+        pl->kernel = scan_kernel_for(T.bps, var);
+    }
+    if (!pl->kernel) return set_error(PFAC_EINVAL, "pfac_match: no kernel for this table");
+    pl->smem = scan_smem(pl->tbl_words);
+    return PFAC_OK;
+}
+
+static std::mutex g_attr_mu;
+
+static int prepare_kernel(void *fn, size_t smem) {
+    // raise the dynamic shared-memory limit once per kernel and size
+    static void *done_fn[64];
+    static size_t done_sz[64];
+    static int n_done = 0;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    for (int i = 0; i < n_done; i++)
+        if (done_fn[i] == fn && done_sz[i] >= smem) return PFAC_OK;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return set_error(PFAC_ECUDA, "pfac_match: smem attribute: %s", cudaGetErrorString(e));
+    if (n_done < 64) {
+        done_fn[n_done] = fn;
+        done_sz[n_done] = smem;
+        n_done++;
+    }
+    return PFAC_OK;
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace pfac
+
+using namespace pfac;
+
+extern "C" int pfac_workspace_bytes(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments,
+                                    const pfac_match_opts *opts, uint64_t *bytes) {
+    (void)opts;
+    if (!t || !bytes) return set_error(PFAC_EINVAL, "pfac_workspace_bytes: NULL argument");
+    *bytes = ws_layout(n_bytes, n_segments).total;
+    return PFAC_OK;
+}
+
+extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
+                                const uint64_t *d_seg_offsets, uint32_t n_segments,
+                                uint64_t *d_out_keys, uint64_t out_capacity, uint64_t *d_count,
+                                int32_t *d_status, void *d_workspace, uint64_t workspace_bytes,
+                                const pfac_match_opts *opts, void *cuda_stream) {
+    if (!t || !d_count || !d_seg_offsets || !d_workspace)
+        return set_error(PFAC_EINVAL, "pfac_match: NULL argument");
+    if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_match: table was built host-only");
+    if (n_bytes && !d_input) return set_error(PFAC_EINVAL, "pfac_match: NULL input");
+    if (((uintptr_t)d_input & 15) != 0)
+        return set_error(PFAC_EINVAL, "pfac_match: input must be 16-byte aligned");
+    if (((uintptr_t)d_workspace & 255) != 0)
+        return set_error(PFAC_EINVAL, "pfac_match: workspace must be 256-byte aligned");
+    if (n_bytes >> (64 - PFAC_ID_BITS))
+        return set_error(PFAC_EINVAL, "pfac_match: input longer than 2^%d bytes", 64 - PFAC_ID_BITS);
+    if (n_bytes && n_segments == 0)
+        return set_error(PFAC_EINVAL, "pfac_match: a non-empty input needs a segment");
+    if (out_capacity && !d_out_keys) return set_error(PFAC_EINVAL, "pfac_match: NULL output");
+    const WsLayout L = ws_layout(n_bytes, n_segments);
+    if (workspace_bytes < L.total)
+        return set_error(PFAC_EINVAL, "pfac_match: workspace of %llu bytes, %llu needed",
+                         (unsigned long long)workspace_bytes, (unsigned long long)L.total);
+    Plan pl;
+    int rc = make_plan(t, opts, &pl);
+    if (rc) return rc;
+    rc = prepare_kernel(pl.kernel, pl.smem);
+    if (rc) return rc;
+
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint8_t *W = (uint8_t *)d_workspace;
+    MatchParams P;
+    memset(&P, 0, sizeof(P));
+    P.T = t->dev;
+    P.in = d_input;
+    P.n = n_bytes;
+    P.seg = d_seg_offsets;
+    P.n_seg = n_segments;
+    P.n_tiles = L.n_tiles;
+    P.out = d_out_keys;
+    P.cap = out_capacity;
+    P.d_count = d_count;
+    P.d_status = d_status;
+    P.hdr = (WsHeader *)(W + L.hdr);
+    P.tile_m = (uint32_t *)(W + L.tile_m);
+    P.tile_k = (uint64_t *)(W + L.tile_k);
+    P.key_off = (uint64_t *)(W + L.key_off);
+    P.chunk = (uint64_t *)(W + L.chunk);
+    P.n_chunks = L.n_chunks;
+    P.ovf_list = (uint32_t *)(W + L.ovf);
+    P.recs = (uint64_t *)(W + L.recs);
+    P.tile_bounds = (uint32_t *)(W + L.bounds);
+    P.k = pl.k;
+    P.D = pl.k ? t->dev.D[pl.k] : nullptr;
+    P.F = pl.k ? t->dev.F[pl.k] : nullptr;
+    P.tbl_words = pl.tbl_words;
+    P.rep_log2 = pl.rep_log2;
+    P.dense_rows = pl.dense_rows;
+
+    cudaError_t e = cudaMemsetAsync(P.hdr, 0, sizeof(WsHeader), st);
+    const int nsm = sm_count();
+    const uint32_t cps = opts && opts->ctas_per_sm ? opts->ctas_per_sm : 1;
+    if (e == cudaSuccess && n_segments > 1 && L.n_tiles) {
+        k_bounds<<<nsm * 2, 256, 0, st>>>(P);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && opts && opts->ev_scan_begin)
+        e = cudaEventRecord((cudaEvent_t)opts->ev_scan_begin, st);
+    if (e == cudaSuccess && L.n_tiles) {
+        int emit = 0;
+        void *args[] = {&P, &emit};
+        const uint32_t grid = (uint32_t)nsm * cps < L.n_tiles ? (uint32_t)nsm * cps : L.n_tiles;
+        e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(NTHREADS), args, pl.smem, st);
+    }
+    if (e == cudaSuccess && opts && opts->ev_scan_end)
+        e = cudaEventRecord((cudaEvent_t)opts->ev_scan_end, st);
+    if (e == cudaSuccess) {
+        k_reduce<<<L.n_chunks ? L.n_chunks : 1, RT, 0, st>>>(P);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && L.n_tiles) {
+        k_offsets<<<L.n_chunks, RT, 0, st>>>(P);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && L.n_tiles) {
+        int emit = 1;
+        void *args[] = {&P, &emit};
+        const uint32_t grid = (uint32_t)nsm * cps < L.n_tiles ? (uint32_t)nsm * cps : L.n_tiles;
+        e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(NTHREADS), args, pl.smem, st);
+    }
+    if (e == cudaSuccess) {
+        uint64_t warps = L.n_tiles ? L.n_tiles : 1;
+        uint64_t blocks = (warps + 7) / 8;
+        const uint64_t maxb = (uint64_t)nsm * 8;
+        if (blocks > maxb) blocks = maxb;
+        k_expand<<<(uint32_t)blocks, 256, 0, st>>>(P);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return set_error(PFAC_ECUDA, "pfac_match: launch failed: %s", cudaGetErrorString(e));
+    return PFAC_OK;
+}
+
+extern "C" int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
+                          const uint64_t *d_seg_offsets, uint32_t n_segments, uint64_t *d_out_keys,
+                          uint64_t out_capacity, uint64_t *n_out, const pfac_match_opts *opts,
+                          void *cuda_stream) {
+    clear_error();
+    if (!t || !n_out) return set_error(PFAC_EINVAL, "pfac_match: NULL argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const WsLayout L = ws_layout(n_bytes, n_segments);
+    void *ws = nullptr, *small = nullptr;
+    cudaError_t e = cudaMallocAsync(&ws, L.total, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&small, 256, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ws) cudaFreeAsync(ws, st);
+        return set_error(e == cudaErrorMemoryAllocation ? PFAC_ENOMEM : PFAC_ECUDA,
+                         "pfac_match: workspace allocation: %s", cudaGetErrorString(e));
+    }
+    uint64_t *d_cnt = (uint64_t *)small;
+    int32_t *d_st = (int32_t *)((uint8_t *)small + 128);
+    int rc = pfac_match_async(t, d_input, n_bytes, d_seg_offsets, n_segments, d_out_keys,
+                              out_capacity, d_cnt, d_st, ws, L.total, opts, cuda_stream);
+    struct {
+        uint64_t cnt;
+        int32_t st;
+    } h{0, 0};
+    if (rc == PFAC_OK) {
+        e = cudaMemcpyAsync(&h.cnt, d_cnt, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h.st, d_st, 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = set_error(PFAC_ECUDA, "pfac_match: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(ws, st);
+    cudaFreeAsync(small, st);
+    if (rc) return rc;
+    *n_out = h.cnt;
+    if (h.st != PFAC_OK)
+        return set_error(h.st, "pfac_match: device reported %s", pfac_status_str(h.st));
+    if (h.cnt > out_capacity)
+        return set_error(PFAC_ENOSPC, "pfac_match: %llu matches, capacity %llu",
+                         (unsigned long long)h.cnt, (unsigned long long)out_capacity);
+    return PFAC_OK;
+}

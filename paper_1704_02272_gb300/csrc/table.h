@@ -1,0 +1,69 @@
+// Device-side view of a matching table and the encodings shared by the host
+// builder (builder.cpp) and the kernels (match.cu).
+//
+// Compressed layout (Sections 3.1 and 3.2):
+//   * Trie nodes are numbered breadth-first over the alphabetically sorted
+//     patterns; siblings are contiguous and in symbol order (Section 3.1).
+//   * A node record holds a bitmap of W = ceil(sigma/32) words (bit c set when
+//     the node has a child on symbol c) and a base; the child on c is
+//     base + rank(c), rank(c) = number of bitmap bits below c (Eq. 1).
+//   * Leaf merge (Eq. 2): leaves have no children, so a node whose children
+//     are all leaves keeps no records for them; its base then indexes
+//     leaf_fin[], which holds each merged leaf's output list, and its meta word
+//     carries META_ALL_LEAF.  Leaves with an internal sibling keep a record
+//     with an empty bitmap.
+//   * Output: every state s carries fin(s), the sorted ids of all patterns
+//     that are prefixes of s's string (its final ancestors and itself).  A
+//     walk reports fin of the state where it stops, which is exactly the set
+//     of finals it passed (Section 2.3).
+//   * Prefix lookup: for k symbols, D_k[x] is the state after walking the k
+//     symbols packed in x (BPS bits each, first symbol lowest) or the output
+//     of a walk that stopped earlier; F_k is the bitmap of D_k entries that
+//     are not "stopped with nothing to report".
+//
+// Dense layout (uncompressed PFAC): stt[s * sigma + c] = child or 0 (the root
+// is never a child), dfin[s] = fin(s).
+#pragma once
+#include <stdint.h>
+
+namespace pfac {
+
+constexpr int KMAX = 16;                 // largest prefix depth held
+constexpr uint32_t META_ALL_LEAF = 0x80000000u;
+constexpr uint32_t META_BASE_MASK = 0x7FFFFFFFu;
+constexpr uint32_t D_CONT = 0x80000000u;  // D entry: continue at record
+constexpr uint32_t D_VAL_MASK = 0x7FFFFFFFu;
+// fin encoding: 0 = empty; else (off << FIN_LEN_BITS) | len, len < FIN_LEN_ESC
+// with ids at pool[off .. off+len); len == FIN_LEN_ESC means the length is
+// pool[off] and the ids follow it.
+constexpr int FIN_LEN_BITS = 6;
+constexpr uint32_t FIN_LEN_ESC = (1u << FIN_LEN_BITS) - 1;
+constexpr uint32_t FIN_MAX_OFF = (1u << (31 - FIN_LEN_BITS)) - 1;
+
+// 32-bit words per record for W bitmap words
+//   W == 1: {bm, meta}                          (fin in a separate array)
+//   W == 2: {bm0, bm1, meta, fin}
+//   W == 8: {bm0..bm7, meta, fin, cum0..3, cum4..7} (cum: popcount of the
+//           words before each word, one byte per word)
+__host__ __device__ constexpr int rec_words(int W) { return W == 1 ? 2 : (W == 2 ? 4 : 12); }
+
+struct DevTable {
+    uint32_t sigma;
+    uint32_t W;           // 1, 2 or 8 (bitmap words per record)
+    uint32_t bps;         // bits per symbol in prefix indices
+    uint32_t kdef;        // default prefix depth
+    uint32_t layout;      // pfac_layout
+    uint32_t max_len;
+    uint32_t n_rec;
+    uint32_t n_nodes;     // dense layout: states
+    const uint32_t *rec;
+    const uint32_t *fin;      // W == 1 only
+    const uint32_t *leaf_fin;
+    const uint32_t *pool;
+    const uint32_t *D[KMAX + 1];
+    const uint32_t *F[KMAX + 1];
+    const uint32_t *stt;      // dense layout
+    const uint32_t *dfin;
+};
+
+}  // namespace pfac

@@ -1,0 +1,121 @@
+"""CPU checks of the library boundary: the shared library loads without a
+GPU, exports every function include/pfac.h declares, and its host-side trie
+builder (run host-only, no device memory) reports the statistics the oracle's
+storage model gives: trie size, leaves, the leaf merge of Eq. 2 and the
+Section 3.1 byte counts."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import trie
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pfac.h")
+
+pfac = pytest.importorskip("paper_1704_02272_gb300")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(pfac_\w+)\s*\(", src, re.M)))
+
+
+def test_header_symbols_exported():
+    names = declared_functions()
+    assert "pfac_build" in names and "pfac_match" in names and len(names) >= 9
+    lib = ctypes.CDLL(pfac.binding.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/pfac.h but not exported"
+
+
+def test_status_strings():
+    lib = pfac.binding.LIB
+    for code in range(0, -9, -1):
+        s = lib.pfac_status_str(code).decode()
+        assert s and s != "unknown status"
+    assert pfac.version() >= 100
+
+
+def host_table(patterns, sigma, **kw):
+    return pfac.Table(patterns, sigma, host_only=True, **kw)
+
+
+@pytest.mark.parametrize("seed,sigma,n,lo,hi", [(1, 4, 500, 1, 12), (2, 256, 3000, 2, 20),
+                                                (3, 20, 800, 1, 8), (4, 64, 900, 1, 9),
+                                                (5, 2, 60, 1, 10), (6, 3, 200, 1, 7)])
+def test_table_statistics_match_storage_model(seed, sigma, n, lo, hi):
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, 0)
+    with host_table(w.patterns, sigma) as t:
+        info = t.info()
+    q = trie.prefix_set_count(w.patterns)
+    leaves = trie.leaf_count(w.patterns)
+    pt = trie.build_paper_trie(w.patterns, sigma)
+    assert info["trie_nodes"] == q == pt.n_nodes
+    assert info["trie_leaves"] == leaves == pt.n_leaves
+    assert info["n_patterns"] == len(w.patterns)
+    assert info["max_len"] == max(len(p) for p in w.patterns)
+    # every merged leaf removes one record; the root always keeps one
+    assert info["records"] + info["merged_leaves"] == q
+    assert info["merged_leaves"] <= leaves
+    assert info["paper_bytes"] == trie.paper_layout_bytes(q, sigma)
+    assert info["dense_bytes"] == trie.dense_stt_bytes(q, sigma)
+    assert info["output_lists"] == len(w.patterns)
+
+
+def test_eq2_leaf_merge_on_prefix_free_sets():
+    rs = np.random.RandomState(3)
+    # equal-length patterns: prefix free, and every parent of a leaf has only
+    # leaf children, so every leaf merges: records = Q - |P| (Eq. 2 counts the
+    # one shared final node on top: Q - (|P| - 1))
+    pats = workloads.dedup([rs.randint(0, 4, 7).astype(np.uint8).tobytes() for _ in range(2000)])
+    with host_table(pats, 4) as t:
+        info = t.info()
+    q = trie.prefix_set_count(pats)
+    assert info["merged_leaves"] == len(pats)
+    assert info["records"] + 1 == trie.leaf_merged_count(q, len(pats))
+
+
+def test_fig1_example_counts():
+    # Section 3.1 worked example: patterns AB, AD and a third first symbol
+    with host_table([b"AB", b"AD", b"E"], 256) as t:
+        info = t.info()
+    assert info["trie_nodes"] == 5 and info["trie_leaves"] == 3
+    # 'AB' and 'AD' are the only children of 'A': both merge; 'E' has an
+    # internal sibling ('A') and keeps its record
+    assert info["merged_leaves"] == 2 and info["records"] == 3
+
+
+@pytest.mark.parametrize("pats,sigma,status", [
+    ([b"ab", b"ab"], 256, -2),
+    ([b"ab", b""], 256, -1),
+    ([b"\x05"], 4, -3),
+    ([b"a"], 0, -1),
+    ([b"a"], 257, -1),
+])
+def test_build_errors(pats, sigma, status):
+    with pytest.raises(pfac.PfacError) as ei:
+        host_table(pats, sigma)
+    assert ei.value.status == status
+
+
+def test_empty_pattern_set_builds():
+    with host_table([], 256) as t:
+        info = t.info()
+    assert info["trie_nodes"] == 1 and info["records"] == 1 and info["n_patterns"] == 0
+
+
+def test_host_only_table_cannot_match():
+    import torch
+    with host_table([b"ab"], 256) as t:
+        with pytest.raises(pfac.PfacError) as ei:
+            z = torch.zeros(16, dtype=torch.uint8)
+            s = torch.tensor([0, 16], dtype=torch.int64)
+            pfac.match_async(t, z, s, torch.zeros(4, dtype=torch.int64),
+                             torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int32),
+                             torch.zeros(1 << 16, dtype=torch.uint8), stream=0)
+        assert ei.value.status == -1

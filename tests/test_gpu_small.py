@@ -1,0 +1,187 @@
+"""GPU parity on small and edge-case inputs: the CUDA path through the C ABI
+against the CPU oracle, element by element (sorted packed keys), for every
+kernel variant, several prefix depths and both table layouts."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from tests.gpu_util import assert_same, keys_np, oracle_keys, to_device
+
+pytestmark = pytest.mark.gpu
+
+pfac = pytest.importorskip("paper_1704_02272_gb300")
+
+
+def run(w, **kw):
+    layout = kw.pop("layout", pfac.LAYOUT_COMPRESSED)
+    prefix = kw.pop("build_prefix", 0)
+    text, seg = to_device(w)
+    with pfac.Table(w.patterns, w.sigma, layout=layout, prefix_depth=prefix) as t:
+        keys = pfac.match(t, text, seg, **kw)
+        torch.cuda.synchronize()
+        return keys_np(keys)
+
+
+def check_all_variants(w, what, depths=None):
+    ref = oracle_keys(w)
+    assert_same(run(w), ref, f"{what} default")
+    assert_same(run(w, layout=pfac.LAYOUT_DENSE), ref, f"{what} dense")
+    for var in (pfac.VARIANT_FILTER, pfac.VARIANT_DSMEM, pfac.VARIANT_DGLOBAL):
+        for k in depths or [0]:
+            try:
+                got = run(w, variant=var, prefix_depth=k or 0)
+            except pfac.PfacError as e:  # a table too large for shared memory
+                assert e.status == -1 and var != pfac.VARIANT_DGLOBAL, str(e)
+                continue
+            assert_same(got, ref, f"{what} variant {var} depth {k}")
+    return ref
+
+
+CASES = [
+    # seed, sigma, n_patterns, lo, hi, n_bytes, n_segments, n_plants, text_sigma
+    (101, 4, 60, 1, 9, 100_000, 1, 300, None),
+    (102, 4, 400, 2, 14, 200_000, 300, 500, None),
+    (103, 256, 2000, 2, 12, 1 << 20, 1, 2000, None),
+    (104, 20, 500, 1, 6, 300_000, 50, 400, None),
+    (105, 64, 800, 1, 7, 300_000, 7, 400, None),
+    (106, 3, 100, 1, 8, 150_000, 20, 200, None),
+    (107, 2, 40, 1, 10, 150_000, 3, 100, None),
+    (108, 4, 200, 1, 8, 120_000, 40, 300, 7),      # out-of-alphabet bytes in the text
+    (109, 100, 700, 1, 5, 250_000, 11, 300, None),
+    (110, 256, 500, 1, 40, 100_003, 1, 300, None),  # ragged tail
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"s{c[0]}-sig{c[1]}" for c in CASES])
+def test_random_cases(case):
+    seed, sigma, n, lo, hi, N, S, plants, ts = case
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, N, n_segments=S, n_plants=plants,
+                            text_sigma=ts)
+    ref = check_all_variants(w, f"case {seed}", depths=[1, None])
+    assert ref.size > 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_prefix_heavy(seed):
+    w = workloads.prefix_heavy_case(seed, 3 + seed, 200_000, n_segments=1 + 30 * (seed % 2))
+    check_all_variants(w, f"prefix-heavy {seed}")
+
+
+@pytest.mark.parametrize("N", [0, 1, 15, 16, 17, 8191, 8192, 8193, 8208, 8209, 16400])
+def test_sizes_around_tiles(N):
+    w = workloads.tiny_case(200 + N, 4, 80, 1, 6, N, n_plants=min(N // 10, 50))
+    check_all_variants(w, f"N={N}")
+
+
+def test_sigma_one():
+    pats = [bytes(k) for k in (1, 2, 5, 31, 40)]
+    text = np.zeros(70_000, np.uint8)
+    text[12345] = 0  # all zeros: every pattern matches nearly everywhere
+    w = workloads.Workload("zeros", 1, pats, text, workloads.single_segment(text.size))
+    ref = check_all_variants(w, "sigma 1")
+    assert ref.size == sum(text.size - len(p) + 1 for p in pats)
+
+
+def test_many_tiny_segments():
+    # more segment ends per tile than the per-tile list holds, empty segments
+    rs = np.random.RandomState(5)
+    N = 60_000
+    lens = rs.randint(0, 4, size=25_000)
+    lens = lens[np.cumsum(lens) <= N]
+    cuts = np.concatenate([[0], np.cumsum(lens), [N]]).astype(np.uint64)
+    pats = workloads.uniform_patterns(rs, 50, 4, 1, 4)
+    text = workloads.uniform_symbols(rs, N, 4)
+    w = workloads.Workload("tiny-segs", 4, pats, text, cuts)
+    check_all_variants(w, "tiny segments")
+
+
+def test_long_patterns_across_tiles():
+    # patterns far longer than the staged halo, planted across tile borders
+    rs = np.random.RandomState(9)
+    pats = workloads.uniform_patterns(rs, 40, 256, 100, 9000)
+    N = 200_000
+    text = workloads.uniform_symbols(rs, N, 256)
+    for i, b in enumerate(range(8192, N - 9000, 8192)):
+        p = pats[i % len(pats)]
+        off = b - len(p) // 2
+        text[off:off + len(p)] = np.frombuffer(p, np.uint8)
+    w = workloads.Workload("long", 256, pats, text, workloads.single_segment(N))
+    ref = check_all_variants(w, "long patterns")
+    assert ref.size >= 15
+
+
+def test_capacity_two_call():
+    w = workloads.tiny_case(301, 4, 300, 2, 6, 200_000)
+    ref = oracle_keys(w)
+    text, seg = to_device(w)
+    with pfac.Table(w.patterns, 4) as t:
+        out = torch.empty(max(ref.size // 3, 1), dtype=torch.int64, device=text.device)
+        with pytest.raises(pfac.PfacError) as ei:
+            pfac.match_into(t, text, seg, out)
+        assert ei.value.status == -5 and ei.value.count == ref.size
+        assert_same(keys_np(out), ref[:out.numel()], "truncated prefix")
+        out2 = torch.empty(ref.size, dtype=torch.int64, device=text.device)
+        assert pfac.match_into(t, text, seg, out2) == ref.size
+        assert_same(keys_np(out2), ref, "second call")
+
+
+def test_bad_offsets_reported():
+    w = workloads.tiny_case(302, 4, 30, 2, 5, 10_000, n_segments=5)
+    text, seg = to_device(w)
+    with pfac.Table(w.patterns, 4) as t:
+        o2, o3 = int(seg[2].item()), int(seg[3].item())
+        bad = seg.clone()
+        bad[2] = o3 + 1  # o_2 > o_3: not non-decreasing
+        bad[3] = o2
+        with pytest.raises(pfac.PfacError) as ei:
+            pfac.match_into(t, text, bad, torch.empty(10_000, dtype=torch.int64,
+                                                      device=text.device))
+        assert ei.value.status == -1
+        bad2 = seg.clone()
+        bad2[-1] -= 1
+        with pytest.raises(pfac.PfacError) as ei:
+            pfac.match_into(t, text, bad2, torch.empty(10_000, dtype=torch.int64,
+                                                       device=text.device))
+        assert ei.value.status == -1
+
+
+def test_unaligned_input_rejected():
+    w = workloads.tiny_case(303, 4, 30, 2, 5, 10_000)
+    text, seg = to_device(w)
+    big = torch.zeros(text.numel() + 16, dtype=torch.uint8, device=text.device)
+    with pfac.Table(w.patterns, 4) as t:
+        with pytest.raises(pfac.PfacError) as ei:
+            pfac.match_into(t, big[1:1 + text.numel()], seg,
+                            torch.empty(10, dtype=torch.int64, device=text.device))
+        assert ei.value.status == -1
+
+
+def test_async_and_graph_replay():
+    w = workloads.tiny_case(304, 256, 1500, 2, 10, 3 << 20, n_segments=200, n_plants=3000)
+    ref = oracle_keys(w)
+    text, seg = to_device(w)
+    dev = text.device
+    with pfac.Table(w.patterns, 256) as t:
+        ws = torch.empty(pfac.workspace_bytes(t, text.numel(), seg.numel() - 1),
+                         dtype=torch.uint8, device=dev)
+        out = torch.empty(ref.size + 10, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            pfac.match_async(t, text, seg, out, cnt, st, ws)
+        s.synchronize()
+        assert int(cnt.item()) == ref.size and int(st.item()) == 0
+        assert_same(keys_np(out[:ref.size]), ref, "async")
+        g = torch.cuda.CUDAGraph()
+        out.zero_()
+        with torch.cuda.graph(g, stream=s):
+            pfac.match_async(t, text, seg, out, cnt, st, ws, stream=s)
+        for _ in range(3):
+            out.zero_()
+            cnt.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert int(cnt.item()) == ref.size and int(st.item()) == 0
+            assert_same(keys_np(out[:ref.size]), ref, "graph replay")
