@@ -177,6 +177,43 @@ int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
                uint64_t out_capacity, uint64_t *n_out, const pfac_match_opts *opts,
                void *cuda_stream);
 
+/*
+ * pfac_match_noalloc - pfac_match_async for callers that cannot allocate
+ * device memory when they match.  (The paper has no counterpart; this is a
+ * deployment aid of this library.)
+ *
+ * Who needs it: code that runs where an allocation is not allowed or not
+ * safe, e.g. inside a custom device-memory allocator's own callbacks, in a
+ * latency-critical packet loop that must never block on the allocator or
+ * fail with out-of-memory halfway through a stream, or in a process whose
+ * device-memory budget is fixed at start-up.  This call allocates nothing:
+ * no cudaMalloc, no cudaFree, no allocating library routine.  Its scratch is
+ * a device array of PFAC_NOALLOC_SCRATCH_BYTES compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * Arguments are those of pfac_match_async without the workspace.  The
+ * caller still provides the input, the offsets, the output keys, d_count and
+ * (optionally) d_status.
+ *
+ * Limits and rules:
+ *   - the scratch an input needs grows with its size (about 0.53 bytes per
+ *     input byte); inputs that need more than PFAC_NOALLOC_SCRATCH_BYTES
+ *     (roughly 60 MiB of input) are rejected with PFAC_EINVAL and a message
+ *     naming both sizes, before any device work;
+ *   - the first call on a device looks up that device's copy of the array
+ *     (cudaGetSymbolAddress, with the device current); make that first call
+ *     before any stream capture;
+ *   - all calls on a device share the one array, and it keeps the previous
+ *     call's contents (each call clears what must start at zero), so calls
+ *     whose device work overlaps in time race and give wrong results: issue
+ *     them on one stream or otherwise order them.
+ */
+#define PFAC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int pfac_match_noalloc(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
+                       const uint64_t *d_seg_offsets, uint32_t n_segments, uint64_t *d_out_keys,
+                       uint64_t out_capacity, uint64_t *d_count, int32_t *d_status,
+                       const pfac_match_opts *opts, void *cuda_stream);
+
 /* pfac_table_info - statistics of a built table (host call, no device work). */
 int pfac_table_info(const pfac_table *t, pfac_table_info_t *out);
 

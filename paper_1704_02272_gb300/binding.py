@@ -77,6 +77,9 @@ def _load():
     lib.pfac_match.restype = ctypes.c_int
     lib.pfac_match.argtypes = [vp, vp, u64, vp, u32, vp, u64, ctypes.POINTER(u64),
                                ctypes.POINTER(MatchOpts), vp]
+    lib.pfac_match_noalloc.restype = ctypes.c_int
+    lib.pfac_match_noalloc.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp,
+                                       ctypes.POINTER(MatchOpts), vp]
     lib.pfac_table_info.restype = ctypes.c_int
     lib.pfac_table_info.argtypes = [vp, ctypes.POINTER(TableInfo)]
     lib.pfac_table_free.restype = None
@@ -191,6 +194,17 @@ def match_async(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.
                                 _ptr(out), out.numel() if out is not None else 0, _ptr(count),
                                 _ptr(status), _ptr(workspace), workspace.numel(),
                                 ctypes.byref(o), ctypes.c_void_p(_stream(stream))))
+
+
+def match_noalloc(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,
+                  count: torch.Tensor, status: torch.Tensor, stream=None, **opt):
+    """pfac_match_noalloc: like match_async, but the library uses its built-in
+    scratch array instead of a workspace, so nothing is allocated."""
+    o = _opts(**opt)
+    n_seg = max(seg.numel() - 1, 0)
+    _check(LIB.pfac_match_noalloc(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg,
+                                  _ptr(out), out.numel() if out is not None else 0, _ptr(count),
+                                  _ptr(status), ctypes.byref(o), ctypes.c_void_p(_stream(stream))))
 
 
 def match_into(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,

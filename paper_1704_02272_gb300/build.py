@@ -30,7 +30,7 @@ def nvcc() -> str:
 
 
 def sources():
-    srcs = ["builder.cpp", "match.cu", "scan_dense.cu"] + [f"scan_bps{i}.cu" for i in range(1, 9)]
+    srcs = ["builder.cpp", "match.cu", "noalloc.cu", "scan_dense.cu"] + [f"scan_bps{i}.cu" for i in range(1, 9)]
     return [os.path.join(CSRC, s) for s in srcs]
 
 
