@@ -67,6 +67,17 @@ WORKLOAD_DESC = {
 }
 
 
+METRIC = ("scan Gbps (1xGB300) compressed vs uncompressed PFAC, bit-exact; table bytes; "
+          "p99 latency")
+
+
+def base_config(w, args):
+    return {"workload": WORKLOAD_DESC.get(args.workload, args.workload),
+            "n_bytes": w.n_bytes, "segments": len(w.seg_offsets) - 1,
+            "patterns": len(w.patterns), "alphabet": w.sigma,
+            "l2": "input larger than L2, no flush"}
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -171,11 +182,11 @@ def run_reference(args):
     sample = (f"start positions [0, {nb >> 20} MiB) of the workload per step, Aho-Corasick with "
               f"failure links in C on {threads} threads")
     print(json.dumps({
-        "impl": "reference", "metric": "scan Gbps", "value": round(v, 4), "unit": "Gbps",
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Gbps",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload)},
+        "config": base_config(w, args),
         "cpu_baseline": {"value": round(v, 4), "unit": "Gbps", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "Gbps", "h2d_bytes_per_step": 0,
@@ -211,7 +222,6 @@ def run_ours(args):
     n_match = keys.numel()
     cap = n_match + 1024
     out = torch.empty(cap, dtype=torch.int64, device=dev)
-    ws = torch.empty(pfac.workspace_bytes(table, N, S), dtype=torch.uint8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
 
@@ -225,9 +235,36 @@ def run_ours(args):
             e.record(stream)
     stream.synchronize()
 
+    user_opt = {}
+    if args.variant:
+        user_opt["variant"] = args.variant
+    if args.prefix_depth:
+        user_opt["prefix_depth"] = args.prefix_depth
+    if args.copies:
+        user_opt["bitmap_copies"] = args.copies
+    if args.autotune:
+        tune = pfac.autotune(table, text, seg)
+    ws = torch.empty(max(pfac.workspace_bytes(table, N, S, **user_opt),
+                         pfac.workspace_bytes(dense, N, S)), dtype=torch.uint8, device=dev)
+
     def step(i=None, tbl=table):
-        opt = {} if i is None else {"scan_events": (sc_b[i], sc_e[i])}
+        opt = dict(user_opt) if tbl is table else {}
+        if i is not None:
+            opt["scan_events"] = (sc_b[i], sc_e[i])
         pfac.match_async(tbl, text, seg, out, cnt, st, ws, stream=stream, **opt)
+
+    use_graph = args.graph or args.workload == "ids"
+    graph = None
+    if use_graph:
+        # the whole call (workspace clear, segment pass, scan, ordering kernels)
+        # captured once and replayed per step
+        for _ in range(2):
+            step()
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            step()
+        stream.synchronize()
 
     for _ in range(W):
         step()
@@ -241,11 +278,20 @@ def run_ours(args):
     t_wall0 = time.perf_counter()
     for i in range(K):
         ev_b[i].record(stream)
-        step(i)
+        if graph is not None:
+            with torch.cuda.stream(stream):
+                graph.replay()
+        else:
+            step(i)
         ev_e[i].record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
+    if graph is not None:
+        # scan-kernel time of the graph steps: one more eager pass with events
+        for i in range(K):
+            step(i)
+        stream.synchronize()
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
@@ -326,15 +372,14 @@ def run_ours(args):
                 "alg_bytes_per_launch": alg_bytes}
 
     line = {
-        "metric": "scan Gbps (1xGB300) compressed vs uncompressed PFAC, bit-exact; table bytes; "
-                  "p99 latency",
+        "metric": METRIC,
         "value": round(value, 3), "unit": "Gbps", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC.get(args.workload, args.workload),
-                   "n_bytes": N, "segments": S, "patterns": len(w.patterns),
-                   "alphabet": w.sigma, "l2": "input larger than L2, no flush",
-                   "variant": "default", "prefix_depth": info["prefix_depth"]},
+        "config": dict(base_config(w, args), prefix_depth=args.prefix_depth or info["prefix_depth"],
+                       variant=args.variant or "default", bitmap_copies=args.copies or "auto",
+                       autotuned=tune if args.autotune else None,
+                       cuda_graph=bool(graph is not None)),
         "p50_ms": round(statistics.median(step_ms), 4),
         "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
         "matches": n_match, "matched_position_frac": round(matched_frac, 6),
@@ -359,6 +404,80 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serving(args):
+    """Serving loop: Poisson arrivals of packet batches (1-4096 packets of
+    64-9000 bytes, 50,000 IDS-shaped patterns resident) at each offered load;
+    reports p50/p99 latency (completion minus scheduled arrival) and the
+    sustained throughput per load level, one JSON line per level."""
+    import threading
+    import torch
+    import paper_1704_02272_gb300 as pfac
+    torch.cuda.set_device(0)
+    pats = workloads.config5_patterns()
+    rs = np.random.RandomState(workloads.seed_for(5) + 1)
+    batches = [workloads.serving_batch(rs, pats) for _ in range(args.serve_batches)]
+    pinned = [(torch.from_numpy(t).pin_memory(), torch.from_numpy(s.view(np.int64)).pin_memory())
+              for t, s in batches]
+    mean_bytes = float(np.mean([t.size for t, _ in batches]))
+    table = pfac.Table(pats, 256)
+    t0, s0 = batches[0]
+    pfac.autotune(table, torch.from_numpy(t0).cuda(), torch.from_numpy(s0.view(np.int64)).cuda())
+    loads = [float(x) for x in args.loads.split(",")]
+    biggest = max(t.size for t, _ in batches)
+    out = []
+    with pfac.Server(table, n_slots=args.serve_slots, device_bytes=args.serve_pool << 20,
+                     max_request_bytes=biggest) as srv:
+        for _ in range(3):  # warm-up
+            rid = srv.submit(*pinned[0])
+            srv.wait(rid, 60)
+            srv.release(rid)
+        for load in loads:
+            rate = load * 1e9 / 8.0 / mean_bytes  # batches per second
+            n = int(min(max(args.serve_min, rate * args.serve_seconds), args.serve_max))
+            arr = workloads.poisson_arrivals(np.random.RandomState(int(load)), rate, n)
+            ids, sched, sizes = [], [], []
+            start = time.monotonic() + 0.05
+
+            def submitter():
+                for k in range(n):
+                    at = start + arr[k]
+                    dt = at - time.monotonic()
+                    if dt > 0:
+                        time.sleep(dt)
+                    t, s = pinned[k % len(pinned)]
+                    ids.append(srv.submit(t, s))
+                    sched.append(at)
+                    sizes.append(t.numel())
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            done = {}
+            while len(done) < n:
+                r = srv.poll()
+                if r is None:
+                    time.sleep(0.0002)
+                    continue
+                done[r["id"]] = r
+            th.join()
+            lat = []
+            for rid, at in zip(ids, sched):
+                r = done[rid]
+                assert r["status"] == 0
+                lat.append(r["t_done"] - at)
+                srv.release(rid)
+            t_end = max(done[i]["t_done"] for i in ids)
+            line = {"impl": "ours", "mode": "serving", "offered_gbps": load,
+                    "sustained_gbps": round(8.0 * sum(sizes) / (t_end - start) / 1e9, 3),
+                    "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                    "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                    "requests": n, "mean_request_bytes": int(mean_bytes),
+                    "slots": args.serve_slots}
+            out.append(line)
+            print(json.dumps(line), flush=True)
+    table.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,10 +489,25 @@ def main():
                     help="dram bytes per scan launch from an ncu capture of this build")
     ap.add_argument("--ref-sample-mib", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=0, help="1: entries via L2, 2: entries in smem")
+    ap.add_argument("--prefix-depth", type=int, default=0)
+    ap.add_argument("--copies", type=int, default=0, help="prefix-bitmap copies in smem")
+    ap.add_argument("--autotune", action="store_true", help="pfac_autotune on the input first")
+    ap.add_argument("--graph", action="store_true",
+                    help="time CUDA-graph replays of the match call (default for packets)")
+    ap.add_argument("--loads", default="10,25,50,100,200,300,400")
+    ap.add_argument("--serve-batches", type=int, default=48)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-pool", type=int, default=4096, help="MiB")
+    ap.add_argument("--serve-seconds", type=float, default=1.5)
+    ap.add_argument("--serve-min", type=int, default=30)
+    ap.add_argument("--serve-max", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.workload == "serving":
+        run_serving(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

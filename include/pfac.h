@@ -83,12 +83,14 @@ typedef struct {
 /* Match options; a NULL pointer means library defaults (the table's
  * autotuned choice when pfac_autotune has run). */
 typedef struct {
-    uint32_t variant;      /* 0 = default, 1 = prefix bitmap filter in shared
-                              memory, 2 = prefix table in shared memory,
-                              3 = prefix table through L2 only */
+    uint32_t variant;      /* 0 = default (autotuned when pfac_autotune ran),
+                              1 = prefix bitmap in shared memory, its
+                              entries read through L2, 2 = prefix bitmap and
+                              entries in shared memory */
     uint32_t prefix_depth; /* 0 = table default; else one the table holds */
     uint32_t ctas_per_sm;  /* 0 = default (1) */
-    uint32_t flags;        /* reserved, 0 */
+    uint32_t bitmap_copies; /* copies of the prefix bitmap in shared memory
+                              (1, 2, 4, ..., 32); 0 = as many as fit */
     void *ev_scan_begin;   /* optional cudaEvent_t recorded on the call's stream
                               right before the scan kernel, for profiling */
     void *ev_scan_end;     /* optional cudaEvent_t recorded right after it */
@@ -196,10 +198,11 @@ int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
  * (optionally) d_status.
  *
  * Limits and rules:
- *   - the scratch an input needs grows with its size (about 0.53 bytes per
- *     input byte); inputs that need more than PFAC_NOALLOC_SCRATCH_BYTES
- *     (roughly 60 MiB of input) are rejected with PFAC_EINVAL and a message
- *     naming both sizes, before any device work;
+ *   - the scratch an input needs grows with its size (about 0.55 bytes per
+ *     input byte, pfac_workspace_bytes gives the exact figure); inputs that
+ *     need more than PFAC_NOALLOC_SCRATCH_BYTES (roughly 58 MiB of input) are
+ *     rejected with PFAC_EINVAL and a message naming both sizes, before any
+ *     device work;
  *   - the first call on a device looks up that device's copy of the array
  *     (cudaGetSymbolAddress, with the device current); make that first call
  *     before any stream capture;
@@ -213,6 +216,70 @@ int pfac_match_noalloc(const pfac_table *t, const uint8_t *d_input, uint64_t n_b
                        const uint64_t *d_seg_offsets, uint32_t n_segments, uint64_t *d_out_keys,
                        uint64_t out_capacity, uint64_t *d_count, int32_t *d_status,
                        const pfac_match_opts *opts, void *cuda_stream);
+
+/*
+ * pfac_autotune - choose the scan configuration of a table by timing it
+ * (the prefix depth resolved in shared memory, whether the prefix entries
+ * live in shared memory, and how many copies of the prefix bitmap are
+ * spread over the shared-memory banks).  Each candidate runs the scan kernel
+ * on the caller's device-resident sample (same argument rules as
+ * pfac_match_async); the fastest becomes the table's default for later
+ * pfac_match calls without options.  With a non-NULL cache_path the choice
+ * is read from / appended to that text file, keyed by alphabet size,
+ * pattern count, maximum pattern length, sample size class and GPU name.
+ * Synchronous (waits for the stream).  out may be NULL.
+ */
+typedef struct {
+    uint32_t variant, prefix_depth, bitmap_copies;
+    uint32_t n_tried;
+    float scan_ms;       /* scan-kernel time of the choice on the sample */
+    float default_ms;    /* scan-kernel time of the library default */
+    int from_cache;
+} pfac_tune_result;
+
+int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,
+                  const uint64_t *d_seg_offsets, uint32_t n_segments, const char *cache_path,
+                  void *cuda_stream, pfac_tune_result *out);
+
+/*
+ * Serving loop (continuous batching over a resident table).
+ *
+ * pfac_server_create starts a dispatcher thread with n_slots CUDA streams and
+ * one device-memory pool of device_bytes.  pfac_server_submit queues a request
+ * (host text and host segment offsets, same rules as pfac_match; both buffers
+ * must stay valid until the request completes; pinned buffers make the copies
+ * asynchronous).  Requests are admitted oldest first as soon as a slot is free
+ * and the pool can hold the request's input, offsets, workspace and output;
+ * admitted requests run concurrently on their streams.  pfac_server_wait
+ * blocks until a request is done (timeout_s <= 0: no limit), pfac_server_poll
+ * returns the next completed request (1 when none), and the result's keys
+ * stay valid until pfac_server_release.  Times are seconds on a monotonic
+ * clock (submit, admission, completion).
+ */
+typedef struct pfac_server pfac_server;
+typedef struct {
+    uint32_t n_slots;           /* concurrent requests on the GPU; 0 = 4 */
+    uint32_t reserved0;
+    uint64_t device_bytes;      /* pool for in-flight requests; 0 = 1 GiB */
+    uint64_t max_request_bytes; /* largest input accepted; 0 = device_bytes / 4 */
+    uint64_t reserved[4];
+} pfac_server_opts;
+typedef struct {
+    uint64_t id;
+    int32_t status;             /* PFAC_OK or the request's error */
+    int32_t reserved0;
+    uint64_t n_keys;
+    const uint64_t *keys;       /* host memory owned by the server */
+    double t_submit, t_admit, t_done;
+} pfac_result;
+
+int pfac_server_create(const pfac_table *t, const pfac_server_opts *opts, pfac_server **out);
+int pfac_server_submit(pfac_server *s, const uint8_t *h_input, uint64_t n_bytes,
+                       const uint64_t *h_seg_offsets, uint32_t n_segments, uint64_t *id);
+int pfac_server_wait(pfac_server *s, uint64_t id, double timeout_s, pfac_result *res);
+int pfac_server_poll(pfac_server *s, pfac_result *res);
+int pfac_server_release(pfac_server *s, uint64_t id);
+void pfac_server_destroy(pfac_server *s);
 
 /* pfac_table_info - statistics of a built table (host call, no device work). */
 int pfac_table_info(const pfac_table *t, pfac_table_info_t *out);

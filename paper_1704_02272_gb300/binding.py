@@ -15,11 +15,13 @@ from dataclasses import dataclass
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libpfac.so")
+# PFAC_LIB may name another build of the same library (for example one
+# compiled with different options); the default is the in-tree build.
+LIB_PATH = os.environ.get("PFAC_LIB") or os.path.join(HERE, "_build", "libpfac.so")
 
 ID_BITS = 24
 LAYOUT_COMPRESSED, LAYOUT_DENSE = 0, 1
-VARIANT_DEFAULT, VARIANT_FILTER, VARIANT_DSMEM, VARIANT_DGLOBAL = 0, 1, 2, 3
+VARIANT_DEFAULT, VARIANT_FILTER, VARIANT_DSMEM = 0, 1, 2  # DSMEM: entries in shared memory too
 
 STATUS = {0: "PFAC_OK", -1: "PFAC_EINVAL", -2: "PFAC_EDUP", -3: "PFAC_ESYMBOL",
           -4: "PFAC_ENOMEM", -5: "PFAC_ENOSPC", -6: "PFAC_ECUDA", -7: "PFAC_ETIMEOUT",
@@ -42,7 +44,7 @@ BUILD_HOST_ONLY = 1
 
 class MatchOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
-                ("ctas_per_sm", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("bitmap_copies", ctypes.c_uint32),
                 ("ev_scan_begin", ctypes.c_void_p), ("ev_scan_end", ctypes.c_void_p),
                 ("reserved", ctypes.c_uint32 * 4)]
 
@@ -56,6 +58,26 @@ class TableInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64), ("paper_bytes", ctypes.c_uint64),
                 ("dense_bytes", ctypes.c_uint64), ("output_lists", ctypes.c_uint64),
                 ("output_list_words", ctypes.c_uint64)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
+                ("bitmap_copies", ctypes.c_uint32), ("n_tried", ctypes.c_uint32),
+                ("scan_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
+                ("from_cache", ctypes.c_int)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64), ("max_request_bytes", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 4)]
+
+
+class ResultC(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("n_keys", ctypes.c_uint64),
+                ("keys", ctypes.POINTER(ctypes.c_uint64)), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 def _load():
@@ -80,6 +102,21 @@ def _load():
     lib.pfac_match_noalloc.restype = ctypes.c_int
     lib.pfac_match_noalloc.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp,
                                        ctypes.POINTER(MatchOpts), vp]
+    lib.pfac_autotune.restype = ctypes.c_int
+    lib.pfac_autotune.argtypes = [vp, vp, u64, vp, u32, ctypes.c_char_p, vp,
+                                  ctypes.POINTER(TuneResult)]
+    lib.pfac_server_create.restype = ctypes.c_int
+    lib.pfac_server_create.argtypes = [vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    lib.pfac_server_submit.restype = ctypes.c_int
+    lib.pfac_server_submit.argtypes = [vp, vp, u64, vp, u32, ctypes.POINTER(u64)]
+    lib.pfac_server_wait.restype = ctypes.c_int
+    lib.pfac_server_wait.argtypes = [vp, u64, ctypes.c_double, ctypes.POINTER(ResultC)]
+    lib.pfac_server_poll.restype = ctypes.c_int
+    lib.pfac_server_poll.argtypes = [vp, ctypes.POINTER(ResultC)]
+    lib.pfac_server_release.restype = ctypes.c_int
+    lib.pfac_server_release.argtypes = [vp, u64]
+    lib.pfac_server_destroy.restype = None
+    lib.pfac_server_destroy.argtypes = [vp]
     lib.pfac_table_info.restype = ctypes.c_int
     lib.pfac_table_info.argtypes = [vp, ctypes.POINTER(TableInfo)]
     lib.pfac_table_free.restype = None
@@ -111,9 +148,10 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, scan_events=None):
+def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, scan_events=None):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
+    o.bitmap_copies = bitmap_copies
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event
@@ -174,6 +212,17 @@ class Table:
 
     def __exit__(self, *a):
         self.close()
+
+
+def autotune(table: Table, text: torch.Tensor, seg: torch.Tensor, cache_path=None,
+             stream=None) -> dict:
+    """pfac_autotune on a device-resident sample; returns the choice."""
+    r = TuneResult()
+    n_seg = max(seg.numel() - 1, 0)
+    cp = cache_path.encode() if cache_path else None
+    _check(LIB.pfac_autotune(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg, cp,
+                             ctypes.c_void_p(_stream(stream)), ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in TuneResult._fields_}
 
 
 def workspace_bytes(table: Table, n_bytes: int, n_segments: int, **opt) -> int:
@@ -253,3 +302,80 @@ def single_segment(n_bytes: int, device) -> torch.Tensor:
 
 def version() -> int:
     return LIB.pfac_version()
+
+
+class Server:
+    """pfac_server_*: continuous batching over a resident table.  Host buffers
+    passed to submit() are kept alive here until release()."""
+
+    def __init__(self, table: Table, n_slots: int = 4, device_bytes: int = 1 << 30,
+                 max_request_bytes: int = 0):
+        o = ServerOpts()
+        o.n_slots, o.device_bytes, o.max_request_bytes = n_slots, device_bytes, max_request_bytes
+        h = ctypes.c_void_p()
+        _check(LIB.pfac_server_create(table.handle, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._table = table
+        self._bufs = {}
+
+    def submit(self, text, seg) -> int:
+        """text: host uint8 array/tensor; seg: host uint64/int64 offsets."""
+        import numpy as np
+        if isinstance(text, torch.Tensor):
+            t_ptr, n = text.data_ptr(), text.numel()
+        else:
+            text = np.ascontiguousarray(text, dtype=np.uint8)
+            t_ptr, n = text.ctypes.data, text.size
+        if isinstance(seg, torch.Tensor):
+            s_ptr, ns = seg.data_ptr(), seg.numel()
+        else:
+            seg = np.ascontiguousarray(seg, dtype=np.uint64)
+            s_ptr, ns = seg.ctypes.data, seg.size
+        rid = ctypes.c_uint64()
+        _check(LIB.pfac_server_submit(self._h, ctypes.c_void_p(t_ptr if n else 0), n,
+                                      ctypes.c_void_p(s_ptr), max(ns - 1, 0), ctypes.byref(rid)))
+        self._bufs[rid.value] = (text, seg)
+        return rid.value
+
+    @staticmethod
+    def _result(r: ResultC) -> dict:
+        import numpy as np
+        keys = np.ctypeslib.as_array(r.keys, shape=(r.n_keys,)).copy() if r.n_keys else \
+            np.zeros(0, np.uint64)
+        return {"id": r.id, "status": r.status, "keys": keys, "t_submit": r.t_submit,
+                "t_admit": r.t_admit, "t_done": r.t_done}
+
+    def wait(self, rid: int, timeout: float = 0.0) -> dict:
+        r = ResultC()
+        _check(LIB.pfac_server_wait(self._h, rid, timeout, ctypes.byref(r)))
+        return self._result(r)
+
+    def poll(self):
+        r = ResultC()
+        rc = LIB.pfac_server_poll(self._h, ctypes.byref(r))
+        if rc == 1:
+            return None
+        _check(rc)
+        return self._result(r)
+
+    def release(self, rid: int):
+        _check(LIB.pfac_server_release(self._h, rid))
+        self._bufs.pop(rid, None)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            LIB.pfac_server_destroy(self._h)
+            self._h = None
+            self._bufs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

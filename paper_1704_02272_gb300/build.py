@@ -30,7 +30,7 @@ def nvcc() -> str:
 
 
 def sources():
-    srcs = ["builder.cpp", "match.cu", "noalloc.cu", "scan_dense.cu"] + [f"scan_bps{i}.cu" for i in range(1, 9)]
+    srcs = ["builder.cpp", "tune.cpp", "serve.cpp", "match.cu", "noalloc.cu", "scan_dense.cu"] + [f"scan_bps{i}.cu" for i in range(1, 9)]
     return [os.path.join(CSRC, s) for s in srcs]
 
 
@@ -70,7 +70,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError("nvcc failed:\n" + " ".join(c) + "\n" + r.stdout + r.stderr)
-    if force or jobs or not os.path.exists(LIB):
+    stale_lib = not os.path.exists(LIB) or any(
+        os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    if force or jobs or stale_lib:
         tmp = LIB + f".tmp{os.getpid()}"
         r = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs], capture_output=True, text=True)
         if r.returncode != 0:

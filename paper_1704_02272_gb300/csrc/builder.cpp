@@ -230,15 +230,16 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
             rec_of[v] = n_rec++;
         }
 
-        // ---- prefix lookups ----------------------------------------------
+        // ---- prefix nodes -------------------------------------------------
+        // depths kmin..kdef: the default depth keeps the bitmap F_k at most
+        // 2^20 bits (128 KiB), small enough for shared memory
         const uint32_t bps = bits_per_symbol(sigma);
-        // prefix tables for depths 1..kdef, where the default depth keeps the
-        // bitmap at 2^16 bits; a deeper one (up to 2^18 entries) on request
-        const uint32_t klim = std::min<uint32_t>(std::max(1u, 18 / bps), KMAX);
-        const uint32_t kdef = std::min<uint32_t>(std::max(1u, 16 / bps), klim);
+        const uint32_t klim = std::min<uint32_t>(std::max(1u, 20 / bps), KMAX);
         if (o.prefix_depth > klim)
             return set_error(PFAC_EINVAL, "pfac_build: prefix_depth %u > %u", o.prefix_depth, klim);
-        const uint32_t kmax = std::max(kdef, o.prefix_depth);
+        const uint32_t kdef = o.prefix_depth ? o.prefix_depth : klim;
+        const uint32_t kmin = kdef > 2 ? kdef - 2 : 1;
+        const uint32_t kmax = kdef;
         // walk the node-level trie over k symbols packed in x
         auto child_of = [&](uint32_t v, uint32_t c) -> int64_t {
             if (c >= sigma) return -1;
@@ -260,12 +261,47 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
             leaf_fin.reserve(merged);
         }
         uint64_t sz_pool = pool.size() * 4;
-        uint64_t sz_D[KMAX + 1] = {0}, sz_F[KMAX + 1] = {0};
+        // prefix node of depth k: bitmap, block counts, entries (Eq. 1 on the
+        // collapsed first k levels)
+        std::vector<uint32_t> Fv[KMAX + 1], Cv[KMAX + 1], Ev[KMAX + 1];
+        uint64_t sz_F[KMAX + 1] = {0}, sz_C[KMAX + 1] = {0}, sz_E[KMAX + 1] = {0};
         if (!dense)
-            for (uint32_t k = 1; k <= kmax; k++) {
-                uint64_t ent = 1ull << (k * bps);
-                sz_D[k] = ent * 4;
-                sz_F[k] = std::max<uint64_t>(ent / 8, 4);
+            for (uint32_t k = kmin; k <= kmax; k++) {
+                const uint64_t ent = 1ull << (k * bps);
+                const uint32_t smask = (1u << bps) - 1;
+                const uint64_t fw = ent >= 32 ? ent / 32 : 1;
+                Fv[k].assign(fw, 0);
+                Cv[k].assign((fw + 7) / 8, 0);
+                for (uint64_t x = 0; x < ent; x++) {
+                    uint32_t v = 0, e = 0;
+                    bool stopped = false;
+                    for (uint32_t i = 0; i < k; i++) {
+                        const int64_t ch = child_of(v, (uint32_t)(x >> (bps * i)) & smask);
+                        if (ch < 0) {
+                            e = fin_code[v];
+                            stopped = true;
+                            break;
+                        }
+                        v = (uint32_t)ch;
+                    }
+                    if (!stopped) {
+                        if (nodes[v].n_child == 0) e = fin_code[v];  // a leaf ends the walk
+                        else e = D_CONT | rec_of[v];
+                    }
+                    if (e) {
+                        Fv[k][x >> 5] |= 1u << (x & 31);
+                        Ev[k].push_back(e);
+                    }
+                }
+                uint32_t run = 0;
+                for (uint64_t w = 0; w < fw; w++) {
+                    if ((w & 7) == 0) Cv[k][w >> 3] = run;
+                    run += __builtin_popcount(Fv[k][w]);
+                }
+                if (Ev[k].empty()) Ev[k].push_back(0);
+                sz_F[k] = fw * 4;
+                sz_C[k] = Cv[k].size() * 4;
+                sz_E[k] = Ev[k].size() * 4;
             }
         uint64_t sz_stt = dense ? Q * sigma * 4 : 0;
         uint64_t sz_dfin = dense ? Q * 4 : 0;
@@ -325,11 +361,13 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         };
         uint64_t o_rec = place(sz_rec), o_fin = place(sz_fin), o_leaf = place(sz_leaf),
                  o_pool = place(sz_pool);
-        uint64_t o_D[KMAX + 1] = {0}, o_F[KMAX + 1] = {0};
-        for (uint32_t k = 1; k <= kmax; k++) {
-            o_D[k] = place(sz_D[k]);
-            o_F[k] = place(sz_F[k]);
-        }
+        uint64_t o_F[KMAX + 1] = {0}, o_C[KMAX + 1] = {0}, o_E[KMAX + 1] = {0};
+        if (!dense)
+            for (uint32_t k = kmin; k <= kmax; k++) {
+                o_F[k] = place(sz_F[k]);
+                o_C[k] = place(sz_C[k]);
+                o_E[k] = place(sz_E[k]);
+            }
         uint64_t o_stt = place(sz_stt), o_dfin = place(sz_dfin);
         const uint64_t blob = std::max<uint64_t>(off, 256);
 
@@ -343,31 +381,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         put(o_leaf, leaf_fin.data(), sz_leaf);
         put(o_pool, pool.data(), sz_pool);
         if (!dense)
-            for (uint32_t k = 1; k <= kmax; k++) {
-                uint32_t *D = (uint32_t *)(host.data() + o_D[k]);
-                uint32_t *F = (uint32_t *)(host.data() + o_F[k]);
-                const uint64_t ent = 1ull << (k * bps);
-                const uint32_t smask = (1u << bps) - 1;
-                for (uint64_t x = 0; x < ent; x++) {
-                    uint32_t v = 0;
-                    uint32_t e = 0;
-                    bool stopped = false;
-                    for (uint32_t i = 0; i < k; i++) {
-                        int64_t ch = child_of(v, (uint32_t)(x >> (bps * i)) & smask);
-                        if (ch < 0) {
-                            e = fin_code[v];
-                            stopped = true;
-                            break;
-                        }
-                        v = (uint32_t)ch;
-                    }
-                    if (!stopped) {
-                        if (nodes[v].n_child == 0) e = fin_code[v];  // a leaf ends the walk
-                        else e = D_CONT | rec_of[v];
-                    }
-                    D[x] = e;
-                    if (e) F[x >> 5] |= 1u << (x & 31);
-                }
+            for (uint32_t k = kmin; k <= kmax; k++) {
+                put(o_F[k], Fv[k].data(), sz_F[k]);
+                put(o_C[k], Cv[k].data(), sz_C[k]);
+                put(o_E[k], Ev[k].data(), sz_E[k]);
             }
         if (dense) {
             uint32_t *S = (uint32_t *)(host.data() + o_stt);
@@ -413,6 +430,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         dv.W = W;
         dv.bps = bps;
         dv.kdef = kdef;
+        dv.kmin = kmin;
         dv.layout = o.layout;
         dv.max_len = max_len;
         dv.n_rec = n_rec;
@@ -422,14 +440,16 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         dv.leaf_fin = (const uint32_t *)(B + o_leaf);
         dv.pool = (const uint32_t *)(B + o_pool);
         if (!dense)
-            for (uint32_t k = 1; k <= kmax; k++) {
-                dv.D[k] = (const uint32_t *)(B + o_D[k]);
+            for (uint32_t k = kmin; k <= kmax; k++) {
                 dv.F[k] = (const uint32_t *)(B + o_F[k]);
+                dv.C[k] = (const uint32_t *)(B + o_C[k]);
+                dv.E[k] = (const uint32_t *)(B + o_E[k]);
+                dv.n_e[k] = (uint32_t)Ev[k].size();
             }
         dv.stt = dense ? (const uint32_t *)(B + o_stt) : nullptr;
         dv.dfin = dense ? (const uint32_t *)(B + o_dfin) : nullptr;
         t->kmax = dense ? 0 : kmax;
-        if (!dense && o.prefix_depth) dv.kdef = o.prefix_depth;
+        t->kmin = dense ? 0 : kmin;
 
         pfac_table_info_t &I = t->info;
         I.alphabet_size = sigma;

@@ -13,11 +13,12 @@ struct pfac_table {
     void *d_blob = nullptr;
     uint64_t blob_bytes = 0;
     pfac_table_info_t info{};
-    uint32_t kmax = 0;        // prefix tables exist for depths 1..kmax
+    uint32_t kmin = 0, kmax = 0;  // prefix nodes exist for depths kmin..kmax
     int device = 0;
     // autotuned defaults (0 = none)
     uint32_t tuned_variant = 0;
     uint32_t tuned_k = 0;
+    uint32_t tuned_copies = 0;
 };
 
 namespace pfac {

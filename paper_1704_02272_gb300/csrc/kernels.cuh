@@ -1,28 +1,26 @@
-// Device code of the failure-less matcher (Section 2.3) on sm_103a.
+// Device code shared by the matcher's kernels (sm_103a), and the tile-
+// synchronous scan kernel used for the uncompressed state-transition table.
 //
-// Scan kernel (k_scan): a persistent grid, one CTA per SM.  Warp 16 is the
-// producer: one lane streams 8 KiB input tiles (plus a 16-byte halo) from HBM
+// k_scan (uncompressed table): a persistent grid, one CTA per SM.  Warp 16 is
+// the producer: one lane streams 8 KiB tiles (plus a 16-byte halo) from HBM
 // into a 4-stage shared-memory ring with cp.async.bulk, completion tracked by
 // mbarriers.  Warps 0..15 consume: each thread owns 16 consecutive start
-// positions.  Per position it forms the index of the next k symbols, tests the
-// prefix bitmap (or reads the prefix table) kept in shared memory, and only the
-// survivors continue the walk through the bitmap records (Eq. 1) in L2.  The
-// walk result of a position is fin(state where it stopped), the sorted id list
-// of every pattern it completed.  A block scan gives each thread its slot; the
-// tile's (position, fin) records go to a per-tile region of the workspace and
-// the tile's match and key counts to per-tile counters.
+// positions and walks the table from the root (Section 2.3), the rows of the
+// shallowest states held in shared memory.  A block scan gives each thread
+// its slot; the tile's (position, fin) records go to a per-tile region of the
+// workspace and the tile's match and key counts to per-unit counters.
 //
-// Ordering kernels: k_reduce scans the per-tile key counts (chunk sums plus a
-// last-block scan of the chunks), k_offsets turns them into per-tile output
-// offsets, k_expand writes the sorted keys of each tile from its records, and
-// tiles whose records did not fit re-run k_scan in emit mode, which writes
-// keys directly.  No kernel waits on another CTA, so there is no inter-CTA
-// spinning anywhere; the only waits are the mbarrier waits of the ring, each
-// bounded by a wall-clock limit after which the kernel records PFAC_ETIMEOUT.
+// Ordering kernels (match.cu): k_reduce scans the per-unit key counts,
+// k_offsets turns them into per-unit output offsets, k_expand writes the
+// sorted keys of each unit from its records, and units whose records did not
+// fit re-run the scan kernel in emit mode, which writes keys directly.  No
+// kernel waits on another CTA; the only waits are mbarrier waits, each bounded
+// by a wall-clock limit after which the kernel records PFAC_ETIMEOUT.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/pfac.h"
 #include "table.h"
 
 namespace pfac {
@@ -44,7 +42,9 @@ constexpr uint64_t WAIT_LIMIT_NS = 4000000000ull;  // bounded waits: 4 s
 
 constexpr int ST_BADSEG = 1, ST_TIMEOUT = 2, ST_DEVICE = 4;
 
-enum { VAR_FILTER = 1, VAR_DSMEM = 2, VAR_DGLOBAL = 3, VAR_DENSE = 4 };
+// scan variants: prefix bitmap in shared memory with its entries in global
+// memory (VAR_F) or in shared memory too (VAR_FE); uncompressed table (VAR_DENSE)
+enum { VAR_F = 1, VAR_FE = 2, VAR_DENSE = 4 };
 
 struct WsHeader {
     int32_t status;
@@ -60,26 +60,32 @@ struct MatchParams {
     uint64_t n;
     const uint64_t *seg;
     uint32_t n_seg;
-    uint32_t n_tiles;
+    uint32_t n_tiles;     // ordering units of the scan kernel in use
+    uint32_t unit_shift;  // log2 of the unit size in bytes
+    uint32_t unit_cap;    // records kept per unit
     uint64_t *out;
     uint64_t cap;
     uint64_t *d_count;
     int32_t *d_status;
     // workspace
     WsHeader *hdr;
-    uint32_t *tile_m;
-    uint64_t *tile_k;
-    uint64_t *key_off;
+    uint32_t *tile_m;     // per unit: records kept, or more than unit_cap
+    uint64_t *tile_k;     // per unit: keys
+    uint64_t *key_off;    // per unit: first output slot
     uint64_t *chunk;      // n_chunks sums, then n_chunks offsets
     uint32_t n_chunks;
     uint32_t *ovf_list;
     uint64_t *recs;
-    uint32_t *tile_bounds;
+    uint32_t *tile_bounds;  // tile-synchronous kernel: segment ends per tile
+    uint32_t *unit_seg;     // queued kernel: first offset index after each unit start
     // scan configuration
     uint32_t k;           // prefix depth
-    const uint32_t *D;    // prefix table of depth k (global)
-    const uint32_t *F;    // prefix bitmap of depth k (global)
-    uint32_t tbl_words;   // 32-bit words of the shared-memory table
+    const uint32_t *F;    // prefix node of depth k: bitmap,
+    const uint32_t *C;    //   block counts,
+    const uint32_t *E;    //   entries
+    uint32_t tbl_words;   // shared-memory words: bitmap copies (or dense rows)
+    uint32_t tbl_c_words;
+    uint32_t tbl_e_words;
     uint32_t rep_log2;    // bitmap copies in shared memory (log2)
     uint32_t dense_rows;  // dense layout: states whose rows live in shared memory
 };
@@ -182,47 +188,6 @@ __device__ __forceinline__ const uint32_t *fin_ids(const uint32_t *__restrict__ 
 
 // ------------------------------------------------------------ walks --------
 
-// Continues a walk at record r with the next symbol at relative position q
-// (Eq. 1 per step); returns fin of the state where it stops.  Positions below
-// `staged` are read from the staged tile, others from global memory; q never
-// reaches `lim` (the segment end, clipped to the input end).
-template <int W>
-__device__ __noinline__ uint32_t walk_rec(const uint32_t *__restrict__ rec,
-                                          const uint32_t *__restrict__ fin1,
-                                          const uint32_t *__restrict__ leaf_fin, uint32_t sigma,
-                                          uint32_t r, const uint8_t *sm, uint32_t staged,
-                                          const uint8_t *__restrict__ g, uint32_t q,
-                                          uint32_t lim) {
-    constexpr int RW = rec_words(W);
-    while (q < lim) {
-        const uint32_t *R = rec + (size_t)r * RW;
-        const uint32_t c = q < staged ? (uint32_t)sm[q] : (uint32_t)__ldg(g + q);
-        if (c >= sigma) break;
-        uint32_t word, below;
-        if (W == 1) {
-            word = __ldg(R);
-            below = 0;
-        } else if (W == 2) {
-            const uint2 b = __ldg(reinterpret_cast<const uint2 *>(R));
-            word = c < 32 ? b.x : b.y;
-            below = c < 32 ? 0u : (uint32_t)__popc(b.x);
-        } else {
-            word = __ldg(R + (c >> 5));
-            const uint32_t cw = __ldg(R + 10 + (c >> 7));
-            below = (cw >> (8 * ((c >> 5) & 3))) & 0xFFu;
-        }
-        const uint32_t bit = c & 31;
-        if (!((word >> bit) & 1u)) break;
-        const uint32_t rank = below + (uint32_t)__popc(word & ((1u << bit) - 1u));
-        const uint32_t meta = __ldg(R + W);
-        const uint32_t base = meta & META_BASE_MASK;
-        if (meta & META_ALL_LEAF) return __ldg(leaf_fin + base + rank);
-        r = base + rank;
-        q++;
-    }
-    return W == 1 ? __ldg(fin1 + r) : __ldg(rec + (size_t)r * RW + W + 1);
-}
-
 // Uncompressed walk: state s, next-state table rows of sigma entries; rows of
 // states below `nrows` are read from shared memory.
 static __device__ __noinline__ uint32_t walk_dense(const uint32_t *__restrict__ stt,
@@ -314,99 +279,6 @@ __device__ __forceinline__ uint32_t seg_limit(const uint32_t *segs, uint32_t p, 
     return r < rem ? r : rem;
 }
 
-// Walk results of one consumer thread's 16 positions (compressed layout).
-template <int W, int BPS, int VAR>
-__device__ __forceinline__ void thread_positions(const MatchParams &P, const uint8_t *sin,
-                                                 uint32_t staged, uint32_t valid, uint32_t rem,
-                                                 const uint32_t *segs, uint64_t tile_start,
-                                                 const uint8_t *__restrict__ g,
-                                                 const uint32_t *stbl, uint32_t tid,
-                                                 uint32_t (&fr)[BPT]) {
-    const uint32_t p0 = tid * BPT;
-    const uint32_t k = P.k;
-    const uint32_t sigma = P.T.sigma;
-#pragma unroll
-    for (int j = 0; j < BPT; j++) fr[j] = 0;
-    if (p0 >= valid) return;
-    const uint32_t lim = seg_limit(segs, p0, rem, P.seg, P.n_seg, tile_start);
-    const uint32_t span = p0 + BPT - 1 + k;  // one past the last symbol read
-    bool fast = span <= lim && span <= staged;
-    uint32_t x[8];
-    if (fast) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(sin + p0);
-        const uint4 b = *reinterpret_cast<const uint4 *>(sin + p0 + 16);
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-        if (BPS < 8) {
-            // every symbol the window uses must fit in BPS bits
-            const uint32_t hm = 0x01010101u * ((0xFFu << BPS) & 0xFFu);
-            const uint32_t nbytes = BPT - 1 + k;
-            uint32_t bad = 0;
-#pragma unroll
-            for (int w = 0; w < 8; w++) {
-                const uint32_t lo = 4u * w;
-                uint32_t m = hm;
-                if (lo + 4 > nbytes)
-                    m = lo >= nbytes ? 0u : (hm & (0xFFFFFFFFu >> (8u * (lo + 4 - nbytes))));
-                bad |= x[w] & m;
-            }
-            fast = bad == 0;
-        }
-    }
-    if (fast) {
-        uint32_t bs[BPS + 1];
-        pack_symbols<BPS>(x, bs);
-        const uint32_t kmask = (1u << (BPS * k)) - 1u;
-        uint32_t idx[BPT];
-#pragma unroll
-        for (int j = 0; j < BPT; j++) idx[j] = symbols_at<BPS>(bs, j) & kmask;
-        uint32_t ent[BPT];
-        uint32_t surv = 0;
-        if (VAR == VAR_FILTER) {
-            const uint32_t rep = P.rep_log2;
-            const uint32_t copy = tid & ((1u << rep) - 1u);
-#pragma unroll
-            for (int j = 0; j < BPT; j++) {
-                const uint32_t w = stbl[((idx[j] >> 5) << rep) | copy];
-                surv |= ((w >> (idx[j] & 31)) & 1u) << j;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < BPT; j++) {
-                ent[j] = VAR == VAR_DSMEM ? stbl[idx[j]] : __ldg(P.D + idx[j]);
-                surv |= (ent[j] != 0 ? 1u : 0u) << j;
-            }
-        }
-        if (surv) {
-#pragma unroll
-            for (int j = 0; j < BPT; j++) {
-                if ((surv >> j) & 1u) {
-                    const uint32_t e = VAR == VAR_FILTER ? __ldg(P.D + idx[j]) : ent[j];
-                    fr[j] = (e & D_CONT)
-                                ? walk_rec<W>(P.T.rec, P.T.fin, P.T.leaf_fin, sigma,
-                                              e & D_VAL_MASK, sin, staged, g, p0 + j + k, lim)
-                                : e;
-                }
-            }
-        }
-        return;
-    }
-    // general path: segment ends inside the window, the input end, or
-    // symbols outside the packed range -> walk every position from the root
-#pragma unroll 1
-    for (int j = 0; j < BPT; j++) {
-        const uint32_t p = p0 + j;
-        if (p >= valid) break;
-        const uint32_t lj = seg_limit(segs, p, rem, P.seg, P.n_seg, tile_start);
-        const uint32_t f = walk_rec<W>(P.T.rec, P.T.fin, P.T.leaf_fin, sigma, 0u, sin, staged, g,
-                                       p, lj);
-        // keep fr in registers: select by position
-#pragma unroll
-        for (int i = 0; i < BPT; i++)
-            if (i == j) fr[i] = f;
-    }
-}
-
 // Walk results of one thread's 16 positions (uncompressed layout).
 __device__ __forceinline__ void thread_positions_dense(const MatchParams &P, const uint8_t *sin,
                                                        uint32_t staged, uint32_t valid,
@@ -485,10 +357,11 @@ __device__ __forceinline__ uint64_t cons_scan(uint64_t v, uint64_t *wt, uint64_t
 
 // ------------------------------------------------------------ scan kernel --
 
+#ifdef PFAC_DEFINE_DENSE_KERNEL
+// Scan kernel of the uncompressed table.
 // emit == 0: scan every tile, keep records, count keys.
 // emit == 1: re-run the tiles listed in ovf_list and write their keys.
-template <int W, int BPS, int VAR>
-__global__ void __launch_bounds__(NTHREADS, 1) k_scan(const MatchParams P, const int emit) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_scan_dense(const MatchParams P, const int emit) {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t tbl_bytes = (P.tbl_words * 4u + 127u) & ~127u;
     uint32_t *stbl = reinterpret_cast<uint32_t *>(smem);
@@ -557,14 +430,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_scan(const MatchParams P, const
     }
 
     // ---------------- consumer warps ----------------
-    if (VAR == VAR_FILTER) {
-        const uint32_t rep = P.rep_log2;
-        for (uint32_t i = tid; i < P.tbl_words; i += NCONS) stbl[i] = __ldg(P.F + (i >> rep));
-    } else if (VAR == VAR_DSMEM) {
-        for (uint32_t i = tid; i < P.tbl_words; i += NCONS) stbl[i] = __ldg(P.D + i);
-    } else if (VAR == VAR_DENSE) {
-        for (uint32_t i = tid; i < P.tbl_words; i += NCONS) stbl[i] = __ldg(P.T.stt + i);
-    }
+    for (uint32_t i = tid; i < P.tbl_words; i += NCONS) stbl[i] = __ldg(P.T.stt + i);
     cons_bar();
 
     const uint32_t lane = tid & 31;
@@ -587,11 +453,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_scan(const MatchParams P, const
         const uint8_t *g = P.in + tile_start;
 
         uint32_t fr[BPT];
-        if (VAR == VAR_DENSE)
-            thread_positions_dense(P, sin, staged, valid, rem, segs, tile_start, g, stbl, tid, fr);
-        else
-            thread_positions<W, BPS, VAR>(P, sin, staged, valid, rem, segs, tile_start, g, stbl,
-                                          tid, fr);
+        thread_positions_dense(P, sin, staged, valid, rem, segs, tile_start, g, stbl, tid, fr);
         // the stage is no longer read: hand it back to the producer
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -630,12 +492,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_scan(const MatchParams P, const
                 if (!f) continue;
                 const uint32_t L = fin_len(P.T.pool, f);
                 const uint32_t *ids = fin_ids(P.T.pool, f);
-                const uint64_t pk = (tile_start + p0 + j) << 24;
+                const uint64_t pk = (tile_start + p0 + j) << PFAC_ID_BITS;
                 for (uint32_t e = 0; e < L; e++, o++)
                     if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
             }
         }
     }
 }
+
+#endif  // PFAC_DEFINE_DENSE_KERNEL
 
 }  // namespace pfac

@@ -8,7 +8,7 @@
 #include <mutex>
 
 #include "internal.h"
-#include "kernels.cuh"
+#include "kernels_q.cuh"
 
 namespace pfac {
 
@@ -59,6 +59,27 @@ __global__ void k_bounds(const MatchParams P) {
             if (o >= end) break;
         }
         B[0] = ovf ? SEG_OVF : cnt;
+    }
+}
+
+// Validates the offsets and records, per 512-byte unit of the queued scan
+// kernel, the index of the first offset beyond the unit start.
+__global__ void k_unitseg(const MatchParams P) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t *seg = P.seg;
+    for (uint64_t s = gt; s < P.n_seg; s += stride)
+        if (__ldg(seg + s + 1) < __ldg(seg + s)) atomicOr(&P.hdr->status, ST_BADSEG);
+    if (gt == 0 && (__ldg(seg) != 0 || __ldg(seg + P.n_seg) != P.n))
+        atomicOr(&P.hdr->status, ST_BADSEG);
+    for (uint64_t u = gt; u < P.n_tiles; u += stride) {
+        const uint64_t start = u << P.unit_shift;
+        uint32_t lo = 1, hi = P.n_seg;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(seg + mid) > start) hi = mid; else lo = mid + 1;
+        }
+        P.unit_seg[u] = lo;
     }
 }
 
@@ -176,10 +197,10 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
     const uint32_t *pool = P.T.pool;
     for (uint64_t t = gw; t < P.n_tiles; t += nwarps) {
         const uint32_t m = P.tile_m[t];
-        if (m == 0 || m > (uint32_t)REC_CAP) continue;
+        if (m == 0 || m > P.unit_cap || P.tile_k[t] == 0) continue;
         uint64_t off = P.key_off[t];
-        const uint64_t *rr = P.recs + t * REC_CAP;
-        const uint64_t tile_start = t * TILE;
+        const uint64_t *rr = P.recs + t * P.unit_cap;
+        const uint64_t tile_start = t << P.unit_shift;
         for (uint32_t i0 = 0; i0 < m; i0 += 32) {
             const uint32_t i = i0 + lane;
             uint64_t r = 0;
@@ -222,11 +243,13 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
 struct Plan {
     int var;
     uint32_t k;
-    uint32_t tbl_words;
+    uint32_t tbl_words, tbl_c_words, tbl_e_words;
     uint32_t rep_log2;
     uint32_t dense_rows;
+    uint32_t unit_shift, unit_cap;
     void *kernel;
     size_t smem;
+    bool queued;
 };
 
 struct WsLayout {
@@ -236,9 +259,10 @@ struct WsLayout {
 
 static inline uint64_t al256(uint64_t x) { return (x + 255) & ~255ull; }
 
-static WsLayout ws_layout(uint64_t n_bytes, uint32_t n_seg) {
+static WsLayout ws_layout(uint64_t n_bytes, uint32_t n_seg, const Plan &pl) {
     WsLayout L{};
-    const uint64_t nt = (n_bytes + TILE - 1) / TILE;
+    const uint64_t ub = 1ull << pl.unit_shift;
+    const uint64_t nt = (n_bytes + ub - 1) / ub;
     L.n_tiles = (uint32_t)nt;
     L.n_chunks = (uint32_t)((nt + CHUNK - 1) / CHUNK);
     uint64_t o = 0;
@@ -253,8 +277,10 @@ static WsLayout ws_layout(uint64_t n_bytes, uint32_t n_seg) {
     L.key_off = put(nt * 8);
     L.chunk = put((uint64_t)L.n_chunks * 16);
     L.ovf = put(nt * 4);
-    L.recs = put(nt * REC_CAP * 8);
-    L.bounds = put(n_seg > 1 ? nt * SEGW * 4 : 0);
+    L.recs = put(nt * pl.unit_cap * 8);
+    // segment data: per-tile lists (tile-synchronous kernel) or the first
+    // offset index per unit (queued kernel)
+    L.bounds = put(n_seg > 1 ? (pl.queued ? nt * 4 : nt * SEGW * 4) : 0);
     L.total = o;
     return L;
 }
@@ -273,10 +299,17 @@ static void *scan_kernel_for(uint32_t bps, int var) {
     }
 }
 
-static size_t scan_smem(uint32_t tbl_words) {
+static size_t dense_smem(uint32_t tbl_words) {
     const size_t tbl = ((size_t)tbl_words * 4 + 127) & ~(size_t)127;
     return tbl + STAGES * STAGE_IN + STAGES * SEGW * 4 + 2 * STAGES * 8 + 2 * STAGES * 4 +
            (CW + 1) * 8;
+}
+
+constexpr size_t SMEM_LIMIT = 232448;  // per-CTA dynamic shared memory on sm_103a
+
+static size_t queued_smem(uint32_t w, uint32_t cw, uint32_t ew) {
+    const size_t tbl = (((size_t)w + cw + ew) * 4 + 127) & ~(size_t)127;
+    return tbl + QW * sizeof(WarpArea);
 }
 
 static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl) {
@@ -289,38 +322,65 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
         pl->dense_rows = rows;
         pl->tbl_words = rows * T.sigma;
         pl->kernel = scan_kernel_dense();
-    } else {
-        uint32_t k = opts && opts->prefix_depth ? opts->prefix_depth
-                                                 : (t->tuned_k ? t->tuned_k : T.kdef);
-        if (k < 1 || k > t->kmax)
-            return set_error(PFAC_EINVAL, "pfac_match: prefix_depth %u not held by the table", k);
-        const uint64_t ent = 1ull << (k * T.bps);
-        int var = opts && opts->variant ? (int)opts->variant
-                                        : (t->tuned_variant ? (int)t->tuned_variant : 0);
-        if (var == 0) var = ent <= 65536 ? VAR_FILTER : (ent * 4 <= TABLE_SMEM_MAX ? VAR_DSMEM : VAR_DGLOBAL);
-        pl->var = var;
-        pl->k = k;
-        if (var == VAR_FILTER) {
-            const uint64_t fw = ent >= 32 ? ent / 32 : 1;
-            uint32_t rep = 0;
-            while (rep < 5 && (fw << (rep + 1)) * 4 <= TABLE_SMEM_MAX) rep++;
-            if (fw * 4 > TABLE_SMEM_MAX)
-                return set_error(PFAC_EINVAL, "pfac_match: prefix bitmap of depth %u too large", k);
-            pl->rep_log2 = rep;
-            pl->tbl_words = (uint32_t)(fw << rep);
-        } else if (var == VAR_DSMEM) {
-            if (ent * 4 > TABLE_SMEM_MAX)
-                return set_error(PFAC_EINVAL, "pfac_match: prefix table of depth %u too large", k);
-            pl->tbl_words = (uint32_t)ent;
-        } else if (var == VAR_DGLOBAL) {
-            pl->tbl_words = 0;
-        } else {
-            return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
-        }
-        pl->kernel = scan_kernel_for(T.bps, var);
+        pl->smem = dense_smem(pl->tbl_words);
+        pl->unit_shift = 13;
+        pl->unit_cap = REC_CAP;
+        pl->queued = false;
+        return PFAC_OK;
     }
+    const uint32_t k = opts && opts->prefix_depth ? opts->prefix_depth
+                                                   : (t->tuned_k ? t->tuned_k : T.kdef);
+    if (k < t->kmin || k > t->kmax)
+        return set_error(PFAC_EINVAL, "pfac_match: prefix depth %u not held (table holds %u..%u)",
+                         k, t->kmin, t->kmax);
+    const uint64_t ent = 1ull << (k * T.bps);
+    const uint32_t fw = (uint32_t)(ent >= 32 ? ent / 32 : 1);
+    const uint32_t cw = (fw + 7) / 8;
+    const uint32_t ew = T.n_e[k];
+    int var = opts && opts->variant ? (int)opts->variant
+                                    : (t->tuned_variant ? (int)t->tuned_variant : 0);
+    // largest power-of-two bitmap replication that fits next to the rest
+    auto best_rep = [&](uint32_t extra) -> int {
+        int rep = -1;
+        for (int r = 0; r <= 5; r++)
+            if (queued_smem((uint32_t)((uint64_t)fw << r), cw, extra) <= SMEM_LIMIT) rep = r;
+        return rep;
+    };
+    const int rep_f = best_rep(0), rep_fe = best_rep(ew);
+    if (var == 0) var = (rep_fe >= 0 && rep_fe >= rep_f - 1) ? VAR_FE : VAR_F;
+    int rep = var == VAR_FE ? rep_fe : rep_f;
+    if (var != VAR_F && var != VAR_FE)
+        return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
+    // the table's tuned choice applies only when the caller picks neither the
+    // variant nor the depth
+    const bool use_tuned = !(opts && (opts->variant || opts->prefix_depth));
+    const uint32_t copies = opts && opts->bitmap_copies ? opts->bitmap_copies
+                                                       : (use_tuned ? t->tuned_copies : 0u);
+    if (copies) {
+        int want = 0;
+        while ((1u << want) < copies) want++;
+        if ((1u << want) != copies || want > 5)
+            return set_error(PFAC_EINVAL, "pfac_match: bitmap_copies %u is not 1, 2, 4, .., 32",
+                             copies);
+        if (want > rep)
+            return set_error(PFAC_EINVAL, "pfac_match: %u bitmap copies do not fit", copies);
+        rep = want;
+    }
+    if (rep < 0)
+        return set_error(PFAC_EINVAL, "pfac_match: prefix node of depth %u does not fit in "
+                         "shared memory with variant %d", k, var);
+    pl->var = var;
+    pl->k = k;
+    pl->rep_log2 = (uint32_t)rep;
+    pl->tbl_words = (uint32_t)((uint64_t)fw << rep);
+    pl->tbl_c_words = cw;
+    pl->tbl_e_words = var == VAR_FE ? ew : 0;
+    pl->kernel = scan_kernel_for(T.bps, var);
+    pl->smem = queued_smem(pl->tbl_words, pl->tbl_c_words, pl->tbl_e_words);
+    pl->unit_shift = SLICE_SHIFT;
+    pl->unit_cap = SCAP;
+    pl->queued = true;
     if (!pl->kernel) return set_error(PFAC_EINVAL, "pfac_match: no kernel for this table");
-    pl->smem = scan_smem(pl->tbl_words);
     return PFAC_OK;
 }
 
@@ -358,9 +418,11 @@ using namespace pfac;
 
 extern "C" int pfac_workspace_bytes(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments,
                                     const pfac_match_opts *opts, uint64_t *bytes) {
-    (void)opts;
     if (!t || !bytes) return set_error(PFAC_EINVAL, "pfac_workspace_bytes: NULL argument");
-    *bytes = ws_layout(n_bytes, n_segments).total;
+    Plan pl;
+    const int rc = make_plan(t, opts, &pl);
+    if (rc) return rc;
+    *bytes = ws_layout(n_bytes, n_segments, pl).total;
     return PFAC_OK;
 }
 
@@ -382,13 +444,13 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     if (n_bytes && n_segments == 0)
         return set_error(PFAC_EINVAL, "pfac_match: a non-empty input needs a segment");
     if (out_capacity && !d_out_keys) return set_error(PFAC_EINVAL, "pfac_match: NULL output");
-    const WsLayout L = ws_layout(n_bytes, n_segments);
-    if (workspace_bytes < L.total)
-        return set_error(PFAC_EINVAL, "pfac_match: workspace of %llu bytes, %llu needed",
-                         (unsigned long long)workspace_bytes, (unsigned long long)L.total);
     Plan pl;
     int rc = make_plan(t, opts, &pl);
     if (rc) return rc;
+    const WsLayout L = ws_layout(n_bytes, n_segments, pl);
+    if (workspace_bytes < L.total)
+        return set_error(PFAC_EINVAL, "pfac_match: workspace of %llu bytes, %llu needed",
+                         (unsigned long long)workspace_bytes, (unsigned long long)L.total);
     rc = prepare_kernel(pl.kernel, pl.smem);
     if (rc) return rc;
 
@@ -415,27 +477,38 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.ovf_list = (uint32_t *)(W + L.ovf);
     P.recs = (uint64_t *)(W + L.recs);
     P.tile_bounds = (uint32_t *)(W + L.bounds);
+    P.unit_seg = (uint32_t *)(W + L.bounds);
+    P.unit_shift = pl.unit_shift;
+    P.unit_cap = pl.unit_cap;
     P.k = pl.k;
-    P.D = pl.k ? t->dev.D[pl.k] : nullptr;
     P.F = pl.k ? t->dev.F[pl.k] : nullptr;
+    P.C = pl.k ? t->dev.C[pl.k] : nullptr;
+    P.E = pl.k ? t->dev.E[pl.k] : nullptr;
     P.tbl_words = pl.tbl_words;
+    P.tbl_c_words = pl.tbl_c_words;
+    P.tbl_e_words = pl.tbl_e_words;
     P.rep_log2 = pl.rep_log2;
     P.dense_rows = pl.dense_rows;
+    const uint32_t nthreads = pl.queued ? QTHREADS : NTHREADS;
+    const uint32_t units_per_cta = pl.queued ? QW : 1;
 
     cudaError_t e = cudaMemsetAsync(P.hdr, 0, sizeof(WsHeader), st);
     const int nsm = sm_count();
     const uint32_t cps = opts && opts->ctas_per_sm ? opts->ctas_per_sm : 1;
     if (e == cudaSuccess && n_segments > 1 && L.n_tiles) {
-        k_bounds<<<nsm * 2, 256, 0, st>>>(P);
+        if (pl.queued) k_unitseg<<<nsm * 4, 256, 0, st>>>(P);
+        else k_bounds<<<nsm * 2, 256, 0, st>>>(P);
         e = cudaGetLastError();
     }
+    // persistent grid: one CTA per SM (fewer when there are few units)
+    const uint64_t want = ((uint64_t)L.n_tiles + units_per_cta - 1) / units_per_cta;
+    const uint32_t grid = (uint64_t)nsm * cps < want ? (uint32_t)nsm * cps : (uint32_t)want;
     if (e == cudaSuccess && opts && opts->ev_scan_begin)
         e = cudaEventRecord((cudaEvent_t)opts->ev_scan_begin, st);
     if (e == cudaSuccess && L.n_tiles) {
         int emit = 0;
         void *args[] = {&P, &emit};
-        const uint32_t grid = (uint32_t)nsm * cps < L.n_tiles ? (uint32_t)nsm * cps : L.n_tiles;
-        e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(NTHREADS), args, pl.smem, st);
+        e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(nthreads), args, pl.smem, st);
     }
     if (e == cudaSuccess && opts && opts->ev_scan_end)
         e = cudaEventRecord((cudaEvent_t)opts->ev_scan_end, st);
@@ -450,8 +523,7 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     if (e == cudaSuccess && L.n_tiles) {
         int emit = 1;
         void *args[] = {&P, &emit};
-        const uint32_t grid = (uint32_t)nsm * cps < L.n_tiles ? (uint32_t)nsm * cps : L.n_tiles;
-        e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(NTHREADS), args, pl.smem, st);
+        e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(nthreads), args, pl.smem, st);
     }
     if (e == cudaSuccess) {
         uint64_t warps = L.n_tiles ? L.n_tiles : 1;
@@ -473,9 +545,11 @@ extern "C" int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t 
     clear_error();
     if (!t || !n_out) return set_error(PFAC_EINVAL, "pfac_match: NULL argument");
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const WsLayout L = ws_layout(n_bytes, n_segments);
+    uint64_t ws_bytes = 0;
+    int rc0 = pfac_workspace_bytes(t, n_bytes, n_segments, opts, &ws_bytes);
+    if (rc0) return rc0;
     void *ws = nullptr, *small = nullptr;
-    cudaError_t e = cudaMallocAsync(&ws, L.total, st);
+    cudaError_t e = cudaMallocAsync(&ws, ws_bytes, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&small, 256, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -486,7 +560,7 @@ extern "C" int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t 
     uint64_t *d_cnt = (uint64_t *)small;
     int32_t *d_st = (int32_t *)((uint8_t *)small + 128);
     int rc = pfac_match_async(t, d_input, n_bytes, d_seg_offsets, n_segments, d_out_keys,
-                              out_capacity, d_cnt, d_st, ws, L.total, opts, cuda_stream);
+                              out_capacity, d_cnt, d_st, ws, ws_bytes, opts, cuda_stream);
     struct {
         uint64_t cnt;
         int32_t st;

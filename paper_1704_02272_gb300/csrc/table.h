@@ -16,10 +16,14 @@
 //     that are prefixes of s's string (its final ancestors and itself).  A
 //     walk reports fin of the state where it stops, which is exactly the set
 //     of finals it passed (Section 2.3).
-//   * Prefix lookup: for k symbols, D_k[x] is the state after walking the k
-//     symbols packed in x (BPS bits each, first symbol lowest) or the output
-//     of a walk that stopped earlier; F_k is the bitmap of D_k entries that
-//     are not "stopped with nothing to report".
+//   * Prefix node: the first k trie levels collapse into one node of fan-out
+//     2^(k*BPS) (k symbols packed BPS bits each, first symbol lowest).  Its
+//     bitmap F_k marks the indices whose walk does something (reaches depth k
+//     or stops after a final); like a node record, its children are addressed
+//     by popcount rank (Eq. 1): C_k holds the count of set bits before each
+//     256-bit block and E_k the entries of the set bits in index order.  An
+//     entry is D_CONT | record of the depth-k state, or the fin of the state
+//     where a shorter walk stopped.
 //
 // Dense layout (uncompressed PFAC): stt[s * sigma + c] = child or 0 (the root
 // is never a child), dfin[s] = fin(s).
@@ -31,7 +35,7 @@ namespace pfac {
 constexpr int KMAX = 16;                 // largest prefix depth held
 constexpr uint32_t META_ALL_LEAF = 0x80000000u;
 constexpr uint32_t META_BASE_MASK = 0x7FFFFFFFu;
-constexpr uint32_t D_CONT = 0x80000000u;  // D entry: continue at record
+constexpr uint32_t D_CONT = 0x80000000u;  // prefix entry: continue at record
 constexpr uint32_t D_VAL_MASK = 0x7FFFFFFFu;
 // fin encoding: 0 = empty; else (off << FIN_LEN_BITS) | len, len < FIN_LEN_ESC
 // with ids at pool[off .. off+len); len == FIN_LEN_ESC means the length is
@@ -52,6 +56,7 @@ struct DevTable {
     uint32_t W;           // 1, 2 or 8 (bitmap words per record)
     uint32_t bps;         // bits per symbol in prefix indices
     uint32_t kdef;        // default prefix depth
+    uint32_t kmin;        // shallowest prefix depth held
     uint32_t layout;      // pfac_layout
     uint32_t max_len;
     uint32_t n_rec;
@@ -60,8 +65,10 @@ struct DevTable {
     const uint32_t *fin;      // W == 1 only
     const uint32_t *leaf_fin;
     const uint32_t *pool;
-    const uint32_t *D[KMAX + 1];
-    const uint32_t *F[KMAX + 1];
+    const uint32_t *F[KMAX + 1];   // prefix bitmap of depth k
+    const uint32_t *C[KMAX + 1];   // set bits before each 256-bit block of F_k
+    const uint32_t *E[KMAX + 1];   // entries of the set bits of F_k
+    uint32_t n_e[KMAX + 1];        // number of entries of depth k
     const uint32_t *stt;      // dense layout
     const uint32_t *dfin;
 };

@@ -1,0 +1,201 @@
+// Autotuner of the scan configuration (pfac_autotune).  For a built table
+// and a device-resident sample it times the scan kernel for each candidate
+// (prefix depth resolved in shared memory x entries in shared memory or not x
+// copies of the prefix bitmap over the banks), keeps the fastest as the
+// table's default, and can remember the choice in a small text cache keyed by
+// the table's shape and the GPU.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace pfac;
+
+namespace {
+
+std::string cache_key(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments) {
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string gpu = "unknown";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) gpu = prop.name;
+    for (char &c : gpu)
+        if (c == ' ' || c == ',') c = '_';
+    uint32_t lg = 0;
+    while ((1ull << (lg + 1)) <= n_bytes) lg++;
+    char buf[256];
+    snprintf(buf, sizeof buf, "sigma=%u,n=%u,maxlen=%u,segs=%s,bytes=2^%u,gpu=%s",
+             t->info.alphabet_size, t->info.n_patterns, t->info.max_len,
+             n_segments > 1 ? "many" : "one", lg, gpu.c_str());
+    return buf;
+}
+
+bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_t *k,
+                  uint32_t *c, float *ms) {
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        char kbuf[300];
+        uint32_t a, b, d;
+        float e;
+        if (sscanf(line, "%299s %u %u %u %f", kbuf, &a, &b, &d, &e) == 5 && key == kbuf) {
+            *v = a;
+            *k = b;
+            *c = d;
+            *ms = e;
+            found = true;  // the last line for a key wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+}  // namespace
+
+extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,
+                             const uint64_t *d_seg_offsets, uint32_t n_segments,
+                             const char *cache_path, void *cuda_stream, pfac_tune_result *out) {
+    clear_error();
+    if (!t) return set_error(PFAC_EINVAL, "pfac_autotune: NULL table");
+    if (t->info.layout != PFAC_LAYOUT_COMPRESSED)
+        return set_error(PFAC_EINVAL, "pfac_autotune: only the compressed layout has choices");
+    pfac_tune_result res;
+    memset(&res, 0, sizeof res);
+    const std::string key = cache_key(t, n_bytes, n_segments);
+    if (cache_path) {
+        uint32_t v, k, c;
+        float ms;
+        if (cache_lookup(cache_path, key, &v, &k, &c, &ms) && k >= t->kmin && k <= t->kmax) {
+            t->tuned_variant = v;
+            t->tuned_k = k;
+            t->tuned_copies = c;
+            res.variant = v;
+            res.prefix_depth = k;
+            res.bitmap_copies = c;
+            res.scan_ms = ms;
+            res.from_cache = 1;
+            if (out) *out = res;
+            return PFAC_OK;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // forget an earlier choice so the default is measured as the library's own
+    t->tuned_variant = t->tuned_k = t->tuned_copies = 0;
+
+    struct Cand {
+        uint32_t var, k, copies;
+        float ms;
+    };
+    std::vector<Cand> cands;
+    cands.push_back({0, 0, 0, 0.f});  // library default
+    for (uint32_t k = t->kmin; k <= t->kmax; k++)
+        for (uint32_t var = 1; var <= 2; var++)
+            for (uint32_t copies = 32; copies >= 1; copies >>= 1) cands.push_back({var, k, copies, 0.f});
+
+    uint64_t ws_max = 0;
+    std::vector<Cand> ok;
+    for (const Cand &c : cands) {
+        pfac_match_opts o;
+        memset(&o, 0, sizeof o);
+        o.variant = c.var;
+        o.prefix_depth = c.k;
+        o.bitmap_copies = c.copies;
+        uint64_t b = 0;
+        if (pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b) != PFAC_OK) continue;
+        ws_max = std::max(ws_max, b);
+        ok.push_back(c);
+    }
+    clear_error();
+    void *ws = nullptr, *small = nullptr;
+    cudaError_t e = cudaMalloc(&ws, ws_max ? ws_max : 256);
+    if (e == cudaSuccess) e = cudaMalloc(&small, 256);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaFree(ws);
+        cudaFree(small);
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return set_error(PFAC_ENOMEM, "pfac_autotune: %s", cudaGetErrorString(e));
+    }
+    uint64_t *d_cnt = (uint64_t *)small;
+    int32_t *d_st = (int32_t *)((uint8_t *)small + 128);
+    std::vector<Cand> timed;
+    for (Cand c : ok) {
+        pfac_match_opts o;
+        memset(&o, 0, sizeof o);
+        o.variant = c.var;
+        o.prefix_depth = c.k;
+        o.bitmap_copies = c.copies;
+        uint64_t b = 0;
+        pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b);
+        // warm-up, then the median of three timed scans
+        int rc = pfac_match_async(t, d_sample, n_bytes, d_seg_offsets, n_segments, nullptr, 0,
+                                  d_cnt, d_st, ws, b, &o, st);
+        if (rc != PFAC_OK) {
+            clear_error();
+            continue;
+        }
+        o.ev_scan_begin = e0;
+        o.ev_scan_end = e1;
+        float t3[3];
+        bool good = true;
+        for (int r = 0; r < 3 && good; r++) {
+            rc = pfac_match_async(t, d_sample, n_bytes, d_seg_offsets, n_segments, nullptr, 0,
+                                  d_cnt, d_st, ws, b, &o, st);
+            if (rc == PFAC_OK && cudaEventSynchronize(e1) == cudaSuccess)
+                cudaEventElapsedTime(&t3[r], e0, e1);
+            else
+                good = false;
+        }
+        if (!good) {
+            clear_error();
+            continue;
+        }
+        std::sort(t3, t3 + 3);
+        c.ms = t3[1];
+        timed.push_back(c);
+    }
+    int32_t h_st = 0;
+    e = cudaMemcpyAsync(&h_st, d_st, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ws);
+    cudaFree(small);
+    if (e != cudaSuccess) return set_error(PFAC_ECUDA, "pfac_autotune: %s", cudaGetErrorString(e));
+    if (h_st != PFAC_OK) return set_error(h_st, "pfac_autotune: device reported %d", h_st);
+    if (timed.empty()) return set_error(PFAC_EINVAL, "pfac_autotune: no candidate ran");
+    const Cand &def = timed[0];
+    Cand best = def;
+    for (const Cand &c : timed)
+        if (c.var && c.ms < best.ms) best = c;
+    res.default_ms = def.var == 0 ? def.ms : 0.f;
+    res.n_tried = (uint32_t)timed.size();
+    if (best.var) {
+        t->tuned_variant = best.var;
+        t->tuned_k = best.k;
+        t->tuned_copies = best.copies;
+    }
+    res.variant = best.var;
+    res.prefix_depth = best.k;
+    res.bitmap_copies = best.copies;
+    res.scan_ms = best.ms;
+    if (cache_path && best.var) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s %u %u %u %.6f\n", key.c_str(), best.var, best.k, best.copies, best.ms);
+            fclose(f);
+        }
+    }
+    if (out) *out = res;
+    return PFAC_OK;
+}

@@ -1,0 +1,102 @@
+"""Serving loop (continuous batching): requests of the serving workload go
+through pfac_server_* concurrently, admitted as slots and pool memory free
+up; each result must equal the same request matched alone (and the oracle
+for a sample of them)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from tests.gpu_util import assert_same, keys_np
+
+pytestmark = pytest.mark.gpu
+
+pfac = pytest.importorskip("paper_1704_02272_gb300")
+
+
+@pytest.fixture(scope="module")
+def serving_setup():
+    pats = workloads.config5_patterns(n_patterns=50000)
+    rs = np.random.RandomState(55)
+    reqs = [workloads.serving_batch(rs, pats, max_packets=300) for _ in range(36)]
+    table = pfac.Table(pats, 256)
+    yield pats, reqs, table
+    table.close()
+
+
+def alone(table, text, seg):
+    t = torch.from_numpy(text).cuda()
+    s = torch.from_numpy(seg.astype(np.int64)).cuda()
+    k = pfac.match(table, t, s)
+    torch.cuda.synchronize()
+    return keys_np(k)
+
+
+def test_results_same_alone_and_in_the_mix(serving_setup):
+    pats, reqs, table = serving_setup
+    ref = [alone(table, t, s) for t, s in reqs]
+    # a pool that holds only a few requests at a time forces admission waits
+    biggest = max(t.size for t, _ in reqs)
+    with pfac.Server(table, n_slots=4, device_bytes=6 * biggest + (64 << 20),
+                     max_request_bytes=biggest) as srv:
+        ids = [srv.submit(t, s) for t, s in reqs]
+        got = [srv.wait(i, timeout=120) for i in ids]
+        for i in ids:
+            srv.release(i)
+    for k, (g, r) in enumerate(zip(got, ref)):
+        assert g["status"] == 0
+        assert_same(g["keys"], r, f"request {k}")
+        assert g["t_submit"] <= g["t_admit"] <= g["t_done"]
+    # later requests waited for earlier ones to free memory or slots
+    assert max(g["t_admit"] - g["t_submit"] for g in got) > 0
+    for k in (0, 7, 35):
+        t, s = reqs[k]
+        pos, ids_ = oracle.match_ac(pats, t, s)
+        assert_same(got[k]["keys"], oracle.pack_keys(pos, ids_), f"oracle request {k}")
+
+
+def test_poisson_arrivals_and_poll(serving_setup):
+    pats, reqs, table = serving_setup
+    ref = [alone(table, t, s) for t, s in reqs[:20]]
+    rs = np.random.RandomState(7)
+    arrivals = workloads.poisson_arrivals(rs, 400.0, 20)
+    done = {}
+    with pfac.Server(table, n_slots=3, device_bytes=1 << 30) as srv:
+        order = []
+
+        def submitter():
+            t0 = time.perf_counter()
+            for (t, s), at in zip(reqs[:20], arrivals):
+                dt = at - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                order.append(srv.submit(t, s))
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        deadline = time.time() + 120
+        while len(done) < 20 and time.time() < deadline:
+            r = srv.poll()
+            if r is None:
+                time.sleep(0.0005)
+                continue
+            done[r["id"]] = r
+        th.join()
+        assert len(done) == 20
+        for k, rid in enumerate(order):
+            assert done[rid]["status"] == 0
+            assert_same(done[rid]["keys"], ref[k], f"poisson request {k}")
+            srv.release(rid)
+
+
+def test_request_larger_than_pool_rejected(serving_setup):
+    pats, reqs, table = serving_setup
+    with pfac.Server(table, n_slots=2, device_bytes=8 << 20, max_request_bytes=1 << 20) as srv:
+        big = np.zeros(2 << 20, np.uint8)
+        with pytest.raises(pfac.PfacError) as ei:
+            srv.submit(big, np.array([0, big.size], np.uint64))
+        assert ei.value.status == -4

@@ -27,12 +27,16 @@ def check_all_variants(w, what, depths=None):
     ref = oracle_keys(w)
     assert_same(run(w), ref, f"{what} default")
     assert_same(run(w, layout=pfac.LAYOUT_DENSE), ref, f"{what} dense")
-    for var in (pfac.VARIANT_FILTER, pfac.VARIANT_DSMEM, pfac.VARIANT_DGLOBAL):
+    for var in (pfac.VARIANT_FILTER, pfac.VARIANT_DSMEM):
         for k in depths or [0]:
             try:
-                got = run(w, variant=var, prefix_depth=k or 0)
-            except pfac.PfacError as e:  # a table too large for shared memory
-                assert e.status == -1 and var != pfac.VARIANT_DGLOBAL, str(e)
+                kk = 0 if k is None else k
+                if k == "min":
+                    with pfac.Table(w.patterns, w.sigma, host_only=True) as th:
+                        kk = max(1, th.info()["prefix_depth"] - 2)
+                got = run(w, variant=var, prefix_depth=kk)
+            except pfac.PfacError as e:  # a prefix node too large for shared memory
+                assert e.status == -1, str(e)
                 continue
             assert_same(got, ref, f"{what} variant {var} depth {k}")
     return ref
@@ -58,7 +62,7 @@ def test_random_cases(case):
     seed, sigma, n, lo, hi, N, S, plants, ts = case
     w = workloads.tiny_case(seed, sigma, n, lo, hi, N, n_segments=S, n_plants=plants,
                             text_sigma=ts)
-    ref = check_all_variants(w, f"case {seed}", depths=[1, None])
+    ref = check_all_variants(w, f"case {seed}", depths=[None, "min"])
     assert ref.size > 0
 
 
@@ -185,3 +189,35 @@ def test_async_and_graph_replay():
             torch.cuda.synchronize()
             assert int(cnt.item()) == ref.size and int(st.item()) == 0
             assert_same(keys_np(out[:ref.size]), ref, "graph replay")
+
+
+@pytest.mark.parametrize("sigma,n,lo,hi", [(256, 3000, 2, 12), (4, 2000, 4, 20)])
+def test_autotune_keeps_results(tmp_path, sigma, n, lo, hi):
+    w = workloads.tiny_case(401 + sigma, sigma, n, lo, hi, 4 << 20, n_plants=2000)
+    ref = oracle_keys(w)
+    text, seg = to_device(w)
+    cache = str(tmp_path / "tune.txt")
+    with pfac.Table(w.patterns, sigma) as t:
+        r = pfac.autotune(t, text, seg, cache_path=cache)
+        assert r["n_tried"] >= 2 and r["from_cache"] == 0
+        assert r["variant"] in (0, 1, 2)
+        assert_same(run_table(t, text, seg), ref, "tuned default")
+        r2 = pfac.autotune(t, text, seg, cache_path=cache)
+        if r["variant"]:
+            assert r2["from_cache"] == 1
+            assert (r2["variant"], r2["prefix_depth"], r2["bitmap_copies"]) == \
+                (r["variant"], r["prefix_depth"], r["bitmap_copies"])
+        assert_same(run_table(t, text, seg), ref, "cached choice")
+
+
+def run_table(t, text, seg):
+    keys = pfac.match(t, text, seg)
+    torch.cuda.synchronize()
+    return keys_np(keys)
+
+
+@pytest.mark.parametrize("copies", [1, 4, 16])
+def test_bitmap_copies_option(copies):
+    w = workloads.tiny_case(410, 256, 1000, 2, 10, 1 << 20, n_plants=1000)
+    ref = oracle_keys(w)
+    assert_same(run(w, variant=pfac.VARIANT_FILTER, bitmap_copies=copies), ref, f"copies {copies}")
