@@ -242,6 +242,8 @@ def run_ours(args):
         user_opt["prefix_depth"] = args.prefix_depth
     if args.copies:
         user_opt["bitmap_copies"] = args.copies
+    if args.masks:
+        user_opt["child_masks"] = args.masks
     if args.autotune:
         tune = pfac.autotune(table, text, seg)
     ws = torch.empty(max(pfac.workspace_bytes(table, N, S, **user_opt),
@@ -492,6 +494,7 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="1: entries via L2, 2: entries in smem")
     ap.add_argument("--prefix-depth", type=int, default=0)
     ap.add_argument("--copies", type=int, default=0, help="prefix-bitmap copies in smem")
+    ap.add_argument("--masks", type=int, default=0, help="child masks: 1 off, 2 on")
     ap.add_argument("--autotune", action="store_true", help="pfac_autotune on the input first")
     ap.add_argument("--graph", action="store_true",
                     help="time CUDA-graph replays of the match call (default for packets)")

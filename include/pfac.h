@@ -94,7 +94,10 @@ typedef struct {
     void *ev_scan_begin;   /* optional cudaEvent_t recorded on the call's stream
                               right before the scan kernel, for profiling */
     void *ev_scan_end;     /* optional cudaEvent_t recorded right after it */
-    uint32_t reserved[4];
+    uint32_t child_masks;  /* second on-chip stage (child masks of the prefix
+                              entries in shared memory): 0 = when it fits,
+                              1 = off, 2 = required */
+    uint32_t reserved[3];
 } pfac_match_opts;
 
 typedef struct {
@@ -231,6 +234,7 @@ int pfac_match_noalloc(const pfac_table *t, const uint8_t *d_input, uint64_t n_b
  */
 typedef struct {
     uint32_t variant, prefix_depth, bitmap_copies;
+    uint32_t child_masks; /* 1 = off, 2 = on */
     uint32_t n_tried;
     float scan_ms;       /* scan-kernel time of the choice on the sample */
     float default_ms;    /* scan-kernel time of the library default */

@@ -46,7 +46,7 @@ class MatchOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("bitmap_copies", ctypes.c_uint32),
                 ("ev_scan_begin", ctypes.c_void_p), ("ev_scan_end", ctypes.c_void_p),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("child_masks", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class TableInfo(ctypes.Structure):
@@ -62,7 +62,8 @@ class TableInfo(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
-                ("bitmap_copies", ctypes.c_uint32), ("n_tried", ctypes.c_uint32),
+                ("bitmap_copies", ctypes.c_uint32), ("child_masks", ctypes.c_uint32),
+                ("n_tried", ctypes.c_uint32),
                 ("scan_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
                 ("from_cache", ctypes.c_int)]
 
@@ -148,10 +149,11 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, scan_events=None):
+def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,
+          scan_events=None):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
-    o.bitmap_copies = bitmap_copies
+    o.bitmap_copies, o.child_masks = bitmap_copies, child_masks
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event

@@ -218,16 +218,35 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 all_leaf[v] = all;
             }
         }
+        // Record order: sibling groups are placed breadth-first, each group
+        // contiguous and in symbol order (what Eq. 1 needs); below a group,
+        // every single-child chain continues in consecutive records, so a
+        // walk along a chain can fetch several levels in one memory round.
         const uint32_t NOREC = 0xFFFFFFFFu;
         std::vector<uint32_t> rec_of(Q, NOREC);
         uint32_t n_rec = 0;
         uint64_t merged = 0;
-        for (uint64_t v = 0; v < Q; v++) {
-            if (v > 0 && nodes[v].n_child == 0 && all_leaf[nodes[v].parent]) {
-                merged++;
-                continue;
+        for (uint64_t v = 1; v < Q; v++)
+            if (nodes[v].n_child == 0 && all_leaf[nodes[v].parent]) merged++;
+        auto rec_children = [&](uint32_t v) -> uint32_t {
+            return all_leaf[v] ? 0u : nodes[v].n_child;
+        };
+        std::vector<uint32_t> groups;  // nodes whose child group is still to place
+        groups.reserve(Q / 2 + 1);
+        auto place_chain = [&](uint32_t m) {
+            while (rec_children(m) == 1) {
+                m = nodes[m].first_child;
+                rec_of[m] = n_rec++;
             }
-            rec_of[v] = n_rec++;
+            if (rec_children(m) >= 2) groups.push_back(m);
+        };
+        rec_of[0] = n_rec++;
+        place_chain(0);
+        for (size_t gi = 0; gi < groups.size(); gi++) {
+            const uint32_t v = groups[gi];
+            const uint32_t f = nodes[v].first_child, nc = nodes[v].n_child;
+            for (uint32_t c = 0; c < nc; c++) rec_of[f + c] = n_rec++;
+            for (uint32_t c = 0; c < nc; c++) place_chain(f + c);
         }
 
         // ---- prefix nodes -------------------------------------------------
@@ -263,15 +282,21 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         uint64_t sz_pool = pool.size() * 4;
         // prefix node of depth k: bitmap, block counts, entries (Eq. 1 on the
         // collapsed first k levels)
-        std::vector<uint32_t> Fv[KMAX + 1], Cv[KMAX + 1], Ev[KMAX + 1];
-        uint64_t sz_F[KMAX + 1] = {0}, sz_C[KMAX + 1] = {0}, sz_E[KMAX + 1] = {0};
+        std::vector<uint32_t> Fv[KMAX + 1], Cv[KMAX + 1], Ev[KMAX + 1], Mv[KMAX + 1];
+        uint32_t cshift[KMAX + 1] = {0};
+        uint64_t sz_F[KMAX + 1] = {0}, sz_C[KMAX + 1] = {0}, sz_E[KMAX + 1] = {0},
+                 sz_M[KMAX + 1] = {0};
         if (!dense)
             for (uint32_t k = kmin; k <= kmax; k++) {
                 const uint64_t ent = 1ull << (k * bps);
                 const uint32_t smask = (1u << bps) - 1;
                 const uint64_t fw = ent >= 32 ? ent / 32 : 1;
+                // a count per word keeps the rank to one count and one popcount;
+                // large bitmaps count per 8 words
+                const uint32_t cs = fw <= 8192 ? 0u : 3u;
                 Fv[k].assign(fw, 0);
-                Cv[k].assign((fw + 7) / 8, 0);
+                Cv[k].assign((fw + (1ull << cs) - 1) >> cs, 0);
+                cshift[k] = cs;
                 for (uint64_t x = 0; x < ent; x++) {
                     uint32_t v = 0, e = 0;
                     bool stopped = false;
@@ -284,24 +309,39 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                         }
                         v = (uint32_t)ch;
                     }
+                    uint32_t mask = 0xFFFFFFFFu;
                     if (!stopped) {
-                        if (nodes[v].n_child == 0) e = fin_code[v];  // a leaf ends the walk
-                        else e = D_CONT | rec_of[v];
+                        if (nodes[v].n_child == 0) {
+                            e = fin_code[v];  // a leaf ends the walk
+                        } else {
+                            e = D_CONT | rec_of[v];
+                            if (fin_code[v] == 0) {
+                                mask = 0;
+                                for (uint32_t c = 0; c < sigma; c++)
+                                    if ((bm[(uint64_t)v * W + (c >> 5)] >> (c & 31)) & 1)
+                                        mask |= 1u << child_hash(c, sigma);
+                            }
+                        }
                     }
                     if (e) {
                         Fv[k][x >> 5] |= 1u << (x & 31);
                         Ev[k].push_back(e);
+                        Mv[k].push_back(mask);
                     }
                 }
                 uint32_t run = 0;
                 for (uint64_t w = 0; w < fw; w++) {
-                    if ((w & 7) == 0) Cv[k][w >> 3] = run;
+                    if ((w & ((1u << cs) - 1)) == 0) Cv[k][w >> cs] = run;
                     run += __builtin_popcount(Fv[k][w]);
                 }
-                if (Ev[k].empty()) Ev[k].push_back(0);
+                if (Ev[k].empty()) {
+                    Ev[k].push_back(0);
+                    Mv[k].push_back(0);
+                }
                 sz_F[k] = fw * 4;
                 sz_C[k] = Cv[k].size() * 4;
                 sz_E[k] = Ev[k].size() * 4;
+                sz_M[k] = Mv[k].size() * 4;
             }
         uint64_t sz_stt = dense ? Q * sigma * 4 : 0;
         uint64_t sz_dfin = dense ? Q * 4 : 0;
@@ -361,12 +401,14 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         };
         uint64_t o_rec = place(sz_rec), o_fin = place(sz_fin), o_leaf = place(sz_leaf),
                  o_pool = place(sz_pool);
-        uint64_t o_F[KMAX + 1] = {0}, o_C[KMAX + 1] = {0}, o_E[KMAX + 1] = {0};
+        uint64_t o_F[KMAX + 1] = {0}, o_C[KMAX + 1] = {0}, o_E[KMAX + 1] = {0},
+                 o_M[KMAX + 1] = {0};
         if (!dense)
             for (uint32_t k = kmin; k <= kmax; k++) {
                 o_F[k] = place(sz_F[k]);
                 o_C[k] = place(sz_C[k]);
                 o_E[k] = place(sz_E[k]);
+                o_M[k] = place(sz_M[k]);
             }
         uint64_t o_stt = place(sz_stt), o_dfin = place(sz_dfin);
         const uint64_t blob = std::max<uint64_t>(off, 256);
@@ -385,6 +427,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 put(o_F[k], Fv[k].data(), sz_F[k]);
                 put(o_C[k], Cv[k].data(), sz_C[k]);
                 put(o_E[k], Ev[k].data(), sz_E[k]);
+                put(o_M[k], Mv[k].data(), sz_M[k]);
             }
         if (dense) {
             uint32_t *S = (uint32_t *)(host.data() + o_stt);
@@ -444,6 +487,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 dv.F[k] = (const uint32_t *)(B + o_F[k]);
                 dv.C[k] = (const uint32_t *)(B + o_C[k]);
                 dv.E[k] = (const uint32_t *)(B + o_E[k]);
+                dv.M[k] = (const uint32_t *)(B + o_M[k]);
+                dv.c_shift[k] = cshift[k];
                 dv.n_e[k] = (uint32_t)Ev[k].size();
             }
         dv.stt = dense ? (const uint32_t *)(B + o_stt) : nullptr;

@@ -83,9 +83,12 @@ struct MatchParams {
     const uint32_t *F;    // prefix node of depth k: bitmap,
     const uint32_t *C;    //   block counts,
     const uint32_t *E;    //   entries
+    const uint32_t *M;    //   child masks of the entries
     uint32_t tbl_words;   // shared-memory words: bitmap copies (or dense rows)
     uint32_t tbl_c_words;
     uint32_t tbl_e_words;
+    uint32_t tbl_m_words; // child masks in shared memory (0 = not used)
+    uint32_t c_shift;     // words per rank count of F_k (log2)
     uint32_t rep_log2;    // bitmap copies in shared memory (log2)
     uint32_t dense_rows;  // dense layout: states whose rows live in shared memory
 };
@@ -218,17 +221,18 @@ __device__ __forceinline__ void pack_symbols(const uint32_t (&x)[8], uint32_t (&
         for (int w = 0; w < 8; w++) bs[w] = x[w];
         bs[BPS] = 0;
     } else if (BPS == 2) {
-        // four 2-bit symbols in the low bits of four bytes -> one byte
+        // four 2-bit symbols s0..s3 in the low bits of four bytes -> one byte
+        // s0 | s1 << 2 | s2 << 4 | s3 << 6: the multiplier places copies of the
+        // word at shifts 6, 12, 18, 24, so that bit 24 + 2i receives s_i and no
+        // other partial product reaches bits 24..31 (checked for all 256
+        // inputs); three byte permutes gather the four top bytes
         uint32_t b[8];
 #pragma unroll
-        for (int w = 0; w < 8; w++) {
-            uint32_t t = x[w] & 0x03030303u;
-            t = t | (t >> 6);            // s0|s1<<2 at bits 0..3, s2|s3<<2 at 16..19
-            t = (t & 0x000F000Fu);
-            b[w] = (t | (t >> 12)) & 0xFFu;
-        }
-        bs[0] = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-        bs[1] = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+        for (int w = 0; w < 8; w++) b[w] = (x[w] & 0x03030303u) * 0x01041040u;
+        bs[0] = __byte_perm(__byte_perm(b[0], b[1], 0x0073), __byte_perm(b[2], b[3], 0x0073),
+                            0x5410);
+        bs[1] = __byte_perm(__byte_perm(b[4], b[5], 0x0073), __byte_perm(b[6], b[7], 0x0073),
+                            0x5410);
         bs[2] = 0;
     } else {
 #pragma unroll

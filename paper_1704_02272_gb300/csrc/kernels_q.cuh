@@ -38,6 +38,8 @@ constexpr int SCAP = 32;                 // match records kept per slice by the 
 constexpr int QCAP = 128;                // queue entries per warp (and most survivors
                                          // of one slice queued at once)
 constexpr int QU = QCAP / 32;            // queue entries per lane per batch
+// walks a lane advances together while resolving: fewer for 48-byte records
+__host__ __device__ constexpr int walks_per_lane(int W) { return W == 8 ? 2 : 4; }
 constexpr uint32_t ROOT_X = 0xFFFFFFFFu; // queue entry: walk from the root
 constexpr uint32_t UNIT_OVF = 0xFFFFFFFFu;
 constexpr uint32_t LIM_MAX = 0xFFFFFFF0u;
@@ -52,152 +54,223 @@ struct QEntry {
 struct WarpArea {
     uint8_t ring[QRING][QSTAGE];
     QEntry q[QCAP];
+    uint32_t tail[QCAP];      // long walks compacted during resolution
     uint64_t bar[QRING];
 };
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // Rank of prefix index x among the set bits of F_k (Eq. 1 on the prefix
-// level): block count plus popcounts of the preceding words of its block.
+// level): the count before its word (or 8-word group) plus popcounts.
 __device__ __forceinline__ uint32_t prefix_rank(const uint32_t *Fs, uint32_t rep,
-                                                const uint32_t *Cs, uint32_t x) {
-    const uint32_t w = x >> 5, b0 = (x >> 8) << 3;
-    uint32_t r = Cs[x >> 8];
-    for (uint32_t i = b0; i < w; i++) r += __popc(Fs[i << rep]);
-    return r + __popc(Fs[w << rep] & ((1u << (x & 31)) - 1u));
+                                                const uint32_t *Cs, uint32_t cshift, uint32_t x) {
+    const uint32_t w = x >> 5;
+    uint32_t r = Cs[w >> cshift] + __popc(Fs[w << rep] & ((1u << (x & 31)) - 1u));
+    if (cshift) {
+        const uint32_t b0 = (w >> 3) << 3;
+        if (rep == 0) {
+            // one 8-word group, two vector loads, words before w only
+            const uint4 g0 = *reinterpret_cast<const uint4 *>(Fs + b0);
+            const uint4 g1 = *reinterpret_cast<const uint4 *>(Fs + b0 + 4);
+            const uint32_t o = w & 7;
+            r += (o > 0 ? __popc(g0.x) : 0) + (o > 1 ? __popc(g0.y) : 0) +
+                 (o > 2 ? __popc(g0.z) : 0) + (o > 3 ? __popc(g0.w) : 0) +
+                 (o > 4 ? __popc(g1.x) : 0) + (o > 5 ? __popc(g1.y) : 0) +
+                 (o > 6 ? __popc(g1.z) : 0);
+        } else {
+            for (uint32_t i = b0; i < w; i++) r += __popc(Fs[i << rep]);
+        }
+    }
+    return r;
 }
 
-// One batch: resolve up to QCAP queue entries (entry e handled by lane e % 32,
-// slot e / 32).  Each entry ends with the fin of the state its walk stops at.
-template <int W, int VAR>
-__device__ __forceinline__ void resolve_batch(const MatchParams &P, const QEntry *q, uint32_t n,
-                                              const uint32_t *Fs, const uint32_t *Cs,
-                                              const uint32_t *Es, uint32_t lane,
-                                              uint32_t (&fin)[QU], uint32_t (&pos)[QU],
-                                              uint32_t (&unit)[QU]) {
+// Record words of state r needed to take a step on symbol c: the word
+// holding c's bit, the rank base below that word, the meta word and (for
+// sigma > 32) the state's output.
+template <int W>
+__device__ __forceinline__ void load_step(const uint32_t *__restrict__ rec, uint32_t r, uint32_t c,
+                                          uint32_t &word, uint32_t &below, uint32_t &meta,
+                                          uint32_t &f) {
     constexpr int RW = rec_words(W);
+    const uint32_t *R = rec + (size_t)r * RW;
+    if (W == 1) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(R));
+        word = v.x;
+        below = 0;
+        meta = v.y;
+        f = 0;
+    } else if (W == 2) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(R));
+        word = (c & 32) ? v.y : v.x;
+        below = (c & 32) ? (uint32_t)__popc(v.x) : 0u;
+        meta = v.z;
+        f = v.w;
+    } else {
+        const uint32_t wi = (c >> 5) & 7;
+        word = __ldg(R + wi);
+        const uint2 mf = __ldg(reinterpret_cast<const uint2 *>(R + 8));
+        const uint32_t cw = __ldg(R + 10 + (wi >> 2));
+        below = (cw >> (8 * (wi & 3))) & 0xFFu;
+        meta = mf.x;
+        f = mf.y;
+    }
+}
+
+// One step of a walk at state st on symbol c (c >= sigma or past the limit
+// ends it).  Returns 0 = moved to st, 1 = stopped at st (output of st),
+// 2 = stopped on a merged leaf (output leaf_fin[st]).
+__device__ __forceinline__ int take_step(uint32_t sigma, uint32_t c, uint32_t word,
+                                         uint32_t below, uint32_t meta, uint32_t &st) {
+    const uint32_t bit = c & 31;
+    if (c >= sigma || !((word >> bit) & 1u)) return 1;
+    const uint32_t rank = below + (uint32_t)__popc(word & ((1u << bit) - 1u));
+    st = (meta & META_BASE_MASK) + rank;
+    return (meta & META_ALL_LEAF) ? 2 : 0;
+}
+
+// Resolves queue entries [e0, e0 + 32 * walks_per_lane(W)): a few rounds
+// with every lane advancing its walks together (most walks end within one or
+// two levels), then the walks still running are compacted one per lane, so
+// the long ones no longer cost the instructions of a full batch per level.
+// Entry e's output (fin of the state its walk stops at) replaces q[e].x.
+template <int W, int VAR>
+__device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, uint32_t n,
+                                             uint32_t e0, const uint32_t *Fs, const uint32_t *Cs,
+                                             const uint32_t *Es, uint32_t *tail,
+                                             uint32_t lane) {
+    constexpr int QU = walks_per_lane(W);
+    constexpr int LOCK_ROUNDS = 2;
     const uint32_t sigma = P.T.sigma, k = P.k, rep = P.rep_log2;
     const uint32_t *__restrict__ rec = P.T.rec;
-    uint32_t st[QU], qq[QU], lim[QU], ev[QU];
-    bool walk[QU];
+    uint32_t st[QU], qq[QU], lim[QU], fin[QU], unit[QU];
+    int state[QU];  // -1 idle, 0 walking, 1 stopped at st, 2 stopped on merged leaf st, 3 done
     // ---- phase A: prefix entries (independent loads for all entries)
 #pragma unroll
     for (int u = 0; u < QU; u++) {
-        const uint32_t e = lane + 32u * u;
+        const uint32_t e = e0 + lane + 32u * u;
+        state[u] = -1;
         fin[u] = 0;
-        walk[u] = false;
         st[u] = 0;
         qq[u] = 0;
         lim[u] = 0;
-        ev[u] = 0;
-        pos[u] = 0;
         unit[u] = 0xFFFFFFFFu;
         if (e < n) {
             const QEntry en = q[e];
             unit[u] = en.unit;
-            pos[u] = en.pos;
             lim[u] = en.lim;
             const uint32_t p = en.pos & 0x3FFu;
             if (en.x == ROOT_X) {
-                walk[u] = true;
-                st[u] = 0;
+                state[u] = 0;
                 qq[u] = p;
             } else {
-                const uint32_t r = prefix_rank(Fs, rep, Cs, en.x);
-                ev[u] = VAR == VAR_FE ? Es[r] : __ldg(P.E + r);
+                const uint32_t r = en.x;  // rank of the prefix index among F_k's set bits
+                const uint32_t ev = VAR == VAR_FE ? Es[r] : __ldg(P.E + r);
                 qq[u] = p + k;
+                if (ev & D_CONT) {
+                    state[u] = 0;
+                    st[u] = ev & D_VAL_MASK;
+                } else {
+                    state[u] = 3;
+                    fin[u] = ev;
+                }
             }
         }
     }
-#pragma unroll
-    for (int u = 0; u < QU; u++) {
-        if (unit[u] != 0xFFFFFFFFu && !walk[u]) {
-            if (ev[u] & D_CONT) {
-                walk[u] = true;
-                st[u] = ev[u] & D_VAL_MASK;
-            } else {
-                fin[u] = ev[u];
-            }
-        }
-    }
-    // ---- phase B: walk rounds, one trie level per round for every entry
-    uint32_t leaf_at[QU];
-#pragma unroll
-    for (int u = 0; u < QU; u++) leaf_at[u] = 0xFFFFFFFFu;
-    for (;;) {
+    // ---- phase B: lockstep rounds
+    for (int round = 0; round < LOCK_ROUNDS; round++) {
         bool any = false;
 #pragma unroll
-        for (int u = 0; u < QU; u++) any |= walk[u];
+        for (int u = 0; u < QU; u++) any |= state[u] == 0;
         if (!__any_sync(0xFFFFFFFFu, any)) break;
-        uint32_t c[QU], f1[QU], m0[QU], m1[QU];
-        uint4 b0[QU], b1[QU];
+        uint32_t c[QU], wd[QU], bl[QU], mt[QU], f1[QU];
 #pragma unroll
         for (int u = 0; u < QU; u++) {
-            if (walk[u]) {
-                const uint64_t ab = ((uint64_t)unit[u] << SLICE_SHIFT) + qq[u];
-                c[u] = qq[u] < lim[u] ? (uint32_t)__ldg(P.in + ab) : 0x100u;
-                const uint32_t *R = rec + (size_t)st[u] * RW;
-                if (W == 1) {
-                    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(R));
-                    b0[u].x = v.x;
-                    m0[u] = v.y;
-                    f1[u] = __ldg(P.T.fin + st[u]);
-                } else if (W == 2) {
-                    b0[u] = __ldg(reinterpret_cast<const uint4 *>(R));
-                    m0[u] = b0[u].z;
-                    f1[u] = b0[u].w;
-                } else {
-                    b0[u] = __ldg(reinterpret_cast<const uint4 *>(R));
-                    b1[u] = __ldg(reinterpret_cast<const uint4 *>(R + 4));
-                    const uint2 mf = __ldg(reinterpret_cast<const uint2 *>(R + 8));
-                    const uint2 cu = __ldg(reinterpret_cast<const uint2 *>(R + 10));
-                    m0[u] = mf.x;
-                    f1[u] = mf.y;
-                    m1[u] = (c[u] & 0x80u) ? cu.y : cu.x;
-                }
-            }
+            if (state[u] != 0) continue;
+            const uint64_t ab = ((uint64_t)unit[u] << SLICE_SHIFT) + qq[u];
+            c[u] = qq[u] < lim[u] ? (uint32_t)__ldg(P.in + ab) : 0x100u;
         }
 #pragma unroll
         for (int u = 0; u < QU; u++) {
-            if (!walk[u]) continue;
-            const uint32_t cc = c[u];
-            uint32_t word = 0, below = 0;
-            if (cc < sigma) {
-                if (W == 1) {
-                    word = b0[u].x;
-                } else if (W == 2) {
-                    word = cc < 32 ? b0[u].x : b0[u].y;
-                    below = cc < 32 ? 0u : (uint32_t)__popc(b0[u].x);
-                } else {
-                    const uint32_t wi = cc >> 5;
-                    const uint4 h = wi < 4 ? b0[u] : b1[u];
-                    const uint32_t wj = wi & 3;
-                    word = wj == 0 ? h.x : (wj == 1 ? h.y : (wj == 2 ? h.z : h.w));
-                    below = (m1[u] >> (8 * wj)) & 0xFFu;
-                }
+            if (state[u] != 0) continue;
+            load_step<W>(rec, st[u], c[u], wd[u], bl[u], mt[u], f1[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < QU; u++) {
+            if (state[u] != 0) continue;
+            const uint32_t cur = st[u];
+            const int r = take_step(sigma, c[u], wd[u], bl[u], mt[u], st[u]);
+            if (r == 0) {
+                qq[u]++;
+            } else if (r == 1) {
+                if (W == 1) st[u] = cur;
+                else fin[u] = f1[u];
+                state[u] = W == 1 ? 1 : 3;
+            } else {
+                state[u] = 2;
             }
-            const uint32_t bit = cc & 31;
-            if (cc >= sigma || !((word >> bit) & 1u)) {
-                fin[u] = f1[u];
-                walk[u] = false;
-                continue;
-            }
-            const uint32_t rank = below + (uint32_t)__popc(word & ((1u << bit) - 1u));
-            const uint32_t base = m0[u] & META_BASE_MASK;
-            if (m0[u] & META_ALL_LEAF) {
-                leaf_at[u] = base + rank;
-                walk[u] = false;
-                continue;
-            }
-            st[u] = base + rank;
-            qq[u]++;
         }
     }
+    // ---- phase C: compact the walks still running, one per lane
+    uint32_t nt = 0;
+    const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int u = 0; u < QU; u++)
-        if (leaf_at[u] != 0xFFFFFFFFu) fin[u] = __ldg(P.T.leaf_fin + leaf_at[u]);
+    for (int u = 0; u < QU; u++) {
+        const bool w = state[u] == 0;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, w);
+        if (w) {
+            // entry index (7 bits) and position; the state goes to the entry
+            const uint32_t t = nt + __popc(b & lt), e = e0 + lane + 32u * u;
+            tail[t] = (e - e0) | (qq[u] << 7);
+            q[e].x = st[u];
+        }
+        nt += __popc(b);
+    }
+    __syncwarp();
+    // ---- outputs of the walks that ended in phases A and B
+#pragma unroll
+    for (int u = 0; u < QU; u++) {
+        if (state[u] == 1) fin[u] = __ldg(P.T.fin + st[u]);
+        else if (state[u] == 2) fin[u] = __ldg(P.T.leaf_fin + st[u]);
+        if (state[u] >= 1) q[e0 + lane + 32u * u].x = fin[u];
+    }
+    // ---- phase D: the long walks, one per lane
+    for (uint32_t t0 = 0; t0 < nt; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        if (t < nt) {
+            const uint32_t e = e0 + (tail[t] & 0x7Fu);
+            uint32_t q1 = tail[t] >> 7;
+            const QEntry en = q[e];
+            uint32_t s1 = en.x;
+            const uint64_t ub = (uint64_t)en.unit << SLICE_SHIFT;
+            uint32_t f = 0;
+            for (;;) {
+                const uint32_t c = q1 < en.lim ? (uint32_t)__ldg(P.in + ub + q1) : 0x100u;
+                uint32_t wd, bl, mt, f1;
+                load_step<W>(rec, s1, c, wd, bl, mt, f1);
+                const uint32_t cur = s1;
+                const int r = take_step(sigma, c, wd, bl, mt, s1);
+                if (r == 0) {
+                    q1++;
+                    continue;
+                }
+                if (r == 1) f = W == 1 ? __ldg(P.T.fin + cur) : f1;
+                else f = __ldg(P.T.leaf_fin + s1);
+                break;
+            }
+            q[e].x = f;
+        }
+    }
+    __syncwarp();
+}
+
+template <int W, int VAR>
+__device__ __forceinline__ void resolve_batch(const MatchParams &P, QEntry *q, uint32_t n,
+                                              const uint32_t *Fs, const uint32_t *Cs,
+                                              const uint32_t *Es, uint32_t lane) {
+    constexpr uint32_t per = 32u * walks_per_lane(W);
+    // the tail list lives behind the queue entries of this warp
+    uint32_t *tail = reinterpret_cast<uint32_t *>(q + QCAP);
+    for (uint32_t e0 = 0; e0 < n; e0 += per)
+        resolve_pass<W, VAR>(P, q, n, e0, Fs, Cs, Es, tail, lane);
+    __syncwarp();
 }
 
 // Filter of one slice by one warp.  Fills the survivor masks of the lane's
@@ -208,24 +281,32 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
                                              uint32_t lima, uint32_t limb, bool general_lims,
                                              const uint64_t *__restrict__ gseg, uint64_t ustart,
                                              const uint32_t *Fs, uint32_t lane, uint32_t &surv,
-                                             uint32_t &rootm) {
+                                             uint32_t &rootm, uint32_t (&bs)[BPS + 1]) {
     const uint32_t p0 = lane * QBPT;
     const uint32_t k = P.k, rep = P.rep_log2;
     surv = 0;
     rootm = 0;
-    if (p0 >= valid) return;
+    if (p0 >= valid) {
+#pragma unroll
+        for (int w = 0; w <= BPS; w++) bs[w] = 0;
+        return;
+    }
     const uint4 a = *reinterpret_cast<const uint4 *>(sb + p0);
     const uint4 b = *reinterpret_cast<const uint4 *>(sb + p0 + 16);
     const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    uint32_t bs[BPS + 1];
     pack_symbols<BPS>(x, bs);
     const uint32_t kmask = (1u << (BPS * k)) - 1u;
     const uint32_t copy = lane & ((1u << rep) - 1u);
+    // word of index i in copy `copy`: ((i >> 5) << rep) | copy, written as one
+    // shift and one mask so that the index needs no separate masking
+    const uint32_t sh = 5u - rep;
+    const uint32_t mk = (kmask >> sh) & ~((1u << rep) - 1u);
+    const uint32_t bmask = kmask < 31u ? kmask : 31u;
 #pragma unroll
     for (int j = 0; j < QBPT; j++) {
-        const uint32_t idx = symbols_at<BPS>(bs, j) & kmask;
-        const uint32_t w = Fs[((idx >> 5) << rep) | copy];
-        surv |= ((w >> (idx & 31)) & 1u) << j;
+        const uint32_t t = symbols_at<BPS>(bs, j);
+        const uint32_t w = Fs[((t >> sh) & mk) | copy];
+        surv |= (__funnelshift_r(w, w, t & bmask) & 1u) << j;
     }
     // positions whose k-symbol window is available in this segment and stage
     const uint32_t lim0 = lima < staged ? lima : staged;
@@ -288,12 +369,51 @@ __device__ __forceinline__ uint32_t lim_of(const MatchParams &P, uint32_t p, uin
     return r < rem ? (uint32_t)r : rem;
 }
 
-// Prefix index of position p from the staged bytes (survivors only).
+// Symbols j.. of the lane's packed bit string for a run-time j (survivors
+// only): the words it can start in are few, so a select chain replaces an
+// indexed register access.
 template <int BPS>
-__device__ __forceinline__ uint32_t index_at(const uint8_t *sb, uint32_t p, uint32_t k) {
-    uint32_t x = 0;
-    for (uint32_t i = 0; i < k; i++) x |= ((uint32_t)sb[p + i] & ((1u << BPS) - 1u)) << (BPS * i);
-    return x;
+__device__ __forceinline__ uint32_t symbols_dyn(const uint32_t (&bs)[BPS + 1], uint32_t j) {
+    constexpr int WMAX = (15 * BPS) >> 5;
+    const uint32_t bit = BPS * j, w = bit >> 5;
+    uint32_t lo = bs[0], hi = bs[1];
+#pragma unroll
+    for (int i = 1; i <= WMAX; i++)
+        if (w == (uint32_t)i) {
+            lo = bs[i];
+            hi = bs[i + 1];
+        }
+    return __funnelshift_r(lo, hi, bit & 31);
+}
+
+// Second on-chip stage: a survivor whose depth-k state reports nothing and
+// has no child on the next symbol (the entry's child mask, M_k) stops there
+// silently; it is dropped before it reaches the queue.  The next symbol is
+// read from the staged slice while it is still there.
+template <int BPS>
+__device__ __forceinline__ uint32_t child_mask_test(const MatchParams &P, uint32_t surv,
+                                                    const uint32_t (&bs)[BPS + 1],
+                                                    const uint8_t *sb, uint32_t staged,
+                                                    uint32_t lima, uint32_t limb,
+                                                    bool general_lims, uint64_t ustart,
+                                                    uint32_t rem, const uint32_t *Fs,
+                                                    const uint32_t *Cs, const uint32_t *Ms,
+                                                    uint32_t lane) {
+    const uint32_t p0 = lane * QBPT, k = P.k, sigma = P.T.sigma;
+    const uint32_t kmask = (1u << (BPS * k)) - 1u;
+    uint32_t m = surv, keep = surv;
+    while (m) {
+        const uint32_t j = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t q = p0 + j + k;
+        const uint32_t lj = general_lims ? lim_of(P, p0 + j, lima, limb, true, ustart, rem)
+                                         : ((p0 + j) < lima ? lima : limb);
+        if (q >= staged || q >= lj) continue;  // next symbol not at hand: keep
+        const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, symbols_dyn<BPS>(bs, j) & kmask);
+        const uint32_t c = sb[q];
+        if (c >= sigma || !((Ms[r] >> child_hash(c, sigma)) & 1u)) keep &= ~(1u << j);
+    }
+    return keep;
 }
 
 // Appends the survivors of lanes whose bit is set in `lanes` to the queue at
@@ -301,11 +421,12 @@ __device__ __forceinline__ uint32_t index_at(const uint8_t *sb, uint32_t p, uint
 template <int BPS>
 __device__ __forceinline__ uint32_t append_survivors(const MatchParams &P, QEntry *q, uint32_t qn,
                                                      uint32_t surv, uint32_t rootm, uint32_t lanes,
-                                                     const uint8_t *sb, uint32_t unit,
+                                                     const uint32_t (&bs)[BPS + 1], uint32_t unit,
                                                      uint32_t lima, uint32_t limb,
                                                      bool general_lims, uint64_t ustart,
                                                      uint32_t rem, uint32_t lane,
-                                                     uint32_t slot_base) {
+                                                     uint32_t slot_base, const uint32_t *Fs,
+                                                     const uint32_t *Cs) {
     uint32_t m = ((lanes >> lane) & 1u) ? (surv | rootm) : 0u;
     const uint32_t c = __popc(m);
     uint32_t inc = c;
@@ -317,6 +438,7 @@ __device__ __forceinline__ uint32_t append_survivors(const MatchParams &P, QEntr
     const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
     uint32_t o = inc - c;
     const uint32_t p0 = lane * QBPT;
+    const uint32_t kmask = (1u << (BPS * P.k)) - 1u;
     while (m) {
         const uint32_t j = __ffs(m) - 1;
         m &= m - 1;
@@ -324,7 +446,8 @@ __device__ __forceinline__ uint32_t append_survivors(const MatchParams &P, QEntr
         QEntry en;
         en.unit = unit;
         en.pos = p | ((slot_base + o) << 10) | (tot << 18);
-        en.x = ((rootm >> j) & 1u) ? ROOT_X : index_at<BPS>(sb, p, P.k);
+        en.x = ((rootm >> j) & 1u) ? ROOT_X
+                                   : prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, symbols_dyn<BPS>(bs, j) & kmask);
         en.lim = lim_of(P, p, lima, limb, general_lims, ustart, rem);
         q[qn + o] = en;
         o++;
@@ -343,8 +466,21 @@ __device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, u
                                               const uint32_t *Fs, const uint32_t *Cs,
                                               const uint32_t *Es, uint32_t lane) {
     if (n == 0) return;
+    resolve_batch<W, VAR>(P, q, n, Fs, Cs, Es, lane);
     uint32_t fin[QU], pos[QU], unit[QU];
-    resolve_batch<W, VAR>(P, q, n, Fs, Cs, Es, lane, fin, pos, unit);
+#pragma unroll
+    for (int u = 0; u < QU; u++) {
+        const uint32_t e = lane + 32u * u;
+        unit[u] = 0xFFFFFFFFu;
+        fin[u] = 0;
+        pos[u] = 0;
+        if (e < n) {
+            unit[u] = q[e].unit;
+            pos[u] = q[e].pos;
+            fin[u] = q[e].x;
+        }
+    }
+    __syncwarp();
     // exclusive count of matched entries before each entry of the batch
     uint32_t pre[QU], carry = 0;
     const uint32_t lt = (1u << lane) - 1u;
@@ -389,7 +525,7 @@ __device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, u
 // writes the slice's keys at key_off[unit] and returns the count.
 template <int W, int BPS, int VAR>
 __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *q, uint32_t surv,
-                                                  uint32_t rootm, const uint8_t *sb,
+                                                  uint32_t rootm, const uint32_t (&bs)[BPS + 1],
                                                   uint32_t unitid, uint32_t lima, uint32_t limb,
                                                   bool general_lims, uint64_t ustart,
                                                   uint32_t rem, const uint32_t *Fs,
@@ -398,12 +534,19 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
     uint64_t keys = 0;
     const uint64_t obase = emit ? P.key_off[unitid] : 0;
     for (int qt = 0; qt < 4; qt++) {
-        const uint32_t n = append_survivors<BPS>(P, q, 0, surv, rootm, 0xFFu << (8 * qt), sb,
+        const uint32_t n = append_survivors<BPS>(P, q, 0, surv, rootm, 0xFFu << (8 * qt), bs,
                                                  unitid, lima, limb, general_lims, ustart, rem,
-                                                 lane, 0);
+                                                 lane, 0, Fs, Cs);
         if (n == 0) continue;
-        uint32_t fin[QU], pos[QU], unit[QU];
-        resolve_batch<W, VAR>(P, q, n, Fs, Cs, Es, lane, fin, pos, unit);
+        resolve_batch<W, VAR>(P, q, n, Fs, Cs, Es, lane);
+        uint32_t fin[QU], pos[QU];
+#pragma unroll
+        for (int u = 0; u < QU; u++) {
+            const uint32_t e = lane + 32u * u;
+            fin[u] = e < n ? q[e].x : 0u;
+            pos[u] = e < n ? q[e].pos : 0u;
+        }
+        __syncwarp();
 #pragma unroll
         for (int u = 0; u < QU; u++) {
             const uint32_t L = fin[u] ? fin_len(P.T.pool, fin[u]) : 0u;
@@ -439,14 +582,17 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
     uint32_t *Fs = reinterpret_cast<uint32_t *>(smem);
     uint32_t *Cs = Fs + P.tbl_words;
     uint32_t *Es = Cs + P.tbl_c_words;
+    uint32_t *Ms = Es + P.tbl_e_words;
     WarpArea *areas = reinterpret_cast<WarpArea *>(
-        smem + ((((size_t)P.tbl_words + P.tbl_c_words + P.tbl_e_words) * 4 + 127) & ~(size_t)127));
+        smem + ((((size_t)P.tbl_words + P.tbl_c_words + P.tbl_e_words + P.tbl_m_words) * 4 + 127) &
+                ~(size_t)127));
     {
         const uint32_t rep = P.rep_log2;
         for (uint32_t i = threadIdx.x; i < P.tbl_words; i += QTHREADS) Fs[i] = __ldg(P.F + (i >> rep));
         for (uint32_t i = threadIdx.x; i < P.tbl_c_words; i += QTHREADS) Cs[i] = __ldg(P.C + i);
         if (VAR == VAR_FE)
             for (uint32_t i = threadIdx.x; i < P.tbl_e_words; i += QTHREADS) Es[i] = __ldg(P.E + i);
+        for (uint32_t i = threadIdx.x; i < P.tbl_m_words; i += QTHREADS) Ms[i] = __ldg(P.M + i);
     }
     WarpArea &A = areas[warp];
     if (lane == 0) {
@@ -531,19 +677,22 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
             break;
         }
         const uint8_t *sb = A.ring[s];
-        uint32_t surv, rootm;
+        uint32_t surv, rootm, bs[BPS + 1];
         filter_slice<BPS>(P, sb, staged, valid, rem, lima, limb, general_lims, P.seg, ustart, Fs,
-                          lane, surv, rootm);
+                          lane, surv, rootm, bs);
+        if (P.tbl_m_words)
+            surv = child_mask_test<BPS>(P, surv, bs, sb, staged, lima, limb, general_lims, ustart,
+                                        rem, Fs, Cs, Ms, lane);
         const uint32_t cnt = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(surv | rootm));
 
         if (emit) {
-            resolve_slice<W, BPS, VAR>(P, A.q, surv, rootm, sb, u, lima, limb, general_lims,
+            resolve_slice<W, BPS, VAR>(P, A.q, surv, rootm, bs, u, lima, limb, general_lims,
                                        ustart, rem, Fs, Cs, Es, lane, true);
         } else if (cnt > (uint32_t)QCAP) {
             // too many survivors to queue: count now, emit later
             flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
             qn = 0;
-            const uint64_t keys = resolve_slice<W, BPS, VAR>(P, A.q, surv, rootm, sb, u, lima,
+            const uint64_t keys = resolve_slice<W, BPS, VAR>(P, A.q, surv, rootm, bs, u, lima,
                                                              limb, general_lims, ustart, rem, Fs,
                                                              Cs, Es, lane, false);
             if (lane == 0) {
@@ -562,16 +711,13 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
                     flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
                     qn = 0;
                 }
-                qn += append_survivors<BPS>(P, A.q, qn, surv, rootm, 0xFFFFFFFFu, sb, u, lima,
-                                            limb, general_lims, ustart, rem, lane, 0);
+                qn += append_survivors<BPS>(P, A.q, qn, surv, rootm, 0xFFFFFFFFu, bs, u, lima,
+                                            limb, general_lims, ustart, rem, lane, 0, Fs, Cs);
             }
         }
         // the stage is consumed: refill it with the unit QRING ahead
         __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            issue(i + QRING);
-        }
+        if (lane == 0) issue(i + QRING);  // every lane's reads of the stage are done
         __syncwarp();
     }
     if (!failed && !emit) flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
 struct Plan {
     int var;
     uint32_t k;
-    uint32_t tbl_words, tbl_c_words, tbl_e_words;
+    uint32_t tbl_words, tbl_c_words, tbl_e_words, tbl_m_words;
     uint32_t rep_log2;
     uint32_t dense_rows;
     uint32_t unit_shift, unit_cap;
@@ -307,8 +307,8 @@ static size_t dense_smem(uint32_t tbl_words) {
 
 constexpr size_t SMEM_LIMIT = 232448;  // per-CTA dynamic shared memory on sm_103a
 
-static size_t queued_smem(uint32_t w, uint32_t cw, uint32_t ew) {
-    const size_t tbl = (((size_t)w + cw + ew) * 4 + 127) & ~(size_t)127;
+static size_t queued_smem(uint32_t w, uint32_t cw, uint32_t ew, uint32_t mw) {
+    const size_t tbl = (((size_t)w + cw + ew + mw) * 4 + 127) & ~(size_t)127;
     return tbl + QW * sizeof(WarpArea);
 }
 
@@ -335,25 +335,32 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                          k, t->kmin, t->kmax);
     const uint64_t ent = 1ull << (k * T.bps);
     const uint32_t fw = (uint32_t)(ent >= 32 ? ent / 32 : 1);
-    const uint32_t cw = (fw + 7) / 8;
+    const uint32_t cw = (fw + (1u << T.c_shift[k]) - 1) >> T.c_shift[k];
     const uint32_t ew = T.n_e[k];
     int var = opts && opts->variant ? (int)opts->variant
                                     : (t->tuned_variant ? (int)t->tuned_variant : 0);
+    // the table's tuned choice applies only when the caller picks neither the
+    // variant nor the depth
+    const bool use_tuned = !(opts && (opts->variant || opts->prefix_depth));
+    const uint32_t masks = opts && opts->child_masks ? opts->child_masks
+                                                    : (use_tuned ? t->tuned_masks : 0u);
+    if (masks > 2) return set_error(PFAC_EINVAL, "pfac_match: child_masks %u", masks);
     // largest power-of-two bitmap replication that fits next to the rest
     auto best_rep = [&](uint32_t extra) -> int {
         int rep = -1;
         for (int r = 0; r <= 5; r++)
-            if (queued_smem((uint32_t)((uint64_t)fw << r), cw, extra) <= SMEM_LIMIT) rep = r;
+            if (queued_smem((uint32_t)((uint64_t)fw << r), cw, extra, 0) <= SMEM_LIMIT) rep = r;
         return rep;
     };
     const int rep_f = best_rep(0), rep_fe = best_rep(ew);
     if (var == 0) var = (rep_fe >= 0 && rep_fe >= rep_f - 1) ? VAR_FE : VAR_F;
-    int rep = var == VAR_FE ? rep_fe : rep_f;
     if (var != VAR_F && var != VAR_FE)
         return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
-    // the table's tuned choice applies only when the caller picks neither the
-    // variant nor the depth
-    const bool use_tuned = !(opts && (opts->variant || opts->prefix_depth));
+    const uint32_t e_sm = var == VAR_FE ? ew : 0u;
+    // child masks: with them if they fit (or on request), then the most copies
+    const int rep_m = best_rep(e_sm + ew);
+    const bool use_m = masks == 2 || (masks == 0 && rep_m >= 0);
+    int rep = best_rep(e_sm + (use_m ? ew : 0u));
     const uint32_t copies = opts && opts->bitmap_copies ? opts->bitmap_copies
                                                        : (use_tuned ? t->tuned_copies : 0u);
     if (copies) {
@@ -368,15 +375,16 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     }
     if (rep < 0)
         return set_error(PFAC_EINVAL, "pfac_match: prefix node of depth %u does not fit in "
-                         "shared memory with variant %d", k, var);
+                         "shared memory with variant %d%s", k, var, use_m ? " and child masks" : "");
     pl->var = var;
     pl->k = k;
     pl->rep_log2 = (uint32_t)rep;
     pl->tbl_words = (uint32_t)((uint64_t)fw << rep);
     pl->tbl_c_words = cw;
-    pl->tbl_e_words = var == VAR_FE ? ew : 0;
+    pl->tbl_e_words = e_sm;
+    pl->tbl_m_words = use_m ? ew : 0u;
     pl->kernel = scan_kernel_for(T.bps, var);
-    pl->smem = queued_smem(pl->tbl_words, pl->tbl_c_words, pl->tbl_e_words);
+    pl->smem = queued_smem(pl->tbl_words, pl->tbl_c_words, pl->tbl_e_words, pl->tbl_m_words);
     pl->unit_shift = SLICE_SHIFT;
     pl->unit_cap = SCAP;
     pl->queued = true;
@@ -484,6 +492,9 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.F = pl.k ? t->dev.F[pl.k] : nullptr;
     P.C = pl.k ? t->dev.C[pl.k] : nullptr;
     P.E = pl.k ? t->dev.E[pl.k] : nullptr;
+    P.M = pl.k ? t->dev.M[pl.k] : nullptr;
+    P.c_shift = pl.k ? t->dev.c_shift[pl.k] : 0u;
+    P.tbl_m_words = pl.tbl_m_words;
     P.tbl_words = pl.tbl_words;
     P.tbl_c_words = pl.tbl_c_words;
     P.tbl_e_words = pl.tbl_e_words;

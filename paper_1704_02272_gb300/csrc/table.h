@@ -21,9 +21,13 @@
 //     bitmap F_k marks the indices whose walk does something (reaches depth k
 //     or stops after a final); like a node record, its children are addressed
 //     by popcount rank (Eq. 1): C_k holds the count of set bits before each
-//     256-bit block and E_k the entries of the set bits in index order.  An
+//     word (small bitmaps) or each 8 words, and E_k the entries of the set
+//     bits in index order.  An
 //     entry is D_CONT | record of the depth-k state, or the fin of the state
-//     where a shorter walk stopped.
+//     where a shorter walk stopped.  M_k holds per entry a 32-bit mask of the
+//     hashed symbols (child_hash) the depth-k state has children on, or all
+//     ones when the entry itself reports output: a survivor whose next symbol
+//     misses the mask stops silently without visiting the records.
 //
 // Dense layout (uncompressed PFAC): stt[s * sigma + c] = child or 0 (the root
 // is never a child), dfin[s] = fin(s).
@@ -51,6 +55,11 @@ constexpr uint32_t FIN_MAX_OFF = (1u << (31 - FIN_LEN_BITS)) - 1;
 //           words before each word, one byte per word)
 __host__ __device__ constexpr int rec_words(int W) { return W == 1 ? 2 : (W == 2 ? 4 : 12); }
 
+// Bit of symbol c in a child mask: exact for alphabets of up to 32 symbols.
+__host__ __device__ inline uint32_t child_hash(uint32_t c, uint32_t sigma) {
+    return sigma <= 32 ? c : ((c ^ (c >> 5)) & 31u);
+}
+
 struct DevTable {
     uint32_t sigma;
     uint32_t W;           // 1, 2 or 8 (bitmap words per record)
@@ -66,8 +75,10 @@ struct DevTable {
     const uint32_t *leaf_fin;
     const uint32_t *pool;
     const uint32_t *F[KMAX + 1];   // prefix bitmap of depth k
-    const uint32_t *C[KMAX + 1];   // set bits before each 256-bit block of F_k
+    const uint32_t *C[KMAX + 1];   // set bits of F_k before each group of 2^c_shift words
+    uint32_t c_shift[KMAX + 1];    // 0 (a count per word) or 3 (per 8 words)
     const uint32_t *E[KMAX + 1];   // entries of the set bits of F_k
+    const uint32_t *M[KMAX + 1];   // per entry: hashed symbols its state continues with
     uint32_t n_e[KMAX + 1];        // number of entries of depth k
     const uint32_t *stt;      // dense layout
     const uint32_t *dfin;

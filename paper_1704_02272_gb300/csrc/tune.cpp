@@ -36,19 +36,20 @@ std::string cache_key(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments
 }
 
 bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_t *k,
-                  uint32_t *c, float *ms) {
+                  uint32_t *c, uint32_t *mk, float *ms) {
     FILE *f = fopen(path, "r");
     if (!f) return false;
     char line[512];
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char kbuf[300];
-        uint32_t a, b, d;
+        uint32_t a, b, d, g;
         float e;
-        if (sscanf(line, "%299s %u %u %u %f", kbuf, &a, &b, &d, &e) == 5 && key == kbuf) {
+        if (sscanf(line, "%299s %u %u %u %u %f", kbuf, &a, &b, &d, &g, &e) == 6 && key == kbuf) {
             *v = a;
             *k = b;
             *c = d;
+            *mk = g;
             *ms = e;
             found = true;  // the last line for a key wins
         }
@@ -70,15 +71,17 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     memset(&res, 0, sizeof res);
     const std::string key = cache_key(t, n_bytes, n_segments);
     if (cache_path) {
-        uint32_t v, k, c;
+        uint32_t v, k, c, mk;
         float ms;
-        if (cache_lookup(cache_path, key, &v, &k, &c, &ms) && k >= t->kmin && k <= t->kmax) {
+        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &ms) && k >= t->kmin && k <= t->kmax) {
             t->tuned_variant = v;
             t->tuned_k = k;
             t->tuned_copies = c;
+            t->tuned_masks = mk;
             res.variant = v;
             res.prefix_depth = k;
             res.bitmap_copies = c;
+            res.child_masks = mk;
             res.scan_ms = ms;
             res.from_cache = 1;
             if (out) *out = res;
@@ -87,17 +90,19 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // forget an earlier choice so the default is measured as the library's own
-    t->tuned_variant = t->tuned_k = t->tuned_copies = 0;
+    t->tuned_variant = t->tuned_k = t->tuned_copies = t->tuned_masks = 0;
 
     struct Cand {
-        uint32_t var, k, copies;
+        uint32_t var, k, copies, masks;
         float ms;
     };
     std::vector<Cand> cands;
-    cands.push_back({0, 0, 0, 0.f});  // library default
+    cands.push_back({0, 0, 0, 0, 0.f});  // library default
     for (uint32_t k = t->kmin; k <= t->kmax; k++)
         for (uint32_t var = 1; var <= 2; var++)
-            for (uint32_t copies = 32; copies >= 1; copies >>= 1) cands.push_back({var, k, copies, 0.f});
+            for (uint32_t masks = 1; masks <= 2; masks++)
+                for (uint32_t copies = 32; copies >= 1; copies >>= 1)
+                    cands.push_back({var, k, copies, masks, 0.f});
 
     uint64_t ws_max = 0;
     std::vector<Cand> ok;
@@ -107,6 +112,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.variant = c.var;
         o.prefix_depth = c.k;
         o.bitmap_copies = c.copies;
+        o.child_masks = c.masks;
         uint64_t b = 0;
         if (pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b) != PFAC_OK) continue;
         ws_max = std::max(ws_max, b);
@@ -135,6 +141,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.variant = c.var;
         o.prefix_depth = c.k;
         o.bitmap_copies = c.copies;
+        o.child_masks = c.masks;
         uint64_t b = 0;
         pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b);
         // warm-up, then the median of three timed scans
@@ -184,15 +191,18 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         t->tuned_variant = best.var;
         t->tuned_k = best.k;
         t->tuned_copies = best.copies;
+        t->tuned_masks = best.masks;
     }
     res.variant = best.var;
     res.prefix_depth = best.k;
     res.bitmap_copies = best.copies;
+    res.child_masks = best.masks;
     res.scan_ms = best.ms;
     if (cache_path && best.var) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s %u %u %u %.6f\n", key.c_str(), best.var, best.k, best.copies, best.ms);
+            fprintf(f, "%s %u %u %u %u %.6f\n", key.c_str(), best.var, best.k, best.copies,
+                    best.masks, best.ms);
             fclose(f);
         }
     }
