@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
-SCAN_KERNELS_PER_STEP = 5  # k_scan, k_reduce, k_offsets, k_scan (overflow re-scan), k_expand
+SCAN_KERNELS_PER_STEP = 5  # scan, key-count reduce, offsets, overflow re-scan, key expansion
 
 
 def peaks():
@@ -358,19 +358,19 @@ def run_ours(args):
 
     hbm_peak, peak_kind = peaks()
     matched_frac = None
-    # algorithmic bytes of one scan launch: every input byte once, the 16-byte
-    # halo of each 8 KiB tile, and one 8-byte record per matched position
+    # algorithmic bytes of one scan launch: every input byte read once and one
+    # 8-byte record per matched position written (the 16-byte halo of each
+    # 512-byte slice is re-read from L2 and not counted)
     pos = keys >> 24
     matched_positions = int(torch.unique_consecutive(pos).numel()) if n_match else 0
     matched_frac = matched_positions / N
-    tiles = (N + 8191) // 8192
-    alg_bytes = N + 16 * tiles + 8 * matched_positions
+    alg_bytes = N + 8 * matched_positions
     scan_avg_ms = sum(scan_ms) / K
     achieved = alg_bytes / (scan_avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                 "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": args.traffic, "kernel": "k_scan",
+                "traffic": args.traffic, "kernel": "k_scanq (compressed-table scan)",
                 "alg_bytes_per_launch": alg_bytes}
 
     line = {

@@ -46,7 +46,7 @@ constexpr uint32_t LIM_MAX = 0xFFFFFFF0u;
 
 struct QEntry {
     uint32_t unit;
-    uint32_t pos;   // position in the slice | slot << 10 | survivors of the slice << 18
+    uint32_t pos;   // position in the slice | slot << 10 | LAST_FLAG on the slice's last
     uint32_t x;     // prefix index, or ROOT_X
     uint32_t lim;   // walk limit relative to the slice start
 };
@@ -161,7 +161,7 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                 state[u] = 0;
                 qq[u] = p;
             } else {
-                const uint32_t r = en.x;  // rank of the prefix index among F_k's set bits
+                const uint32_t r = prefix_rank(Fs, rep, Cs, P.c_shift, en.x);
                 const uint32_t ev = VAR == VAR_FE ? Es[r] : __ldg(P.E + r);
                 qq[u] = p + k;
                 if (ev & D_CONT) {
@@ -241,19 +241,45 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
             uint32_t s1 = en.x;
             const uint64_t ub = (uint64_t)en.unit << SLICE_SHIFT;
             uint32_t f = 0;
-            for (;;) {
-                const uint32_t c = q1 < en.lim ? (uint32_t)__ldg(P.in + ub + q1) : 0x100u;
-                uint32_t wd, bl, mt, f1;
-                load_step<W>(rec, s1, c, wd, bl, mt, f1);
-                const uint32_t cur = s1;
-                const int r = take_step(sigma, c, wd, bl, mt, s1);
-                if (r == 0) {
-                    q1++;
-                    continue;
+            // Each round fetches TS consecutive records from the current state
+            // and the next TS symbols; along a single-child chain (placed in
+            // consecutive records) a round advances up to TS levels.
+            constexpr int TS = W == 8 ? 4 : 8;
+            const uint32_t n_rec = P.T.n_rec;
+            bool done = false;
+            while (!done) {
+                uint32_t c[TS], wd[TS], bl[TS], mt[TS], f1[TS];
+#pragma unroll
+                for (int i = 0; i < TS; i++) {
+                    c[i] = q1 + i < en.lim ? (uint32_t)__ldg(P.in + ub + q1 + i) : 0x100u;
+                    if (i == 0 || s1 + i < n_rec) {
+                        load_step<W>(rec, s1 + i, c[i], wd[i], bl[i], mt[i], f1[i]);
+                    } else {
+                        wd[i] = bl[i] = mt[i] = f1[i] = 0;
+                    }
                 }
-                if (r == 1) f = W == 1 ? __ldg(P.T.fin + cur) : f1;
-                else f = __ldg(P.T.leaf_fin + s1);
-                break;
+#pragma unroll
+                for (int i = 0; i < TS; i++) {
+                    // state s1 + i holds the data of block entry i while the
+                    // walk stays on the consecutive chain
+                    uint32_t nx = 0;
+                    const uint32_t cur = s1 + i;
+                    const int r = take_step(sigma, c[i], wd[i], bl[i], mt[i], nx);
+                    if (r == 1) {
+                        f = W == 1 ? __ldg(P.T.fin + cur) : f1[i];
+                        done = true;
+                        break;
+                    }
+                    if (r == 2) {
+                        f = __ldg(P.T.leaf_fin + nx);
+                        done = true;
+                        break;
+                    }
+                    if (i + 1 < TS && nx == cur + 1) continue;
+                    s1 = nx;
+                    q1 += i + 1;
+                    break;
+                }
             }
             q[e].x = f;
         }
@@ -386,49 +412,91 @@ __device__ __forceinline__ uint32_t symbols_dyn(const uint32_t (&bs)[BPS + 1], u
     return __funnelshift_r(lo, hi, bit & 31);
 }
 
-// Second on-chip stage: a survivor whose depth-k state reports nothing and
-// has no child on the next symbol (the entry's child mask, M_k) stops there
-// silently; it is dropped before it reaches the queue.  The next symbol is
-// read from the staged slice while it is still there.
-template <int BPS>
-__device__ __forceinline__ uint32_t child_mask_test(const MatchParams &P, uint32_t surv,
-                                                    const uint32_t (&bs)[BPS + 1],
-                                                    const uint8_t *sb, uint32_t staged,
-                                                    uint32_t lima, uint32_t limb,
-                                                    bool general_lims, uint64_t ustart,
-                                                    uint32_t rem, const uint32_t *Fs,
-                                                    const uint32_t *Cs, const uint32_t *Ms,
-                                                    uint32_t lane) {
-    const uint32_t p0 = lane * QBPT, k = P.k, sigma = P.T.sigma;
-    const uint32_t kmask = (1u << (BPS * k)) - 1u;
-    uint32_t m = surv, keep = surv;
-    while (m) {
-        const uint32_t j = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t q = p0 + j + k;
-        const uint32_t lj = general_lims ? lim_of(P, p0 + j, lima, limb, true, ustart, rem)
-                                         : ((p0 + j) < lima ? lima : limb);
-        if (q >= staged || q >= lj) continue;  // next symbol not at hand: keep
-        const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, symbols_dyn<BPS>(bs, j) & kmask);
-        const uint32_t c = sb[q];
-        if (c >= sigma || !((Ms[r] >> child_hash(c, sigma)) & 1u)) keep &= ~(1u << j);
-    }
-    return keep;
+// Second on-chip stage for one survivor: with child masks, a survivor whose
+// depth-k state reports nothing and has no child on the next symbol (read
+// from the staged slice) stops there silently and is dropped.  An entry that
+// reports output has an all-ones mask and is kept whatever follows; a byte
+// outside the alphabet ends every other walk.  A survivor whose next symbol
+// is not at hand is kept.
+__device__ __forceinline__ bool mask_keep(const MatchParams &P, uint32_t x, uint32_t p,
+                                          uint32_t lim, const uint8_t *sb, uint32_t staged,
+                                          const uint32_t *Fs, const uint32_t *Cs,
+                                          const uint32_t *Ms) {
+    const uint32_t qn1 = p + P.k, sigma = P.T.sigma;
+    if (qn1 >= staged || qn1 >= lim) return true;
+    const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, x);
+    const uint32_t cs = sb[qn1], mr = Ms[r];
+    return cs < sigma ? ((mr >> child_hash(cs, sigma)) & 1u) != 0 : mr == 0xFFFFFFFFu;
 }
 
-// Appends the survivors of lanes whose bit is set in `lanes` to the queue at
-// qn, in position order.  Returns the number appended (warp-uniform).
+// Appends the survivors of the lanes set in `lanes` to the queue at qn, in
+// position order, after the second on-chip stage (mask_keep).  Entry fields:
+// the slice, the position, the slot among the slice's appended survivors
+// and, on the last one, LAST_FLAG; the prefix index (or ROOT_X); the walk
+// limit.  Sparse slices (at most two candidates per lane) are handled by
+// each lane for its own candidates; denser ones are dealt out one per lane
+// (candidate i of each group of 32 to lane i, which finds the owning lane by
+// a shuffle search over the lanes' exclusive counts and the position in
+// that lane's mask by __fns), so the work runs 32 wide.
+// Returns the number appended, or cap + 1 (nothing kept) when more than
+// `cap` survive.
+constexpr uint32_t LAST_FLAG = 0x80000000u;
+
 template <int BPS>
-__device__ __forceinline__ uint32_t append_survivors(const MatchParams &P, QEntry *q, uint32_t qn,
-                                                     uint32_t surv, uint32_t rootm, uint32_t lanes,
-                                                     const uint32_t (&bs)[BPS + 1], uint32_t unit,
-                                                     uint32_t lima, uint32_t limb,
-                                                     bool general_lims, uint64_t ustart,
-                                                     uint32_t rem, uint32_t lane,
-                                                     uint32_t slot_base, const uint32_t *Fs,
-                                                     const uint32_t *Cs) {
-    uint32_t m = ((lanes >> lane) & 1u) ? (surv | rootm) : 0u;
+__device__ __forceinline__ uint32_t gather_append(const MatchParams &P, QEntry *q, uint32_t qn,
+                                                  uint32_t cap, uint32_t cand, uint32_t rootm,
+                                                  uint32_t lanes, const uint32_t (&bs)[BPS + 1],
+                                                  const uint8_t *sb, uint32_t staged,
+                                                  uint32_t unit, uint32_t lima, uint32_t limb,
+                                                  bool general_lims, uint64_t ustart,
+                                                  uint32_t rem, const uint32_t *Fs,
+                                                  const uint32_t *Cs, const uint32_t *Ms,
+                                                  uint32_t lane) {
+    const uint32_t m = ((lanes >> lane) & 1u) ? cand : 0u;
     const uint32_t c = __popc(m);
+    const uint32_t kmask = (1u << (BPS * P.k)) - 1u;
+    const bool masks = P.tbl_m_words != 0;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t p0 = lane * QBPT;
+
+    if (__reduce_max_sync(0xFFFFFFFFu, c) <= 2u) {
+        // per lane: second stage on the lane's own candidates, then a
+        // warp-wide rank of the kept ones
+        uint32_t keepm = m;
+        if (masks) {
+            uint32_t mm = m & ~rootm;
+            while (mm) {
+                const uint32_t j = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const uint32_t p = p0 + j;
+                const uint32_t lim = lim_of(P, p, lima, limb, general_lims, ustart, rem);
+                if (!mask_keep(P, symbols_dyn<BPS>(bs, j) & kmask, p, lim, sb, staged, Fs, Cs, Ms))
+                    keepm &= ~(1u << j);
+            }
+        }
+        const uint32_t kc = __popc(keepm);
+        const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, kc >= 1u);
+        const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, kc >= 2u);
+        const uint32_t tot = __popc(b1) + __popc(b2);
+        if (tot > cap) return cap + 1;
+        uint32_t o = __popc(b1 & lt) + __popc(b2 & lt);
+        uint32_t mm = keepm;
+        while (mm) {
+            const uint32_t j = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t p = p0 + j;
+            QEntry en;
+            en.unit = unit;
+            en.pos = p | (o << 10) | (o + 1 == tot ? LAST_FLAG : 0u);
+            en.x = ((rootm >> j) & 1u) ? ROOT_X : (symbols_dyn<BPS>(bs, j) & kmask);
+            en.lim = lim_of(P, p, lima, limb, general_lims, ustart, rem);
+            q[qn + o] = en;
+            o++;
+        }
+        __syncwarp();
+        return tot;
+    }
+
     uint32_t inc = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -436,24 +504,62 @@ __device__ __forceinline__ uint32_t append_survivors(const MatchParams &P, QEntr
         if (lane >= (uint32_t)o) inc += nb;
     }
     const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-    uint32_t o = inc - c;
-    const uint32_t p0 = lane * QBPT;
-    const uint32_t kmask = (1u << (BPS * P.k)) - 1u;
-    while (m) {
-        const uint32_t j = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t p = p0 + j;
-        QEntry en;
-        en.unit = unit;
-        en.pos = p | ((slot_base + o) << 10) | (tot << 18);
-        en.x = ((rootm >> j) & 1u) ? ROOT_X
-                                   : prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, symbols_dyn<BPS>(bs, j) & kmask);
-        en.lim = lim_of(P, p, lima, limb, general_lims, ustart, rem);
-        q[qn + o] = en;
-        o++;
+    const uint32_t excl = inc - c;
+    uint32_t kept = 0;
+    bool flagged = false;  // the last kept entry carries LAST_FLAG
+    for (uint32_t base = 0; base < tot; base += 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < tot;
+        // owner: the last lane whose exclusive count is <= i
+        uint32_t L = 0;
+#pragma unroll
+        for (int st = 16; st >= 1; st >>= 1) {
+            const uint32_t v = __shfl_sync(0xFFFFFFFFu, excl, L + st);
+            if (v <= i) L += st;
+        }
+        const uint32_t exL = __shfl_sync(0xFFFFFFFFu, excl, L);
+        const uint32_t mL = __shfl_sync(0xFFFFFFFFu, m, L);
+        const uint32_t rL = __shfl_sync(0xFFFFFFFFu, rootm, L);
+        uint32_t bsL[BPS + 1];
+#pragma unroll
+        for (int w = 0; w <= BPS; w++) bsL[w] = __shfl_sync(0xFFFFFFFFu, bs[w], L);
+        const uint32_t laL = __shfl_sync(0xFFFFFFFFu, lima, L);
+        const uint32_t lbL = __shfl_sync(0xFFFFFFFFu, limb, L);
+        bool keep = false;
+        uint32_t p = 0, x = ROOT_X, lim = 0;
+        if (valid) {
+            const uint32_t j = __fns(mL, 0, (int)(i - exL) + 1);
+            p = L * QBPT + j;
+            lim = lim_of(P, p, laL, lbL, general_lims, ustart, rem);
+            keep = true;
+            if (!((rL >> j) & 1u)) {
+                x = symbols_dyn<BPS>(bsL, j) & kmask;
+                if (masks) keep = mask_keep(P, x, p, lim, sb, staged, Fs, Cs, Ms);
+            }
+        }
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
+        const uint32_t slot = kept + __popc(b & lt);
+        const uint32_t nk = kept + __popc(b);
+        if (nk > cap) return cap + 1;  // warp-uniform
+        const bool lastg = base + 32 >= tot;
+        if (keep) {
+            QEntry en;
+            en.unit = unit;
+            en.pos = p | (slot << 10) | (lastg && slot + 1 == nk ? LAST_FLAG : 0u);
+            en.x = x;
+            en.lim = lim;
+            q[qn + slot] = en;
+        }
+        if (lastg) flagged = b != 0;
+        kept = nk;
     }
     __syncwarp();
-    return tot;
+    if (kept && !flagged) {
+        // every candidate of the last group was dropped: flag the last kept one
+        if (lane == 0) q[qn + kept - 1].pos |= LAST_FLAG;
+        __syncwarp();
+    }
+    return kept;
 }
 
 // Record-mode flush: resolve the queue, then keep a record (position, fin)
@@ -498,7 +604,8 @@ __device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, u
     for (int u = 0; u < QU; u++) {
         if (unit[u] == 0xFFFFFFFFu) continue;
         const uint32_t e = lane + 32u * u;
-        const uint32_t p = pos[u] & 0x3FFu, slot = (pos[u] >> 10) & 0xFFu, cnt = pos[u] >> 18;
+        const uint32_t p = pos[u] & 0x3FFu, slot = (pos[u] >> 10) & 0xFFu;
+        const bool last = (pos[u] & LAST_FLAG) != 0;
         const uint32_t base = q[e - slot].x;
         const uint32_t rank = pre[u] - base;
         if (fin[u]) {
@@ -507,7 +614,7 @@ __device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, u
             atomicAdd((unsigned long long *)(P.tile_k + unit[u]),
                       (unsigned long long)fin_len(P.T.pool, fin[u]));
         }
-        if (slot + 1 == cnt) {
+        if (last) {
             const uint32_t m = rank + (fin[u] ? 1u : 0u);
             if (m > (uint32_t)SCAP) {
                 P.tile_m[unit[u]] = UNIT_OVF;
@@ -521,22 +628,23 @@ __device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, u
 }
 
 // Resolves every survivor of one slice in quarters of 8 lanes (at most 128
-// entries each).  emit == 0: returns the slice's key count.  emit == 1:
+// candidates each).  emit == 0: returns the slice's key count.  emit == 1:
 // writes the slice's keys at key_off[unit] and returns the count.
 template <int W, int BPS, int VAR>
-__device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *q, uint32_t surv,
+__device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *q, uint32_t cand,
                                                   uint32_t rootm, const uint32_t (&bs)[BPS + 1],
+                                                  const uint8_t *sb, uint32_t staged,
                                                   uint32_t unitid, uint32_t lima, uint32_t limb,
                                                   bool general_lims, uint64_t ustart,
                                                   uint32_t rem, const uint32_t *Fs,
                                                   const uint32_t *Cs, const uint32_t *Es,
-                                                  uint32_t lane, bool emit) {
+                                                  const uint32_t *Ms, uint32_t lane, bool emit) {
     uint64_t keys = 0;
     const uint64_t obase = emit ? P.key_off[unitid] : 0;
     for (int qt = 0; qt < 4; qt++) {
-        const uint32_t n = append_survivors<BPS>(P, q, 0, surv, rootm, 0xFFu << (8 * qt), bs,
-                                                 unitid, lima, limb, general_lims, ustart, rem,
-                                                 lane, 0, Fs, Cs);
+        const uint32_t n = gather_append<BPS>(P, q, 0, QCAP, cand, rootm, 0xFFu << (8 * qt), bs, sb,
+                                              staged, unitid, lima, limb, general_lims, ustart,
+                                              rem, Fs, Cs, Ms, lane);
         if (n == 0) continue;
         resolve_batch<W, VAR>(P, q, n, Fs, Cs, Es, lane);
         uint32_t fin[QU], pos[QU];
@@ -680,39 +788,45 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
         uint32_t surv, rootm, bs[BPS + 1];
         filter_slice<BPS>(P, sb, staged, valid, rem, lima, limb, general_lims, P.seg, ustart, Fs,
                           lane, surv, rootm, bs);
-        if (P.tbl_m_words)
-            surv = child_mask_test<BPS>(P, surv, bs, sb, staged, lima, limb, general_lims, ustart,
-                                        rem, Fs, Cs, Ms, lane);
-        const uint32_t cnt = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(surv | rootm));
+        const uint32_t cand = surv | rootm;
+        const uint32_t cnt = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(cand));
 
         if (emit) {
-            resolve_slice<W, BPS, VAR>(P, A.q, surv, rootm, bs, u, lima, limb, general_lims,
-                                       ustart, rem, Fs, Cs, Es, lane, true);
-        } else if (cnt > (uint32_t)QCAP) {
-            // too many survivors to queue: count now, emit later
-            flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
-            qn = 0;
-            const uint64_t keys = resolve_slice<W, BPS, VAR>(P, A.q, surv, rootm, bs, u, lima,
-                                                             limb, general_lims, ustart, rem, Fs,
-                                                             Cs, Es, lane, false);
-            if (lane == 0) {
-                P.tile_m[u] = UNIT_OVF;
-                P.tile_k[u] = keys;
-                P.ovf_list[atomicAdd(&P.hdr->ovf_count, 1u)] = u;
-            }
+            resolve_slice<W, BPS, VAR>(P, A.q, cand, rootm, bs, sb, staged, u, lima, limb,
+                                       general_lims, ustart, rem, Fs, Cs, Es, Ms, lane, true);
         } else {
             if (lane == 0) {
                 P.tile_m[u] = 0;  // the slice's last entry sets it when resolved
                 P.tile_k[u] = 0;
             }
             __syncwarp();
+            uint32_t got = 0;
             if (cnt) {
-                if (qn + cnt > (uint32_t)QCAP) {
+                got = gather_append<BPS>(P, A.q, qn, QCAP - qn, cand, rootm, 0xFFFFFFFFu, bs, sb,
+                                         staged, u, lima, limb, general_lims, ustart, rem, Fs, Cs,
+                                         Ms, lane);
+                if (got > (uint32_t)QCAP - qn && qn > 0) {
+                    // the queue is full: resolve it, then append again
                     flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
                     qn = 0;
+                    got = gather_append<BPS>(P, A.q, 0, QCAP, cand, rootm, 0xFFFFFFFFu, bs, sb,
+                                             staged, u, lima, limb, general_lims, ustart, rem, Fs,
+                                             Cs, Ms, lane);
                 }
-                qn += append_survivors<BPS>(P, A.q, qn, surv, rootm, 0xFFFFFFFFu, bs, u, lima,
-                                            limb, general_lims, ustart, rem, lane, 0, Fs, Cs);
+            }
+            if (got > (uint32_t)QCAP - qn) {
+                // more survivors than the queue holds: count now, emit later
+                const uint64_t keys = resolve_slice<W, BPS, VAR>(P, A.q + qn, cand, rootm, bs, sb,
+                                                                 staged, u, lima, limb,
+                                                                 general_lims, ustart, rem, Fs,
+                                                                 Cs, Es, Ms, lane, false);
+                if (lane == 0) {
+                    P.tile_m[u] = UNIT_OVF;
+                    P.tile_k[u] = keys;
+                    P.ovf_list[atomicAdd(&P.hdr->ovf_count, 1u)] = u;
+                }
+            } else {
+                qn += got;
             }
         }
         // the stage is consumed: refill it with the unit QRING ahead

@@ -54,7 +54,15 @@ CASES = [
     (108, 4, 200, 1, 8, 120_000, 40, 300, 7),      # out-of-alphabet bytes in the text
     (109, 100, 700, 1, 5, 250_000, 11, 300, None),
     (110, 256, 500, 1, 40, 100_003, 1, 300, None),  # ragged tail
+    # few patterns, so that the child masks fit: out-of-alphabet bytes right
+    # after outputs (byte >= 2^bits-per-symbol, and sigma <= byte < 2^bps)
+    (111, 4, 30, 3, 12, 200_000, 5, 600, 7),
+    (112, 5, 40, 2, 10, 200_000, 3, 600, 8),
+    (113, 20, 60, 2, 9, 200_000, 9, 600, 40),
+    # dense survivors (more than 32 per slice) that the child masks mostly drop
+    (114, 4, 5000, 9, 14, 300_000, 3, 600, None),
 ]
+MASK_CASES = CASES[-4:]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"s{c[0]}-sig{c[1]}" for c in CASES])
@@ -64,6 +72,19 @@ def test_random_cases(case):
                             text_sigma=ts)
     ref = check_all_variants(w, f"case {seed}", depths=[None, "min"])
     assert ref.size > 0
+
+
+@pytest.mark.parametrize("case", MASK_CASES, ids=[f"s{c[0]}" for c in MASK_CASES])
+def test_child_masks_forced(case):
+    # the second on-chip stage on and off must give the oracle's keys
+    seed, sigma, n, lo, hi, N, S, plants, ts = case
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, N, n_segments=S, n_plants=plants,
+                            text_sigma=ts)
+    ref = oracle_keys(w)
+    with pfac.Table(w.patterns, w.sigma, host_only=True) as th:
+        k = max(1, th.info()["prefix_depth"] - 2)  # the shallowest depth held fits with masks
+    assert_same(run(w, prefix_depth=k, child_masks=2), ref, "child masks on")
+    assert_same(run(w, prefix_depth=k, child_masks=1), ref, "child masks off")
 
 
 @pytest.mark.parametrize("seed", range(4))
