@@ -244,8 +244,11 @@ def run_ours(args):
         user_opt["bitmap_copies"] = args.copies
     if args.masks:
         user_opt["child_masks"] = args.masks
+    if args.gram:
+        user_opt["gram_filter"] = args.gram
     if args.autotune:
         tune = pfac.autotune(table, text, seg)
+    plan = pfac.plan(table, **user_opt)
     ws = torch.empty(max(pfac.workspace_bytes(table, N, S, **user_opt),
                          pfac.workspace_bytes(dense, N, S)), dtype=torch.uint8, device=dev)
 
@@ -378,9 +381,9 @@ def run_ours(args):
         "value": round(value, 3), "unit": "Gbps", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": dict(base_config(w, args), prefix_depth=args.prefix_depth or info["prefix_depth"],
+        "config": dict(base_config(w, args), prefix_depth=plan["prefix_depth"],
                        variant=args.variant or "default", bitmap_copies=args.copies or "auto",
-                       autotuned=tune if args.autotune else None,
+                       autotuned=tune if args.autotune else None, scan_plan=plan,
                        cuda_graph=bool(graph is not None)),
         "p50_ms": round(statistics.median(step_ms), 4),
         "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
@@ -495,6 +498,7 @@ def main():
     ap.add_argument("--prefix-depth", type=int, default=0)
     ap.add_argument("--copies", type=int, default=0, help="prefix-bitmap copies in smem")
     ap.add_argument("--masks", type=int, default=0, help="child masks: 1 off, 2 on")
+    ap.add_argument("--gram", type=int, default=0, help="gram filter first stage: 1 off, 2 on")
     ap.add_argument("--autotune", action="store_true", help="pfac_autotune on the input first")
     ap.add_argument("--graph", action="store_true",
                     help="time CUDA-graph replays of the match call (default for packets)")

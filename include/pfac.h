@@ -71,7 +71,9 @@ typedef struct pfac_table pfac_table;
 typedef struct {
     uint32_t layout;       /* pfac_layout */
     uint32_t prefix_depth; /* symbols resolved by the dense prefix lookup
-                              (compressed layout); 0 = chosen by the library */
+                              (compressed layout); 0 = chosen by the library;
+                              else at most 20 / b and at least 5 / b rounded
+                              up, b = bits per symbol (PFAC_EINVAL otherwise) */
     uint32_t flags;        /* PFAC_BUILD_* bits */
     uint32_t reserved[5];
 } pfac_build_opts;
@@ -97,7 +99,14 @@ typedef struct {
     uint32_t child_masks;  /* second on-chip stage (child masks of the prefix
                               entries in shared memory): 0 = when it fits,
                               1 = off, 2 = required */
-    uint32_t reserved[3];
+    uint32_t gram_filter;  /* first on-chip stage over the table's gram filter
+                              (a hashed bitmap of the g-symbol strings that
+                              start a match, g = deepest prefix depth + 1)
+                              instead of the prefix bitmap: 0 = when the
+                              library expects it to pass fewer positions,
+                              1 = off, 2 = required.  With it, bitmap_copies
+                              counts copies of the gram filter. */
+    uint32_t reserved[2];
 } pfac_match_opts;
 
 typedef struct {
@@ -115,6 +124,9 @@ typedef struct {
     uint64_t dense_bytes;      /* Q * 4 * sigma: one next state per symbol */
     uint64_t output_lists;     /* distinct sorted id lists */
     uint64_t output_list_words;
+    uint32_t gram_len;         /* g: symbols per gram-filter string (0: none) */
+    uint32_t gram_bits;        /* log2 of the gram filter's bits */
+    uint64_t gram_strings;     /* g-symbol strings whose walk does something */
 } pfac_table_info_t;
 
 /*
@@ -144,6 +156,23 @@ int pfac_build(const uint8_t *const *patterns, const uint32_t *lengths, uint32_t
  */
 int pfac_workspace_bytes(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments,
                          const pfac_match_opts *opts, uint64_t *bytes);
+
+/*
+ * pfac_match_plan - the scan configuration a pfac_match call with these
+ * options would use (no device work).  Library extension: the paper has no
+ * counterpart.  Fields are 0 for the uncompressed layout except smem_bytes.
+ */
+typedef struct {
+    uint32_t variant;        /* 1 or 2, as pfac_match_opts.variant */
+    uint32_t prefix_depth;   /* k */
+    uint32_t bitmap_copies;  /* copies of the first-stage bitmap */
+    uint32_t child_masks;    /* 1 = off, 2 = on */
+    uint32_t gram_filter;    /* 1 = off, 2 = on */
+    uint32_t gram_bits;      /* log2 of the bits of one shared copy of the gram filter */
+    uint32_t smem_bytes;     /* dynamic shared memory per CTA of the scan kernel */
+    uint32_t reserved;
+} pfac_plan_info;
+int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts, pfac_plan_info *out);
 
 /*
  * pfac_match_async - match a device-resident text (Section 2.3), fully
@@ -223,8 +252,9 @@ int pfac_match_noalloc(const pfac_table *t, const uint8_t *d_input, uint64_t n_b
 /*
  * pfac_autotune - choose the scan configuration of a table by timing it
  * (the prefix depth resolved in shared memory, whether the prefix entries
- * live in shared memory, and how many copies of the prefix bitmap are
- * spread over the shared-memory banks).  Each candidate runs the scan kernel
+ * live in shared memory, the child masks, the gram filter or the prefix
+ * bitmap as the first stage, and how many copies of that bitmap are spread
+ * over the shared-memory banks).  Each candidate runs the scan kernel
  * on the caller's device-resident sample (same argument rules as
  * pfac_match_async); the fastest becomes the table's default for later
  * pfac_match calls without options.  With a non-NULL cache_path the choice
@@ -239,6 +269,7 @@ typedef struct {
     float scan_ms;       /* scan-kernel time of the choice on the sample */
     float default_ms;    /* scan-kernel time of the library default */
     int from_cache;
+    uint32_t gram_filter; /* 1 = off, 2 = on */
 } pfac_tune_result;
 
 int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,

@@ -46,7 +46,8 @@ class MatchOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("bitmap_copies", ctypes.c_uint32),
                 ("ev_scan_begin", ctypes.c_void_p), ("ev_scan_end", ctypes.c_void_p),
-                ("child_masks", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("child_masks", ctypes.c_uint32), ("gram_filter", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class TableInfo(ctypes.Structure):
@@ -57,7 +58,8 @@ class TableInfo(ctypes.Structure):
                 ("records", ctypes.c_uint64), ("merged_leaves", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("paper_bytes", ctypes.c_uint64),
                 ("dense_bytes", ctypes.c_uint64), ("output_lists", ctypes.c_uint64),
-                ("output_list_words", ctypes.c_uint64)]
+                ("output_list_words", ctypes.c_uint64), ("gram_len", ctypes.c_uint32),
+                ("gram_bits", ctypes.c_uint32), ("gram_strings", ctypes.c_uint64)]
 
 
 class TuneResult(ctypes.Structure):
@@ -65,7 +67,14 @@ class TuneResult(ctypes.Structure):
                 ("bitmap_copies", ctypes.c_uint32), ("child_masks", ctypes.c_uint32),
                 ("n_tried", ctypes.c_uint32),
                 ("scan_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
-                ("from_cache", ctypes.c_int)]
+                ("from_cache", ctypes.c_int), ("gram_filter", ctypes.c_uint32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
+                ("bitmap_copies", ctypes.c_uint32), ("child_masks", ctypes.c_uint32),
+                ("gram_filter", ctypes.c_uint32), ("gram_bits", ctypes.c_uint32),
+                ("smem_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -94,6 +103,8 @@ def _load():
     lib.pfac_workspace_bytes.restype = ctypes.c_int
     lib.pfac_workspace_bytes.argtypes = [vp, u64, u32, ctypes.POINTER(MatchOpts),
                                          ctypes.POINTER(u64)]
+    lib.pfac_match_plan.restype = ctypes.c_int
+    lib.pfac_match_plan.argtypes = [vp, ctypes.POINTER(MatchOpts), ctypes.POINTER(PlanInfo)]
     lib.pfac_match_async.restype = ctypes.c_int
     lib.pfac_match_async.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp, vp, u64,
                                      ctypes.POINTER(MatchOpts), vp]
@@ -150,10 +161,10 @@ def _stream(stream) -> int:
 
 
 def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,
-          scan_events=None):
+          gram_filter=0, scan_events=None):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
-    o.bitmap_copies, o.child_masks = bitmap_copies, child_masks
+    o.bitmap_copies, o.child_masks, o.gram_filter = bitmap_copies, child_masks, gram_filter
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event
@@ -233,6 +244,14 @@ def workspace_bytes(table: Table, n_bytes: int, n_segments: int, **opt) -> int:
     _check(LIB.pfac_workspace_bytes(table.handle, n_bytes, n_segments, ctypes.byref(o),
                                     ctypes.byref(b)))
     return b.value
+
+
+def plan(table: Table, **opt) -> dict:
+    """pfac_match_plan: the scan configuration a match with these options uses."""
+    o = _opts(**opt)
+    r = PlanInfo()
+    _check(LIB.pfac_match_plan(table.handle, ctypes.byref(o), ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in PlanInfo._fields_ if f != "reserved"}
 
 
 def match_async(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,

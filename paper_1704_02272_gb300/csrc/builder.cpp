@@ -254,10 +254,16 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         // 2^20 bits (128 KiB), small enough for shared memory
         const uint32_t bps = bits_per_symbol(sigma);
         const uint32_t klim = std::min<uint32_t>(std::max(1u, 20 / bps), KMAX);
+        // every prefix index spans at least 5 bits, so that its low 5 bits
+        // address a bit within a 32-bit bitmap word
+        const uint32_t kfloor = (5 + bps - 1) / bps;
         if (o.prefix_depth > klim)
             return set_error(PFAC_EINVAL, "pfac_build: prefix_depth %u > %u", o.prefix_depth, klim);
+        if (o.prefix_depth && o.prefix_depth < kfloor)
+            return set_error(PFAC_EINVAL, "pfac_build: prefix_depth %u < %u for this alphabet",
+                             o.prefix_depth, kfloor);
         const uint32_t kdef = o.prefix_depth ? o.prefix_depth : klim;
-        const uint32_t kmin = kdef > 2 ? kdef - 2 : 1;
+        const uint32_t kmin = std::max(kdef > 2 ? kdef - 2 : 1u, kfloor);
         const uint32_t kmax = kdef;
         // walk the node-level trie over k symbols packed in x
         auto child_of = [&](uint32_t v, uint32_t c) -> int64_t {
@@ -343,6 +349,74 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 sz_E[k] = Ev[k].size() * 4;
                 sz_M[k] = Mv[k].size() * 4;
             }
+        // ---- gram filter over g = kmax + 1 symbols (see table.h) -----------
+        uint32_t g_len = 0, g_bits = 0;
+        uint64_t g_set = 0;
+        std::vector<uint32_t> Gv;
+        if (!dense && (kmax + 1) * bps <= 32) {
+            g_len = kmax + 1;
+            const uint32_t A = 1u << bps;  // packed symbol values (>= sigma: no child)
+            // pass 0 counts the strings, pass 1 sets their bits
+            for (int pass = 0; pass < 2; pass++) {
+                // every string x + (any symbols at depths d .. g-1)
+                auto add_all = [&](uint32_t x, uint32_t d) {
+                    const uint64_t n = 1ull << (bps * (g_len - d));
+                    if (pass == 0) {
+                        g_set += n;
+                        return;
+                    }
+                    for (uint64_t y = 0; y < n; y++) {
+                        const uint32_t h = (x | (uint32_t)(y << (bps * d))) * GRAM_MUL;
+                        Gv[gram_word(h, g_bits)] |= 1u << (h & 31);
+                    }
+                };
+                std::vector<std::pair<uint32_t, uint32_t>> stack;  // node, packed prefix
+                stack.push_back({0u, 0u});
+                while (!stack.empty()) {
+                    const uint32_t v = stack.back().first, x = stack.back().second;
+                    stack.pop_back();
+                    const uint32_t d = nodes[v].depth;
+                    const uint32_t *b = &bm[(uint64_t)v * W];
+                    uint32_t ci = nodes[v].first_child;
+                    if (fin_code[v]) {
+                        // v reports output: a missing child ends the walk with it
+                        for (uint32_t c = 0; c < A; c++) {
+                            const uint32_t xc = x | (c << (bps * d));
+                            if (c < sigma && ((b[c >> 5] >> (c & 31)) & 1)) {
+                                if (d + 1 == g_len) add_all(xc, g_len);
+                                else stack.push_back({ci, xc});
+                                ci++;
+                            } else {
+                                add_all(xc, d + 1);
+                            }
+                        }
+                    } else {
+                        for (uint32_t w = 0; w < W; w++)
+                            for (uint32_t m = b[w]; m; m &= m - 1) {
+                                const uint32_t c = 32 * w + (uint32_t)__builtin_ctz(m);
+                                const uint32_t xc = x | (c << (bps * d));
+                                if (d + 1 == g_len) add_all(xc, g_len);
+                                else stack.push_back({ci, xc});
+                                ci++;
+                            }
+                    }
+                }
+                if (pass == 0 && g_set > (1ull << 26)) {
+                    // too many strings for a useful filter: none
+                    g_len = 0;
+                    g_set = 0;
+                    break;
+                }
+                if (pass == 0) {
+                    // about 16 bits per string, within [2^10, 2^20] bits
+                    g_bits = GRAM_MIN_BITS;
+                    while (g_bits < GRAM_MAX_BITS && (1ull << g_bits) < 16 * g_set) g_bits++;
+                    Gv.assign((1ull << g_bits) / 32, 0);
+                }
+            }
+        }
+        const uint64_t sz_G = Gv.size() * 4;
+
         uint64_t sz_stt = dense ? Q * sigma * 4 : 0;
         uint64_t sz_dfin = dense ? Q * 4 : 0;
 
@@ -410,6 +484,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 o_E[k] = place(sz_E[k]);
                 o_M[k] = place(sz_M[k]);
             }
+        const uint64_t o_G = place(sz_G);
         uint64_t o_stt = place(sz_stt), o_dfin = place(sz_dfin);
         const uint64_t blob = std::max<uint64_t>(off, 256);
 
@@ -429,6 +504,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 put(o_E[k], Ev[k].data(), sz_E[k]);
                 put(o_M[k], Mv[k].data(), sz_M[k]);
             }
+        put(o_G, Gv.data(), sz_G);
         if (dense) {
             uint32_t *S = (uint32_t *)(host.data() + o_stt);
             uint32_t *DF = (uint32_t *)(host.data() + o_dfin);
@@ -491,6 +567,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 dv.c_shift[k] = cshift[k];
                 dv.n_e[k] = (uint32_t)Ev[k].size();
             }
+        dv.G = g_len ? (const uint32_t *)(B + o_G) : nullptr;
+        dv.g_len = g_len;
+        dv.g_bits = g_bits;
+        dv.g_set = g_set;
         dv.stt = dense ? (const uint32_t *)(B + o_stt) : nullptr;
         dv.dfin = dense ? (const uint32_t *)(B + o_dfin) : nullptr;
         t->kmax = dense ? 0 : kmax;
@@ -512,6 +592,9 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         I.dense_bytes = Q * 4ull * sigma;
         I.output_lists = n_lists;
         I.output_list_words = pool.size();
+        I.gram_len = g_len;
+        I.gram_bits = g_bits;
+        I.gram_strings = g_set;
         *out = t;
         return PFAC_OK;
     } catch (const std::bad_alloc &) {

@@ -20,6 +20,7 @@ struct pfac_table {
     uint32_t tuned_k = 0;
     uint32_t tuned_copies = 0;
     uint32_t tuned_masks = 0;
+    uint32_t tuned_gram = 0;
 };
 
 namespace pfac {

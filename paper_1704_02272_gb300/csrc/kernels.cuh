@@ -90,6 +90,11 @@ struct MatchParams {
     uint32_t tbl_m_words; // child masks in shared memory (0 = not used)
     uint32_t c_shift;     // words per rank count of F_k (log2)
     uint32_t rep_log2;    // bitmap copies in shared memory (log2)
+    uint32_t tbl_g_words; // gram filter in shared memory, all copies (0 = not used)
+    uint32_t g_rep;       // gram filter copies (log2)
+    uint32_t g_fold;      // gram filter words OR-ed together per shared word (log2)
+    uint32_t g_hb;        // log2 of the shared gram filter's bits per copy
+    uint32_t kf;          // symbols the first stage tests: k, or g with the gram filter
     uint32_t dense_rows;  // dense layout: states whose rows live in shared memory
 };
 

@@ -300,16 +300,19 @@ __device__ __forceinline__ void resolve_batch(const MatchParams &P, QEntry *q, u
 }
 
 // Filter of one slice by one warp.  Fills the survivor masks of the lane's
-// 16 positions and their walk limits (relative to the slice start).
+// 16 positions and their walk limits (relative to the slice start).  The
+// first stage tests the k-symbol prefix index against the prefix bitmap F_k,
+// or, with the gram filter, the next g symbols against G.
 template <int BPS>
 __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t *sb,
                                              uint32_t staged, uint32_t valid, uint32_t rem,
                                              uint32_t lima, uint32_t limb, bool general_lims,
                                              const uint64_t *__restrict__ gseg, uint64_t ustart,
-                                             const uint32_t *Fs, uint32_t lane, uint32_t &surv,
+                                             const uint32_t *Fs, const uint32_t *Gs,
+                                             uint32_t lane, uint32_t &surv,
                                              uint32_t &rootm, uint32_t (&bs)[BPS + 1]) {
     const uint32_t p0 = lane * QBPT;
-    const uint32_t k = P.k, rep = P.rep_log2;
+    const uint32_t k = P.kf, rep = P.rep_log2;
     surv = 0;
     rootm = 0;
     if (p0 >= valid) {
@@ -321,18 +324,40 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
     const uint4 b = *reinterpret_cast<const uint4 *>(sb + p0 + 16);
     const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     pack_symbols<BPS>(x, bs);
-    const uint32_t kmask = (1u << (BPS * k)) - 1u;
-    const uint32_t copy = lane & ((1u << rep) - 1u);
-    // word of index i in copy `copy`: ((i >> 5) << rep) | copy, written as one
-    // shift and one mask so that the index needs no separate masking
-    const uint32_t sh = 5u - rep;
-    const uint32_t mk = (kmask >> sh) & ~((1u << rep) - 1u);
-    const uint32_t bmask = kmask < 31u ? kmask : 31u;
+    if (P.tbl_g_words == 0) {
+        const uint32_t kmask = (1u << (BPS * k)) - 1u;  // k * BPS >= 5
+        // Byte offset of the word of index t in copy `copy`:
+        // ((((t & kmask) >> 5) << rep) | copy) * 4.  Rotating t right by
+        // 3 - rep (left by rep - 3) puts the word bits at rep + 2 and
+        // everything else (the bit number, the symbols above the window, the
+        // wrapped bits) outside wmask, so one rotate and one and-or give it.
+        const uint32_t ramt = (3u - rep) & 31u;
+        const uint32_t wmask = (kmask >> 5) << (rep + 2);
+        const uint32_t c4 = (lane & ((1u << rep) - 1u)) << 2;
+        const uint8_t *Fb = reinterpret_cast<const uint8_t *>(Fs);
 #pragma unroll
-    for (int j = 0; j < QBPT; j++) {
-        const uint32_t t = symbols_at<BPS>(bs, j);
-        const uint32_t w = Fs[((t >> sh) & mk) | copy];
-        surv |= (__funnelshift_r(w, w, t & bmask) & 1u) << j;
+        for (int j = 0; j < QBPT; j++) {
+            const uint32_t t = symbols_at<BPS>(bs, j);
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(
+                Fb + ((__funnelshift_r(t, t, ramt) & wmask) | c4));
+            surv |= (__funnelshift_r(w, w, t) & 1u) << j;  // bit t & 31 of the word
+        }
+    } else {
+        // gram filter: y = x * GRAM_MUL for the g-symbol string x; word =
+        // top hbw bits of y, bit = y & 31 (table.h), copies interleaved
+        const uint32_t gmask = BPS * k >= 32 ? 0xFFFFFFFFu : (1u << (BPS * k)) - 1u;
+        const uint32_t gr = P.g_rep, hbw = P.g_hb - 5;
+        const uint32_t gsh = 30u - hbw - gr;  // y >> gsh puts the word at bit gr + 2
+        const uint32_t gwm = ((1u << hbw) - 1u) << (gr + 2);
+        const uint32_t c4 = (lane & ((1u << gr) - 1u)) << 2;
+        const uint8_t *Gb = reinterpret_cast<const uint8_t *>(Gs);
+#pragma unroll
+        for (int j = 0; j < QBPT; j++) {
+            const uint32_t y = (symbols_at<BPS>(bs, j) & gmask) * GRAM_MUL;
+            const uint32_t w =
+                *reinterpret_cast<const uint32_t *>(Gb + (((y >> gsh) & gwm) | c4));
+            surv |= (__funnelshift_r(w, w, y) & 1u) << j;  // bit y & 31 of the word
+        }
     }
     // positions whose k-symbol window is available in this segment and stage
     const uint32_t lim0 = lima < staged ? lima : staged;
@@ -412,16 +437,23 @@ __device__ __forceinline__ uint32_t symbols_dyn(const uint32_t (&bs)[BPS + 1], u
     return __funnelshift_r(lo, hi, bit & 31);
 }
 
-// Second on-chip stage for one survivor: with child masks, a survivor whose
-// depth-k state reports nothing and has no child on the next symbol (read
-// from the staged slice) stops there silently and is dropped.  An entry that
-// reports output has an all-ones mask and is kept whatever follows; a byte
-// outside the alphabet ends every other walk.  A survivor whose next symbol
-// is not at hand is kept.
+// Second on-chip stage for one survivor.  With the gram filter as the first
+// stage, the prefix index must be set in F_k (the filter may let other
+// positions through).  With child masks, a survivor whose depth-k state
+// reports nothing and has no child on the next symbol (read from the staged
+// slice) stops there silently and is dropped: an entry that reports output
+// has an all-ones mask and is kept whatever follows; a byte outside the
+// alphabet ends every other walk.  A survivor whose next symbol is not at
+// hand passes the mask test.
 __device__ __forceinline__ bool mask_keep(const MatchParams &P, uint32_t x, uint32_t p,
                                           uint32_t lim, const uint8_t *sb, uint32_t staged,
                                           const uint32_t *Fs, const uint32_t *Cs,
                                           const uint32_t *Ms) {
+    if (P.tbl_g_words) {
+        const uint32_t fwd = Fs[(x >> 5) << P.rep_log2];
+        if (!((fwd >> (x & 31)) & 1u)) return false;
+    }
+    if (!P.tbl_m_words) return true;
     const uint32_t qn1 = p + P.k, sigma = P.T.sigma;
     if (qn1 >= staged || qn1 >= lim) return true;
     const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, x);
@@ -455,7 +487,7 @@ __device__ __forceinline__ uint32_t gather_append(const MatchParams &P, QEntry *
     const uint32_t m = ((lanes >> lane) & 1u) ? cand : 0u;
     const uint32_t c = __popc(m);
     const uint32_t kmask = (1u << (BPS * P.k)) - 1u;
-    const bool masks = P.tbl_m_words != 0;
+    const bool masks = P.tbl_m_words != 0 || P.tbl_g_words != 0;  // a second stage
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t p0 = lane * QBPT;
 
@@ -679,8 +711,12 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
     return keys;
 }
 
-template <int W, int BPS, int VAR>
-__global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, const int emit) {
+// EMIT == 0: the scan pass (records and key counts).  EMIT == 1: the emit
+// pass over the slices listed in ovf_list.  The int argument is unused (the
+// launch signature is shared with the uncompressed kernel).
+template <int W, int BPS, int VAR, int EMIT>
+__global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, const int) {
+    constexpr bool emit = EMIT != 0;
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n_units = emit ? *(volatile uint32_t *)&P.hdr->ovf_count : P.n_tiles;
@@ -691,8 +727,10 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
     uint32_t *Cs = Fs + P.tbl_words;
     uint32_t *Es = Cs + P.tbl_c_words;
     uint32_t *Ms = Es + P.tbl_e_words;
+    uint32_t *Gs = Ms + P.tbl_m_words;
     WarpArea *areas = reinterpret_cast<WarpArea *>(
-        smem + ((((size_t)P.tbl_words + P.tbl_c_words + P.tbl_e_words + P.tbl_m_words) * 4 + 127) &
+        smem + ((((size_t)P.tbl_words + P.tbl_c_words + P.tbl_e_words + P.tbl_m_words +
+                  P.tbl_g_words) * 4 + 127) &
                 ~(size_t)127));
     {
         const uint32_t rep = P.rep_log2;
@@ -701,6 +739,14 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
         if (VAR == VAR_FE)
             for (uint32_t i = threadIdx.x; i < P.tbl_e_words; i += QTHREADS) Es[i] = __ldg(P.E + i);
         for (uint32_t i = threadIdx.x; i < P.tbl_m_words; i += QTHREADS) Ms[i] = __ldg(P.M + i);
+        // gram filter: word w of each copy is the OR of 2^g_fold table words
+        const uint32_t gr = P.g_rep, gf = P.g_fold;
+        for (uint32_t i = threadIdx.x; i < P.tbl_g_words; i += QTHREADS) {
+            const uint32_t *src = P.T.G + ((size_t)(i >> gr) << gf);
+            uint32_t v = 0;
+            for (uint32_t f = 0; f < (1u << gf); f++) v |= __ldg(src + f);
+            Gs[i] = v;
+        }
     }
     WarpArea &A = areas[warp];
     if (lane == 0) {
@@ -787,7 +833,7 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
         const uint8_t *sb = A.ring[s];
         uint32_t surv, rootm, bs[BPS + 1];
         filter_slice<BPS>(P, sb, staged, valid, rem, lima, limb, general_lims, P.seg, ustart, Fs,
-                          lane, surv, rootm, bs);
+                          Gs, lane, surv, rootm, bs);
         const uint32_t cand = surv | rootm;
         const uint32_t cnt = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(cand));
 
@@ -795,11 +841,8 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
             resolve_slice<W, BPS, VAR>(P, A.q, cand, rootm, bs, sb, staged, u, lima, limb,
                                        general_lims, ustart, rem, Fs, Cs, Es, Ms, lane, true);
         } else {
-            if (lane == 0) {
-                P.tile_m[u] = 0;  // the slice's last entry sets it when resolved
-                P.tile_k[u] = 0;
-            }
-            __syncwarp();
+            // tile_m / tile_k start at zero; the slice's last entry sets its
+            // record count when resolved
             uint32_t got = 0;
             if (cnt) {
                 got = gather_append<BPS>(P, A.q, qn, QCAP - qn, cand, rootm, 0xFFFFFFFFu, bs, sb,

@@ -2,6 +2,7 @@
 // kernels, and the C ABI calls pfac_workspace_bytes / pfac_match_async /
 // pfac_match (Section 2.3 semantics; see include/pfac.h).
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -12,17 +13,17 @@
 
 namespace pfac {
 
-void *scan_kernel_bps1(int);
-void *scan_kernel_bps2(int);
-void *scan_kernel_bps3(int);
-void *scan_kernel_bps4(int);
-void *scan_kernel_bps5(int);
-void *scan_kernel_bps6(int);
-void *scan_kernel_bps7(int);
-void *scan_kernel_bps8(int);
+void *scan_kernel_bps1(int, int);
+void *scan_kernel_bps2(int, int);
+void *scan_kernel_bps3(int, int);
+void *scan_kernel_bps4(int, int);
+void *scan_kernel_bps5(int, int);
+void *scan_kernel_bps6(int, int);
+void *scan_kernel_bps7(int, int);
+void *scan_kernel_bps8(int, int);
 void *scan_kernel_dense();
 
-constexpr int CHUNK = 4096;      // tiles per chunk of the key-count scan
+constexpr int CHUNK = 1024;      // tiles per chunk of the key-count scan
 constexpr int RT = 1024;         // threads of the scan/offset kernels
 
 // ------------------------------------------------ segment bounds per tile --
@@ -187,43 +188,27 @@ __global__ void __launch_bounds__(RT) k_offsets(const MatchParams P) {
     }
 }
 
-// Writes the keys of every tile whose records were kept (one warp per tile);
+// Writes the keys of every tile whose records were kept (one thread per tile);
 // the last CTA publishes the call's status.
 __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
     __shared__ bool last;
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // one thread per unit: most units hold a few records or none, so the
+    // units' loads are issued side by side rather than one unit per warp
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     const uint32_t *pool = P.T.pool;
-    for (uint64_t t = gw; t < P.n_tiles; t += nwarps) {
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P.n_tiles; t += nthr) {
         const uint32_t m = P.tile_m[t];
-        if (m == 0 || m > P.unit_cap || P.tile_k[t] == 0) continue;
-        uint64_t off = P.key_off[t];
+        if (m == 0 || m > P.unit_cap) continue;
+        uint64_t o = P.key_off[t];
         const uint64_t *rr = P.recs + t * P.unit_cap;
         const uint64_t tile_start = t << P.unit_shift;
-        for (uint32_t i0 = 0; i0 < m; i0 += 32) {
-            const uint32_t i = i0 + lane;
-            uint64_t r = 0;
-            uint32_t L = 0;
-            if (i < m) {
-                r = rr[i];
-                L = fin_len(pool, (uint32_t)r);
-            }
-            uint32_t inc = L;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-                if (lane >= (uint32_t)o) inc += nb;
-            }
-            const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-            if (L) {
-                const uint64_t pk = (tile_start + (r >> 32)) << PFAC_ID_BITS;
-                const uint32_t *ids = fin_ids(pool, (uint32_t)r);
-                uint64_t o = off + inc - L;
-                for (uint32_t e = 0; e < L; e++, o++)
-                    if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
-            }
-            off += tot;
+        for (uint32_t i = 0; i < m; i++) {
+            const uint64_t r = rr[i];
+            const uint32_t L = fin_len(pool, (uint32_t)r);
+            const uint32_t *ids = fin_ids(pool, (uint32_t)r);
+            const uint64_t pk = (tile_start + (r >> 32)) << PFAC_ID_BITS;
+            for (uint32_t e = 0; e < L; e++, o++)
+                if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
         }
     }
     __syncthreads();
@@ -245,9 +230,11 @@ struct Plan {
     uint32_t k;
     uint32_t tbl_words, tbl_c_words, tbl_e_words, tbl_m_words;
     uint32_t rep_log2;
+    uint32_t tbl_g_words, g_rep, g_fold;  // gram filter: words (all copies), copies, fold
     uint32_t dense_rows;
     uint32_t unit_shift, unit_cap;
-    void *kernel;
+    void *kernel;       // scan pass
+    void *kernel_emit;  // emit pass
     size_t smem;
     bool queued;
 };
@@ -285,16 +272,16 @@ static WsLayout ws_layout(uint64_t n_bytes, uint32_t n_seg, const Plan &pl) {
     return L;
 }
 
-static void *scan_kernel_for(uint32_t bps, int var) {
+static void *scan_kernel_for(uint32_t bps, int var, int emit) {
     switch (bps) {
-        case 1: return scan_kernel_bps1(var);
-        case 2: return scan_kernel_bps2(var);
-        case 3: return scan_kernel_bps3(var);
-        case 4: return scan_kernel_bps4(var);
-        case 5: return scan_kernel_bps5(var);
-        case 6: return scan_kernel_bps6(var);
-        case 7: return scan_kernel_bps7(var);
-        case 8: return scan_kernel_bps8(var);
+        case 1: return scan_kernel_bps1(var, emit);
+        case 2: return scan_kernel_bps2(var, emit);
+        case 3: return scan_kernel_bps3(var, emit);
+        case 4: return scan_kernel_bps4(var, emit);
+        case 5: return scan_kernel_bps5(var, emit);
+        case 6: return scan_kernel_bps6(var, emit);
+        case 7: return scan_kernel_bps7(var, emit);
+        case 8: return scan_kernel_bps8(var, emit);
         default: return nullptr;
     }
 }
@@ -307,9 +294,16 @@ static size_t dense_smem(uint32_t tbl_words) {
 
 constexpr size_t SMEM_LIMIT = 232448;  // per-CTA dynamic shared memory on sm_103a
 
-static size_t queued_smem(uint32_t w, uint32_t cw, uint32_t ew, uint32_t mw) {
-    const size_t tbl = (((size_t)w + cw + ew + mw) * 4 + 127) & ~(size_t)127;
+static size_t queued_smem(uint64_t words) {
+    const size_t tbl = ((size_t)words * 4 + 127) & ~(size_t)127;
     return tbl + QW * sizeof(WarpArea);
+}
+
+// Shared-memory wavefronts of one warp-wide bitmap load with 2^rep copies
+// (interleaved word by word): lanes sharing a copy collide on a bank.
+static double load_wavefronts(int rep) {
+    static const double wf[6] = {3.7, 3.4, 3.1, 2.85, 2.0, 1.0};
+    return wf[rep < 0 ? 0 : (rep > 5 ? 5 : rep)];
 }
 
 static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl) {
@@ -321,7 +315,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
         if (rows > T.n_nodes) rows = T.n_nodes;
         pl->dense_rows = rows;
         pl->tbl_words = rows * T.sigma;
-        pl->kernel = scan_kernel_dense();
+        pl->kernel = pl->kernel_emit = scan_kernel_dense();
         pl->smem = dense_smem(pl->tbl_words);
         pl->unit_shift = 13;
         pl->unit_cap = REC_CAP;
@@ -345,68 +339,140 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     const uint32_t masks = opts && opts->child_masks ? opts->child_masks
                                                     : (use_tuned ? t->tuned_masks : 0u);
     if (masks > 2) return set_error(PFAC_EINVAL, "pfac_match: child_masks %u", masks);
-    // largest power-of-two bitmap replication that fits next to the rest
-    auto best_rep = [&](uint32_t extra) -> int {
-        int rep = -1;
-        for (int r = 0; r <= 5; r++)
-            if (queued_smem((uint32_t)((uint64_t)fw << r), cw, extra, 0) <= SMEM_LIMIT) rep = r;
-        return rep;
-    };
-    const int rep_f = best_rep(0), rep_fe = best_rep(ew);
-    if (var == 0) var = (rep_fe >= 0 && rep_fe >= rep_f - 1) ? VAR_FE : VAR_F;
-    if (var != VAR_F && var != VAR_FE)
-        return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
-    const uint32_t e_sm = var == VAR_FE ? ew : 0u;
-    // child masks: with them if they fit (or on request), then the most copies
-    const int rep_m = best_rep(e_sm + ew);
-    const bool use_m = masks == 2 || (masks == 0 && rep_m >= 0);
-    int rep = best_rep(e_sm + (use_m ? ew : 0u));
+    const uint32_t gram = opts && opts->gram_filter ? opts->gram_filter
+                                                   : (use_tuned ? t->tuned_gram : 0u);
+    if (gram > 2) return set_error(PFAC_EINVAL, "pfac_match: gram_filter %u", gram);
+    if (gram == 2 && !T.g_len)
+        return set_error(PFAC_EINVAL, "pfac_match: the table has no gram filter");
     const uint32_t copies = opts && opts->bitmap_copies ? opts->bitmap_copies
                                                        : (use_tuned ? t->tuned_copies : 0u);
+    int want = -1;
     if (copies) {
-        int want = 0;
+        want = 0;
         while ((1u << want) < copies) want++;
         if ((1u << want) != copies || want > 5)
             return set_error(PFAC_EINVAL, "pfac_match: bitmap_copies %u is not 1, 2, 4, .., 32",
                              copies);
-        if (want > rep)
-            return set_error(PFAC_EINVAL, "pfac_match: %u bitmap copies do not fit", copies);
-        rep = want;
     }
-    if (rep < 0)
-        return set_error(PFAC_EINVAL, "pfac_match: prefix node of depth %u does not fit in "
-                         "shared memory with variant %d%s", k, var, use_m ? " and child masks" : "");
+    if (var != 0 && var != VAR_F && var != VAR_FE)
+        return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
+
+    // ---- prefix bitmap as the first stage: largest replication that fits
+    auto best_rep = [&](uint64_t extra) -> int {
+        int rep = -1;
+        for (int r = 0; r <= 5; r++)
+            if (queued_smem(((uint64_t)fw << r) + cw + extra) <= SMEM_LIMIT) rep = r;
+        return rep;
+    };
+    int var_f = var;
+    if (var_f == 0) {
+        const int rep_f = best_rep(0), rep_fe = best_rep(ew);
+        var_f = (rep_fe >= 0 && rep_fe >= rep_f - 1) ? VAR_FE : VAR_F;
+    }
+    const uint32_t e_f = var_f == VAR_FE ? ew : 0u;
+    // child masks: with them if they fit (or on request), then the most copies
+    const bool m_f = masks == 2 || (masks == 0 && best_rep(e_f + ew) >= 0);
+    int rep_f = best_rep(e_f + (m_f ? ew : 0u));
+    if (want >= 0 && want <= rep_f) rep_f = want;
+    else if (want >= 0) rep_f = -2;  // the requested copies do not fit
+    const double dens_f = (double)ew / (double)ent;
+
+    // ---- gram filter as the first stage: the prefix bitmap once (for the
+    // exact test of survivors), the filter folded (adjacent words OR-ed)
+    // until the chosen copies fit
+    bool use_g = false;
+    int var_g = var, rep_g = -1;
+    uint32_t fold_g = 0;
+    bool m_g = false;
+    double cost_g = 1e30;
+    if (T.g_len && gram != 1) {
+        const uint32_t hb = T.g_bits;
+        const uint64_t gw0 = (1ull << hb) / 32;
+        if (var_g == 0) var_g = queued_smem(fw + cw + ew + (gw0 >> (hb - GRAM_MIN_BITS))) <= SMEM_LIMIT
+                                    ? VAR_FE : VAR_F;
+        const uint32_t e_g = var_g == VAR_FE ? ew : 0u;
+        m_g = masks == 2 || (masks == 0 && queued_smem(fw + cw + e_g + ew +
+                                                       (gw0 >> (hb - GRAM_MIN_BITS))) <= SMEM_LIMIT);
+        const uint64_t base = fw + cw + e_g + (m_g ? ew : 0u);
+        for (int r = 0; r <= 5; r++) {
+            if (want >= 0 && r != want) continue;
+            for (uint32_t f = 0; hb - f >= GRAM_MIN_BITS; f++) {
+                if (queued_smem(base + ((gw0 >> f) << r)) > SMEM_LIMIT) continue;
+                // expected share of positions through the first stage
+                const double dens = 1.0 - exp(-(double)T.g_set / (double)(1ull << (hb - f)));
+                const double c = load_wavefronts(r) + 100.0 * dens;
+                if (c < cost_g) {
+                    cost_g = c;
+                    rep_g = r;
+                    fold_g = f;
+                }
+                break;  // the least folding that fits
+            }
+        }
+        if (rep_g >= 0) {
+            const double cost_f = rep_f >= 0 ? load_wavefronts(rep_f) + 100.0 * dens_f : 1e30;
+            use_g = gram == 2 || cost_g < 0.8 * cost_f;
+        } else if (gram == 2) {
+            return set_error(PFAC_EINVAL, "pfac_match: the gram filter does not fit in shared "
+                             "memory with depth %u%s", k, want >= 0 ? " and these copies" : "");
+        }
+    }
+    if (use_g) {
+        var = var_g;
+        pl->rep_log2 = 0;
+        pl->tbl_words = fw;
+        pl->tbl_e_words = var == VAR_FE ? ew : 0u;
+        pl->tbl_m_words = m_g ? ew : 0u;
+        pl->g_rep = (uint32_t)rep_g;
+        pl->g_fold = fold_g;
+        pl->tbl_g_words = (uint32_t)((((1ull << T.g_bits) / 32) >> fold_g) << rep_g);
+    } else {
+        if (rep_f == -2)
+            return set_error(PFAC_EINVAL, "pfac_match: %u bitmap copies do not fit", copies);
+        if (rep_f < 0)
+            return set_error(PFAC_EINVAL, "pfac_match: prefix node of depth %u does not fit in "
+                             "shared memory with variant %d%s", k, var_f,
+                             m_f ? " and child masks" : "");
+        var = var_f;
+        pl->rep_log2 = (uint32_t)rep_f;
+        pl->tbl_words = (uint32_t)((uint64_t)fw << rep_f);
+        pl->tbl_e_words = e_f;
+        pl->tbl_m_words = m_f ? ew : 0u;
+    }
     pl->var = var;
     pl->k = k;
-    pl->rep_log2 = (uint32_t)rep;
-    pl->tbl_words = (uint32_t)((uint64_t)fw << rep);
     pl->tbl_c_words = cw;
-    pl->tbl_e_words = e_sm;
-    pl->tbl_m_words = use_m ? ew : 0u;
-    pl->kernel = scan_kernel_for(T.bps, var);
-    pl->smem = queued_smem(pl->tbl_words, pl->tbl_c_words, pl->tbl_e_words, pl->tbl_m_words);
+    pl->kernel = scan_kernel_for(T.bps, var, 0);
+    pl->kernel_emit = scan_kernel_for(T.bps, var, 1);
+    pl->smem = queued_smem((uint64_t)pl->tbl_words + pl->tbl_c_words + pl->tbl_e_words +
+                           pl->tbl_m_words + pl->tbl_g_words);
     pl->unit_shift = SLICE_SHIFT;
     pl->unit_cap = SCAP;
     pl->queued = true;
-    if (!pl->kernel) return set_error(PFAC_EINVAL, "pfac_match: no kernel for this table");
+    if (!pl->kernel || !pl->kernel_emit)
+        return set_error(PFAC_EINVAL, "pfac_match: no kernel for this table");
     return PFAC_OK;
 }
 
 static std::mutex g_attr_mu;
 
 static int prepare_kernel(void *fn, size_t smem) {
-    // raise the dynamic shared-memory limit once per kernel and size
-    static void *done_fn[64];
-    static size_t done_sz[64];
+    // raise the dynamic shared-memory limit once per kernel, device and size
+    static void *done_fn[128];
+    static int done_dev[128];
+    static size_t done_sz[128];
     static int n_done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_attr_mu);
     for (int i = 0; i < n_done; i++)
-        if (done_fn[i] == fn && done_sz[i] >= smem) return PFAC_OK;
+        if (done_fn[i] == fn && done_dev[i] == dev && done_sz[i] >= smem) return PFAC_OK;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return set_error(PFAC_ECUDA, "pfac_match: smem attribute: %s", cudaGetErrorString(e));
-    if (n_done < 64) {
+    if (n_done < 128) {
         done_fn[n_done] = fn;
+        done_dev[n_done] = dev;
         done_sz[n_done] = smem;
         n_done++;
     }
@@ -431,6 +497,26 @@ extern "C" int pfac_workspace_bytes(const pfac_table *t, uint64_t n_bytes, uint3
     const int rc = make_plan(t, opts, &pl);
     if (rc) return rc;
     *bytes = ws_layout(n_bytes, n_segments, pl).total;
+    return PFAC_OK;
+}
+
+extern "C" int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts,
+                               pfac_plan_info *out) {
+    clear_error();
+    if (!t || !out) return set_error(PFAC_EINVAL, "pfac_match_plan: NULL argument");
+    Plan pl;
+    const int rc = make_plan(t, opts, &pl);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    out->smem_bytes = (uint32_t)pl.smem;
+    if (!pl.queued) return PFAC_OK;
+    out->variant = (uint32_t)pl.var;
+    out->prefix_depth = pl.k;
+    const bool g = pl.tbl_g_words != 0;
+    out->bitmap_copies = 1u << (g ? pl.g_rep : pl.rep_log2);
+    out->child_masks = pl.tbl_m_words ? 2u : 1u;
+    out->gram_filter = g ? 2u : 1u;
+    out->gram_bits = g ? t->dev.g_bits - pl.g_fold : 0u;
     return PFAC_OK;
 }
 
@@ -460,6 +546,7 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
         return set_error(PFAC_EINVAL, "pfac_match: workspace of %llu bytes, %llu needed",
                          (unsigned long long)workspace_bytes, (unsigned long long)L.total);
     rc = prepare_kernel(pl.kernel, pl.smem);
+    if (!rc && pl.kernel_emit != pl.kernel) rc = prepare_kernel(pl.kernel_emit, pl.smem);
     if (rc) return rc;
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -495,6 +582,11 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.M = pl.k ? t->dev.M[pl.k] : nullptr;
     P.c_shift = pl.k ? t->dev.c_shift[pl.k] : 0u;
     P.tbl_m_words = pl.tbl_m_words;
+    P.tbl_g_words = pl.tbl_g_words;
+    P.g_rep = pl.g_rep;
+    P.g_fold = pl.g_fold;
+    P.g_hb = pl.tbl_g_words ? t->dev.g_bits - pl.g_fold : 0u;
+    P.kf = pl.tbl_g_words ? t->dev.g_len : pl.k;
     P.tbl_words = pl.tbl_words;
     P.tbl_c_words = pl.tbl_c_words;
     P.tbl_e_words = pl.tbl_e_words;
@@ -503,7 +595,9 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     const uint32_t nthreads = pl.queued ? QTHREADS : NTHREADS;
     const uint32_t units_per_cta = pl.queued ? QW : 1;
 
-    cudaError_t e = cudaMemsetAsync(P.hdr, 0, sizeof(WsHeader), st);
+    // header, and for the queued kernel the per-unit record and key counts
+    // (the scan pass writes them only for units with kept survivors)
+    cudaError_t e = cudaMemsetAsync(P.hdr, 0, pl.queued ? L.key_off : sizeof(WsHeader), st);
     const int nsm = sm_count();
     const uint32_t cps = opts && opts->ctas_per_sm ? opts->ctas_per_sm : 1;
     if (e == cudaSuccess && n_segments > 1 && L.n_tiles) {
@@ -534,11 +628,11 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     if (e == cudaSuccess && L.n_tiles) {
         int emit = 1;
         void *args[] = {&P, &emit};
-        e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(nthreads), args, pl.smem, st);
+        e = cudaLaunchKernel(pl.kernel_emit, dim3(grid), dim3(nthreads), args, pl.smem, st);
     }
     if (e == cudaSuccess) {
-        uint64_t warps = L.n_tiles ? L.n_tiles : 1;
-        uint64_t blocks = (warps + 7) / 8;
+        const uint64_t units = L.n_tiles ? L.n_tiles : 1;
+        uint64_t blocks = (units + 255) / 256;
         const uint64_t maxb = (uint64_t)nsm * 8;
         if (blocks > maxb) blocks = maxb;
         k_expand<<<(uint32_t)blocks, 256, 0, st>>>(P);

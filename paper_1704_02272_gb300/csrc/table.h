@@ -29,6 +29,14 @@
 //     ones when the entry itself reports output: a survivor whose next symbol
 //     misses the mask stops silently without visiting the records.
 //
+// Gram filter (an optional first on-chip stage): a bitmap G of 2^hb bits
+// over strings of g symbols (packed like a prefix index).  Bit gram_pos(x)
+// is set for every string x whose walk from the root reaches depth g, or
+// stops before depth g at a state that reports output; a start position
+// whose next g symbols miss G reports nothing.  Hashing keeps G small when
+// 2^(g*b) is far beyond shared memory; collisions only let extra positions
+// through to the exact prefix-node test.
+//
 // Dense layout (uncompressed PFAC): stt[s * sigma + c] = child or 0 (the root
 // is never a child), dfin[s] = fin(s).
 #pragma once
@@ -55,6 +63,13 @@ constexpr uint32_t FIN_MAX_OFF = (1u << (31 - FIN_LEN_BITS)) - 1;
 //           words before each word, one byte per word)
 __host__ __device__ constexpr int rec_words(int W) { return W == 1 ? 2 : (W == 2 ? 4 : 12); }
 
+// Gram filter hash: y = x * GRAM_MUL (Knuth's multiplicative hashing with
+// the golden-ratio constant); the word is the top hb - 5 bits of y, the bit
+// within the word its low 5 bits.
+constexpr uint32_t GRAM_MUL = 0x9E3779B1u;
+constexpr uint32_t GRAM_MIN_BITS = 10, GRAM_MAX_BITS = 20;
+__host__ __device__ inline uint32_t gram_word(uint32_t y, uint32_t hb) { return y >> (37 - hb); }
+
 // Bit of symbol c in a child mask: exact for alphabets of up to 32 symbols.
 __host__ __device__ inline uint32_t child_hash(uint32_t c, uint32_t sigma) {
     return sigma <= 32 ? c : ((c ^ (c >> 5)) & 31u);
@@ -80,6 +95,10 @@ struct DevTable {
     const uint32_t *E[KMAX + 1];   // entries of the set bits of F_k
     const uint32_t *M[KMAX + 1];   // per entry: hashed symbols its state continues with
     uint32_t n_e[KMAX + 1];        // number of entries of depth k
+    const uint32_t *G;             // gram filter (nullptr when none)
+    uint32_t g_len;                // g: symbols per gram
+    uint32_t g_bits;               // hb: log2 of the bits of G
+    uint64_t g_set;                // strings whose bit is set
     const uint32_t *stt;      // dense layout
     const uint32_t *dfin;
 };

@@ -119,3 +119,42 @@ def test_host_only_table_cannot_match():
                              torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int32),
                              torch.zeros(1 << 16, dtype=torch.uint8), stream=0)
         assert ei.value.status == -1
+
+
+def gram_strings_brute(patterns, g, bps):
+    """Strings x of g symbols (values 0 .. 2^bps - 1) whose walk from the root
+    reaches depth g (x is a prefix of a pattern) or stops before depth g at a
+    state with output (a pattern is a prefix of x)."""
+    import itertools
+    pats = [bytes(p) for p in patterns]
+    prefixes = {p[:i] for p in pats for i in range(1, len(p) + 1)}
+    pset = set(pats)
+    n = 0
+    for x in itertools.product(range(1 << bps), repeat=g):
+        s = bytes(x)
+        if s in prefixes or any(s[:i] in pset for i in range(1, g + 1)):
+            n += 1
+    return n
+
+
+@pytest.mark.parametrize("seed,sigma,n,lo,hi,k,bps", [(11, 4, 40, 1, 6, 3, 2),
+                                                       (12, 3, 30, 2, 9, 4, 2),
+                                                       (13, 20, 60, 1, 4, 1, 5),
+                                                       (14, 5, 25, 1, 7, 2, 3),
+                                                       (15, 2, 20, 1, 12, 8, 1)])
+def test_gram_filter_string_count(seed, sigma, n, lo, hi, k, bps):
+    # the gram filter covers g = k + 1 symbols; its count of strings that
+    # start a match is the brute-force count over all g-symbol strings
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, 0)
+    with host_table(w.patterns, sigma, prefix_depth=k) as t:
+        info = t.info()
+    assert info["gram_len"] == k + 1
+    assert info["gram_strings"] == gram_strings_brute(w.patterns, k + 1, bps)
+    assert 10 <= info["gram_bits"] <= 20
+
+
+def test_prefix_depth_too_small_rejected():
+    # a prefix index must span at least 5 bits
+    with pytest.raises(pfac.PfacError) as ei:
+        host_table([b"\x01\x02"], 4, prefix_depth=2)
+    assert ei.value.status == -1

@@ -97,3 +97,23 @@ def test_sweep_cell(sigma, n):
         ref = oracle_keys(w, lo=a, hi=a + win, ac=ac)
         assert_same(window(kc, a, a + win), ref, f"{w.name} window {a}")
     ac.close()
+
+
+GRAM_CELLS = [("ids", 0, 0), ("sweep", 256, 10000), ("sweep", 256, 100000), ("sweep", 20, 100000),
+              ("sweep", 4, 1000)]
+
+
+@pytest.mark.parametrize("kind,sigma,n", GRAM_CELLS, ids=[f"{k}-{s}-{n}" for k, s, n in GRAM_CELLS])
+def test_gram_filter_full_size(kind, sigma, n):
+    # the gram filter as the first stage, forced on and off, gives the same
+    # keys as the uncompressed kernel on full-size workloads
+    w = workloads.config3() if kind == "ids" else workloads.config4(sigma, n)
+    text, seg = to_device(w)
+    kd = device_keys(w, text, seg, pfac.LAYOUT_DENSE)
+    with pfac.Table(w.patterns, w.sigma) as t:
+        assert t.info()["gram_len"] > 0
+        for gram in (2, 1):
+            kg = pfac.match(t, text, seg, gram_filter=gram)
+            torch.cuda.synchronize()
+            assert kg.numel() == kd.numel() and torch.equal(kg, kd), f"gram_filter={gram}"
+            del kg

@@ -87,6 +87,30 @@ def test_child_masks_forced(case):
     assert_same(run(w, prefix_depth=k, child_masks=1), ref, "child masks off")
 
 
+@pytest.mark.parametrize("case", CASES, ids=[f"s{c[0]}-sig{c[1]}" for c in CASES])
+def test_gram_filter_forced(case):
+    # the gram filter as the first stage (then the exact prefix-bitmap test)
+    # at both ends of the depths held and with 1 and 32 copies
+    seed, sigma, n, lo, hi, N, S, plants, ts = case
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, N, n_segments=S, n_plants=plants,
+                            text_sigma=ts)
+    ref = oracle_keys(w)
+    with pfac.Table(w.patterns, w.sigma, host_only=True) as th:
+        info = th.info()
+    assert info["gram_len"] == info["prefix_depth"] + 1
+    ran = 0
+    for k in (info["prefix_depth"], max(1, info["prefix_depth"] - 2)):
+        for copies in (0, 1, 32):
+            try:
+                got = run(w, prefix_depth=k, gram_filter=2, bitmap_copies=copies)
+            except pfac.PfacError as e:  # does not fit in shared memory
+                assert e.status == -1, str(e)
+                continue
+            assert_same(got, ref, f"gram filter depth {k} copies {copies}")
+            ran += 1
+    assert ran >= 2
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_prefix_heavy(seed):
     w = workloads.prefix_heavy_case(seed, 3 + seed, 200_000, n_segments=1 + 30 * (seed % 2))
