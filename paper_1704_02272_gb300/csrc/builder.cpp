@@ -408,9 +408,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                     break;
                 }
                 if (pass == 0) {
-                    // about 16 bits per string, within [2^10, 2^20] bits
+                    // about 64 bits per string, within [2^10, 2^20] bits (the
+                    // planner folds it down to fit shared memory)
                     g_bits = GRAM_MIN_BITS;
-                    while (g_bits < GRAM_MAX_BITS && (1ull << g_bits) < 16 * g_set) g_bits++;
+                    while (g_bits < GRAM_MAX_BITS && (1ull << g_bits) < 64 * g_set) g_bits++;
                     Gv.assign((1ull << g_bits) / 32, 0);
                 }
             }
