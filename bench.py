@@ -41,7 +41,10 @@ SCAN_KERNELS_PER_STEP = 5  # scan, key-count reduce, offsets, overflow re-scan, 
 # dram__bytes_read.sum + dram__bytes_write.sum of one scan launch from one
 # ncu capture per workload (summaries under profiles/), with the digest of the
 # kernel sources it was taken on; reported only while the sources still match
-MEASURED_TRAFFIC = {"dna": (306808832, "49344556a0520ca2")}
+MEASURED_TRAFFIC = {"dna": (306808832, "49344556a0520ca2",
+                           {"variant": 1, "prefix_depth": 10, "bitmap_copies": 1,
+                            "child_masks": 1, "gram_filter": 1})}
+TUNE_SAMPLE = 128 << 20
 KERNEL_SOURCES = ["kernels_q.cuh", "kernels.cuh", "table.h"]
 
 
@@ -54,9 +57,11 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload):
+def measured_traffic(workload, plan):
     t = MEASURED_TRAFFIC.get(workload)
-    return t[0] if t and t[1] == kernel_digest() else None
+    if not t or t[1] != kernel_digest():
+        return None
+    return t[0] if all(plan.get(k) == v for k, v in t[2].items()) else None
 
 
 def peaks():
@@ -267,8 +272,15 @@ def run_ours(args):
         user_opt["child_masks"] = args.masks
     if args.gram:
         user_opt["gram_filter"] = args.gram
-    if args.autotune:
-        tune = pfac.autotune(table, text, seg)
+    tune = None
+    if not args.no_autotune and not user_opt:
+        # the autotuner on a bounded prefix sample of the input (whole
+        # segments, at most TUNE_SAMPLE bytes); untimed
+        nb = max(16, min(N, TUNE_SAMPLE) & ~15)
+        offs = w.seg_offsets.astype(np.int64)
+        cut = int(np.searchsorted(offs, nb, side="left"))  # offsets below nb
+        s_offs = torch.from_numpy(np.concatenate([offs[:cut], [nb]])).to(dev)
+        tune = pfac.autotune(table, text[:nb], s_offs)
     plan = pfac.plan(table, **user_opt)
     ws = torch.empty(max(pfac.workspace_bytes(table, N, S, **user_opt),
                          pfac.workspace_bytes(dense, N, S)), dtype=torch.uint8, device=dev)
@@ -395,7 +407,7 @@ def run_ours(args):
                 "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": args.traffic if args.traffic is not None else (
-                    measured_traffic(args.workload) if not user_opt and not args.autotune else None),
+                    measured_traffic(args.workload, plan) if not user_opt else None),
                 "kernel": "k_scanq (compressed-table scan)",
                 "alg_bytes_per_launch": alg_bytes}
 
@@ -406,7 +418,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": dict(base_config(w, args), prefix_depth=plan["prefix_depth"],
                        variant=args.variant or "default", bitmap_copies=args.copies or "auto",
-                       autotuned=tune if args.autotune else None, scan_plan=plan,
+                       autotuned=tune, scan_plan=plan,
                        cuda_graph=bool(graph is not None)),
         "p50_ms": round(statistics.median(step_ms), 4),
         "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
@@ -522,7 +534,9 @@ def main():
     ap.add_argument("--copies", type=int, default=0, help="prefix-bitmap copies in smem")
     ap.add_argument("--masks", type=int, default=0, help="child masks: 1 off, 2 on")
     ap.add_argument("--gram", type=int, default=0, help="gram filter first stage: 1 off, 2 on")
-    ap.add_argument("--autotune", action="store_true", help="pfac_autotune on the input first")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip pfac_autotune on a sample of the input (it runs by default "
+                         "when no scan option is given)")
     ap.add_argument("--graph", action="store_true",
                     help="time CUDA-graph replays of the match call (default for packets)")
     ap.add_argument("--loads", default="10,25,50,100,200,300,400")

@@ -347,6 +347,20 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 sz_F[k] = fw * 4;
                 sz_C[k] = Cv[k].size() * 4;
                 sz_E[k] = Ev[k].size() * 4;
+                // narrow masks for small alphabets: mask_bits(sigma) bits per
+                // entry, packed low entry first (an all-ones mask still means
+                // "keep whatever follows")
+                const uint32_t mb = mask_bits(sigma);
+                if (mb < 32) {
+                    std::vector<uint32_t> packed((Mv[k].size() * mb + 31) / 32, 0);
+                    const uint32_t ones = (1u << mb) - 1u;
+                    for (size_t r = 0; r < Mv[k].size(); r++)
+                        packed[(r * mb) >> 5] |= (Mv[k][r] & ones) << ((r * mb) & 31);
+                    Mv[k].swap(packed);
+                }
+                // child masks are only used from shared memory: none when the
+                // entries could never fit there
+                if (Mv[k].size() * 4 > MASKS_MAX_BYTES) Mv[k].clear();
                 sz_M[k] = Mv[k].size() * 4;
             }
         // ---- gram filter over g = kmax + 1 symbols (see table.h) -----------
@@ -564,9 +578,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 dv.F[k] = (const uint32_t *)(B + o_F[k]);
                 dv.C[k] = (const uint32_t *)(B + o_C[k]);
                 dv.E[k] = (const uint32_t *)(B + o_E[k]);
-                dv.M[k] = (const uint32_t *)(B + o_M[k]);
+                dv.M[k] = sz_M[k] ? (const uint32_t *)(B + o_M[k]) : nullptr;
                 dv.c_shift[k] = cshift[k];
                 dv.n_e[k] = (uint32_t)Ev[k].size();
+                dv.m_words[k] = (uint32_t)Mv[k].size();
             }
         dv.G = g_len ? (const uint32_t *)(B + o_G) : nullptr;
         dv.g_len = g_len;

@@ -41,6 +41,7 @@ constexpr int QU = QCAP / 32;            // queue entries per lane per batch
 // walks a lane advances together while resolving: fewer for 48-byte records
 __host__ __device__ constexpr int walks_per_lane(int W) { return W == 8 ? 2 : 4; }
 constexpr uint32_t ROOT_X = 0xFFFFFFFFu; // queue entry: walk from the root
+constexpr uint32_t LAST_FLAG = 0x80000000u;  // queue entry: the slice's last
 constexpr uint32_t UNIT_OVF = 0xFFFFFFFFu;
 constexpr uint32_t LIM_MAX = 0xFFFFFFF0u;
 
@@ -373,19 +374,30 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
                 if ((x[i >> 2] >> (8 * (i & 3))) & ((0xFFu << BPS) & 0xFFu)) badb |= 1u << i;
         }
     }
-    const uint32_t kwin = (k >= 32) ? 0xFFFFFFFFu : ((1u << k) - 1u);
     // every position's window is available (the window limits are exact
     // only when the slice's segment ends fit the lane's window)
     if (!general_lims && p0 + QBPT - 1 + k <= lim0 && badb == 0) return;
+    // fv: positions whose whole window lies in their segment and the stage;
+    // ex: positions inside their segment (the others start no walk)
     uint32_t fv = 0, ex = 0;
+    if (!general_lims) {
+        // positions before lima end at lima, the others at limb: each set is
+        // a run of low bits, so the masks come from a few compares
+        auto below = [&](uint32_t x) -> uint32_t {  // positions p0 + j < x
+            const uint32_t n = x > p0 ? (x - p0 < (uint32_t)QBPT ? x - p0 : (uint32_t)QBPT) : 0u;
+            return (1u << n) - 1u;
+        };
+        const uint32_t in_a = below(lima), vm = below(valid);
+        const uint32_t la = lima < staged ? lima : staged, lb = limb < staged ? limb : staged;
+        const uint32_t fa = la >= k ? below(la - k + 1) : 0u;  // p + k <= la
+        const uint32_t fb = lb >= k ? below(lb - k + 1) : 0u;
+        ex = (in_a | below(limb)) & vm;
+        fv = ((fa & in_a) | (fb & ~in_a)) & vm;
+    } else {
 #pragma unroll 1
-    for (int j = 0; j < QBPT; j++) {
-        const uint32_t p = p0 + j;
-        if (p >= valid) break;
-        uint32_t lj;
-        if (!general_lims) {
-            lj = p < lima ? lima : limb;
-        } else {
+        for (int j = 0; j < QBPT; j++) {
+            const uint32_t p = p0 + j;
+            if (p >= valid) break;
             uint32_t lo = 1, hi = P.n_seg;
             const uint64_t ap = ustart + p;
             while (lo < hi) {
@@ -394,11 +406,17 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
             }
             const uint64_t e = __ldg(gseg + lo);
             const uint64_t r = e > ustart ? e - ustart : 0;
-            lj = r < rem ? (uint32_t)r : rem;
+            const uint32_t lj = r < rem ? (uint32_t)r : rem;
+            if (lj > p) ex |= 1u << j;
+            const uint32_t lw = lj < staged ? lj : staged;
+            if (p + k <= lw) fv |= 1u << j;
         }
-        if (lj > p) ex |= 1u << j;
-        const uint32_t lw = lj < staged ? lj : staged;
-        if (p + k <= lw && ((badb >> j) & kwin) == 0) fv |= 1u << j;
+    }
+    if (badb) {
+        // windows holding a byte outside the packed symbol range
+        uint32_t bw = 0;
+        for (uint32_t t = 0; t < k; t++) bw |= badb >> t;
+        fv &= ~bw;
     }
     surv &= fv;
     rootm = ex & ~fv;
@@ -457,141 +475,10 @@ __device__ __forceinline__ bool mask_keep(const MatchParams &P, uint32_t x, uint
     const uint32_t qn1 = p + P.k, sigma = P.T.sigma;
     if (qn1 >= staged || qn1 >= lim) return true;
     const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, x);
-    const uint32_t cs = sb[qn1], mr = Ms[r];
-    return cs < sigma ? ((mr >> child_hash(cs, sigma)) & 1u) != 0 : mr == 0xFFFFFFFFu;
-}
-
-// Appends the survivors of the lanes set in `lanes` to the queue at qn, in
-// position order, after the second on-chip stage (mask_keep).  Entry fields:
-// the slice, the position, the slot among the slice's appended survivors
-// and, on the last one, LAST_FLAG; the prefix index (or ROOT_X); the walk
-// limit.  Sparse slices (at most two candidates per lane) are handled by
-// each lane for its own candidates; denser ones are dealt out one per lane
-// (candidate i of each group of 32 to lane i, which finds the owning lane by
-// a shuffle search over the lanes' exclusive counts and the position in
-// that lane's mask by __fns), so the work runs 32 wide.
-// Returns the number appended, or cap + 1 (nothing kept) when more than
-// `cap` survive.
-constexpr uint32_t LAST_FLAG = 0x80000000u;
-
-template <int BPS>
-__device__ __forceinline__ uint32_t gather_append(const MatchParams &P, QEntry *q, uint32_t qn,
-                                                  uint32_t cap, uint32_t cand, uint32_t rootm,
-                                                  uint32_t lanes, const uint32_t (&bs)[BPS + 1],
-                                                  const uint8_t *sb, uint32_t staged,
-                                                  uint32_t unit, uint32_t lima, uint32_t limb,
-                                                  bool general_lims, uint64_t ustart,
-                                                  uint32_t rem, const uint32_t *Fs,
-                                                  const uint32_t *Cs, const uint32_t *Ms,
-                                                  uint32_t lane) {
-    const uint32_t m = ((lanes >> lane) & 1u) ? cand : 0u;
-    const uint32_t c = __popc(m);
-    const uint32_t kmask = (1u << (BPS * P.k)) - 1u;
-    const bool masks = P.tbl_m_words != 0 || P.tbl_g_words != 0;  // a second stage
-    const uint32_t lt = (1u << lane) - 1u;
-    const uint32_t p0 = lane * QBPT;
-
-    if (__reduce_max_sync(0xFFFFFFFFu, c) <= 2u) {
-        // per lane: second stage on the lane's own candidates, then a
-        // warp-wide rank of the kept ones
-        uint32_t keepm = m;
-        if (masks) {
-            uint32_t mm = m & ~rootm;
-            while (mm) {
-                const uint32_t j = __ffs(mm) - 1;
-                mm &= mm - 1;
-                const uint32_t p = p0 + j;
-                const uint32_t lim = lim_of(P, p, lima, limb, general_lims, ustart, rem);
-                if (!mask_keep(P, symbols_dyn<BPS>(bs, j) & kmask, p, lim, sb, staged, Fs, Cs, Ms))
-                    keepm &= ~(1u << j);
-            }
-        }
-        const uint32_t kc = __popc(keepm);
-        const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, kc >= 1u);
-        const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, kc >= 2u);
-        const uint32_t tot = __popc(b1) + __popc(b2);
-        if (tot > cap) return cap + 1;
-        uint32_t o = __popc(b1 & lt) + __popc(b2 & lt);
-        uint32_t mm = keepm;
-        while (mm) {
-            const uint32_t j = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const uint32_t p = p0 + j;
-            QEntry en;
-            en.unit = unit;
-            en.pos = p | (o << 10) | (o + 1 == tot ? LAST_FLAG : 0u);
-            en.x = ((rootm >> j) & 1u) ? ROOT_X : (symbols_dyn<BPS>(bs, j) & kmask);
-            en.lim = lim_of(P, p, lima, limb, general_lims, ustart, rem);
-            q[qn + o] = en;
-            o++;
-        }
-        __syncwarp();
-        return tot;
-    }
-
-    uint32_t inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-        if (lane >= (uint32_t)o) inc += nb;
-    }
-    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-    const uint32_t excl = inc - c;
-    uint32_t kept = 0;
-    bool flagged = false;  // the last kept entry carries LAST_FLAG
-    for (uint32_t base = 0; base < tot; base += 32) {
-        const uint32_t i = base + lane;
-        const bool valid = i < tot;
-        // owner: the last lane whose exclusive count is <= i
-        uint32_t L = 0;
-#pragma unroll
-        for (int st = 16; st >= 1; st >>= 1) {
-            const uint32_t v = __shfl_sync(0xFFFFFFFFu, excl, L + st);
-            if (v <= i) L += st;
-        }
-        const uint32_t exL = __shfl_sync(0xFFFFFFFFu, excl, L);
-        const uint32_t mL = __shfl_sync(0xFFFFFFFFu, m, L);
-        const uint32_t rL = __shfl_sync(0xFFFFFFFFu, rootm, L);
-        uint32_t bsL[BPS + 1];
-#pragma unroll
-        for (int w = 0; w <= BPS; w++) bsL[w] = __shfl_sync(0xFFFFFFFFu, bs[w], L);
-        const uint32_t laL = __shfl_sync(0xFFFFFFFFu, lima, L);
-        const uint32_t lbL = __shfl_sync(0xFFFFFFFFu, limb, L);
-        bool keep = false;
-        uint32_t p = 0, x = ROOT_X, lim = 0;
-        if (valid) {
-            const uint32_t j = __fns(mL, 0, (int)(i - exL) + 1);
-            p = L * QBPT + j;
-            lim = lim_of(P, p, laL, lbL, general_lims, ustart, rem);
-            keep = true;
-            if (!((rL >> j) & 1u)) {
-                x = symbols_dyn<BPS>(bsL, j) & kmask;
-                if (masks) keep = mask_keep(P, x, p, lim, sb, staged, Fs, Cs, Ms);
-            }
-        }
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
-        const uint32_t slot = kept + __popc(b & lt);
-        const uint32_t nk = kept + __popc(b);
-        if (nk > cap) return cap + 1;  // warp-uniform
-        const bool lastg = base + 32 >= tot;
-        if (keep) {
-            QEntry en;
-            en.unit = unit;
-            en.pos = p | (slot << 10) | (lastg && slot + 1 == nk ? LAST_FLAG : 0u);
-            en.x = x;
-            en.lim = lim;
-            q[qn + slot] = en;
-        }
-        if (lastg) flagged = b != 0;
-        kept = nk;
-    }
-    __syncwarp();
-    if (kept && !flagged) {
-        // every candidate of the last group was dropped: flag the last kept one
-        if (lane == 0) q[qn + kept - 1].pos |= LAST_FLAG;
-        __syncwarp();
-    }
-    return kept;
+    const uint32_t mb = mask_bits(sigma), ones = mb == 32 ? 0xFFFFFFFFu : (1u << mb) - 1u;
+    const uint32_t mr = mb == 32 ? Ms[r] : (Ms[(r * mb) >> 5] >> ((r * mb) & 31)) & ones;
+    const uint32_t cs = sb[qn1];
+    return cs < sigma ? ((mr >> child_hash(cs, sigma)) & 1u) != 0 : mr == ones;
 }
 
 // Record-mode flush: resolve the queue, then keep a record (position, fin)
@@ -659,6 +546,205 @@ __device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, u
     __syncwarp();
 }
 
+// Appends the candidates of the lanes set in `lanes` to the queue after the
+// second on-chip stage (mask_keep), in position order.  Entry fields: the
+// slice, the position, the slot among the slice's appended survivors and,
+// on the last one, LAST_FLAG; the prefix index (or ROOT_X); the walk limit.
+// Three ways, by the slice's candidates:
+//   * at most two per lane: every lane tests and writes its own;
+//   * at most QCAP: every lane parks its own candidates in the warp's
+//     scratch (the long-walk buffer, idle here), then lane i takes candidate
+//     i of each group of 32 for the test and the queue write;
+//   * more: candidate i of each group of 32 goes to lane i, which finds the
+//     owning lane by a shuffle search over the lanes' exclusive counts and
+//     the position in that lane's mask by __fns.
+// Returns AP_DONE (qn advanced), AP_FLUSH (the queue must be resolved first:
+// the caller flushes q[0, qn), moves the slice's st.kept entries at q[qn..]
+// to the front and calls again with qn = 0; the call resumes where it
+// stopped) or AP_OVER (more than a whole queue survives; qn is 0).
+enum { AP_DONE = 0, AP_FLUSH = 1, AP_OVER = 2 };
+struct AppendState {
+    uint32_t base;  // next group of 32 candidates (dense slices)
+    uint32_t kept;  // entries of this slice already in the queue
+    bool flagged;   // LAST_FLAG written
+};
+
+template <int BPS>
+__device__ __forceinline__ int append_slice(const MatchParams &P, QEntry *q, uint32_t qn,
+                                            AppendState &st, uint32_t cand, uint32_t rootm,
+                                            uint32_t lanes, const uint32_t (&bs)[BPS + 1],
+                                            const uint8_t *sb, uint32_t staged, uint32_t unit,
+                                            uint32_t lima, uint32_t limb, bool general_lims,
+                                            uint64_t ustart, uint32_t rem, const uint32_t *Fs,
+                                            const uint32_t *Cs, const uint32_t *Ms, uint32_t lane) {
+    const uint32_t m = ((lanes >> lane) & 1u) ? cand : 0u;
+    const uint32_t c = __popc(m);
+    const uint32_t k = P.k, kmask = (1u << (BPS * k)) - 1u;
+    const bool stage2 = P.tbl_m_words != 0 || P.tbl_g_words != 0;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t p0 = lane * QBPT;
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += nb;
+    }
+    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    const uint32_t excl = inc - c;
+    auto entry = [&](uint32_t p, uint32_t x, uint32_t lim, uint32_t slot, bool last) {
+        QEntry en;
+        en.unit = unit;
+        en.pos = p | (slot << 10) | (last ? LAST_FLAG : 0u);
+        en.x = x;
+        en.lim = lim;
+        return en;
+    };
+
+    if (__reduce_max_sync(0xFFFFFFFFu, c) <= 2u) {
+        // sparse: every lane tests and writes its own (at most two) candidates
+        uint32_t keepm = m;
+        if (stage2) {
+            uint32_t mm = m & ~rootm;
+            while (mm) {
+                const uint32_t j = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const uint32_t p = p0 + j;
+                if (!mask_keep(P, symbols_dyn<BPS>(bs, j) & kmask, p,
+                               lim_of(P, p, lima, limb, general_lims, ustart, rem), sb, staged,
+                               Fs, Cs, Ms))
+                    keepm &= ~(1u << j);
+            }
+        }
+        const uint32_t kc = __popc(keepm);
+        const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, kc >= 1u);
+        const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, kc >= 2u);
+        const uint32_t kept = __popc(b1) + __popc(b2);
+        if (qn + kept > (uint32_t)QCAP) return qn ? AP_FLUSH : AP_OVER;
+        uint32_t o = __popc(b1 & lt) + __popc(b2 & lt), mm = keepm;
+        while (mm) {
+            const uint32_t j = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t p = p0 + j;
+            const uint32_t x = ((rootm >> j) & 1u) ? ROOT_X : (symbols_dyn<BPS>(bs, j) & kmask);
+            q[qn + o] = entry(p, x, lim_of(P, p, lima, limb, general_lims, ustart, rem), o,
+                              o + 1 == kept);
+            o++;
+        }
+        __syncwarp();
+        st.kept = kept;
+        return AP_DONE;
+    }
+
+    if (tot <= (uint32_t)QCAP) {
+        // Each lane parks its candidates in the scratch as one word: position
+        // (9 bits), prefix index (21 bits; narrow symbols only, wide ones
+        // are re-read from the stage), root flag (bit 31).  The scratch is
+        // rebuilt when the call resumes after a flush, which reuses it.
+        uint32_t *scratch = reinterpret_cast<uint32_t *>(q + QCAP);  // QCAP words
+        uint32_t o = excl, mm = m;
+        while (mm) {
+            const uint32_t j = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t root = (rootm >> j) & 1u;
+            const uint32_t x = BPS <= 5 && !root ? (symbols_dyn<BPS>(bs, j) & kmask) : 0u;
+            scratch[o++] = (p0 + j) | (x << 9) | (root << 31);
+        }
+        __syncwarp();
+        for (; st.base < tot; st.base += 32) {
+            const uint32_t i = st.base + lane;
+            const bool valid = i < tot;
+            const uint32_t e = valid ? scratch[i] : 0u;
+            const uint32_t p = e & 511u;
+            // the owning lane's segment ends
+            const uint32_t laL = __shfl_sync(0xFFFFFFFFu, lima, p / QBPT);
+            const uint32_t lbL = __shfl_sync(0xFFFFFFFFu, limb, p / QBPT);
+            uint32_t x = ROOT_X, lim = 0;
+            bool keep = false;
+            if (valid) {
+                lim = lim_of(P, p, laL, lbL, general_lims, ustart, rem);
+                keep = true;
+                if (!(e >> 31)) {
+                    if (BPS <= 5) {
+                        x = (e >> 9) & 0x1FFFFFu;
+                    } else {
+                        // k <= 3 symbols of the window, first symbol lowest
+                        x = 0;
+                        for (uint32_t t = 0; t < k; t++)
+                            x |= ((uint32_t)sb[p + t] & ((1u << BPS) - 1u)) << (BPS * t);
+                    }
+                    if (stage2) keep = mask_keep(P, x, p, lim, sb, staged, Fs, Cs, Ms);
+                }
+            }
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
+            const uint32_t nk = st.kept + __popc(b);
+            if (qn + nk > (uint32_t)QCAP) {
+                __syncwarp();
+                return qn ? AP_FLUSH : AP_OVER;  // resume at this group
+            }
+            const uint32_t slot = st.kept + __popc(b & lt);
+            const bool lastg = st.base + 32 >= tot;
+            if (keep) q[qn + slot] = entry(p, x, lim, slot, lastg && slot + 1 == nk);
+            if (lastg) st.flagged = b != 0;
+            st.kept = nk;
+        }
+        __syncwarp();
+        if (st.kept && !st.flagged) {
+            // every candidate of the last group was dropped: flag the last kept one
+            if (lane == 0) q[qn + st.kept - 1].pos |= LAST_FLAG;
+            __syncwarp();
+        }
+        return AP_DONE;
+    }
+
+    for (; st.base < tot; st.base += 32) {
+        const uint32_t base = st.base;
+        const uint32_t i = base + lane;
+        const bool valid = i < tot;
+        // owner: the last lane whose exclusive count is <= i
+        uint32_t L = 0;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            const uint32_t v = __shfl_sync(0xFFFFFFFFu, excl, L + s);
+            if (v <= i) L += s;
+        }
+        const uint32_t exL = __shfl_sync(0xFFFFFFFFu, excl, L);
+        const uint32_t mL = __shfl_sync(0xFFFFFFFFu, m, L);
+        const uint32_t rL = __shfl_sync(0xFFFFFFFFu, rootm, L);
+        uint32_t bsL[BPS + 1];
+#pragma unroll
+        for (int w = 0; w <= BPS; w++) bsL[w] = __shfl_sync(0xFFFFFFFFu, bs[w], L);
+        const uint32_t laL = __shfl_sync(0xFFFFFFFFu, lima, L);
+        const uint32_t lbL = __shfl_sync(0xFFFFFFFFu, limb, L);
+        bool keep = false;
+        uint32_t p = 0, x = ROOT_X, lim = 0;
+        if (valid) {
+            const uint32_t j = __fns(mL, 0, (int)(i - exL) + 1);
+            p = L * QBPT + j;
+            lim = lim_of(P, p, laL, lbL, general_lims, ustart, rem);
+            keep = true;
+            if (!((rL >> j) & 1u)) {
+                x = symbols_dyn<BPS>(bsL, j) & kmask;
+                keep = mask_keep(P, x, p, lim, sb, staged, Fs, Cs, Ms);
+            }
+        }
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
+        const uint32_t nk = st.kept + __popc(b);
+        if (qn + nk > (uint32_t)QCAP) return qn ? AP_FLUSH : AP_OVER;  // resume at this group
+        const uint32_t slot = st.kept + __popc(b & lt);
+        const bool lastg = base + 32 >= tot;
+        if (keep) q[qn + slot] = entry(p, x, lim, slot, lastg && slot + 1 == nk);
+        if (lastg) st.flagged = b != 0;
+        st.kept = nk;
+    }
+    __syncwarp();
+    if (st.kept && !st.flagged) {
+        // every candidate of the last group was dropped: flag the last kept one
+        if (lane == 0) q[qn + st.kept - 1].pos |= LAST_FLAG;
+        __syncwarp();
+    }
+    return AP_DONE;
+}
+
 // Resolves every survivor of one slice in quarters of 8 lanes (at most 128
 // candidates each).  emit == 0: returns the slice's key count.  emit == 1:
 // writes the slice's keys at key_off[unit] and returns the count.
@@ -674,9 +760,10 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
     uint64_t keys = 0;
     const uint64_t obase = emit ? P.key_off[unitid] : 0;
     for (int qt = 0; qt < 4; qt++) {
-        const uint32_t n = gather_append<BPS>(P, q, 0, QCAP, cand, rootm, 0xFFu << (8 * qt), bs, sb,
-                                              staged, unitid, lima, limb, general_lims, ustart,
-                                              rem, Fs, Cs, Ms, lane);
+        AppendState ast{0u, 0u, false};
+        append_slice<BPS>(P, q, 0u, ast, cand, rootm, 0xFFu << (8 * qt), bs, sb, staged, unitid,
+                          lima, limb, general_lims, ustart, rem, Fs, Cs, Ms, lane);
+        const uint32_t n = ast.kept;  // a quarter has at most QCAP candidates
         if (n == 0) continue;
         resolve_batch<W, VAR>(P, q, n, Fs, Cs, Es, lane);
         uint32_t fin[QU], pos[QU];
@@ -776,6 +863,19 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
     __syncwarp();
 
     const bool multi = P.n_seg > 1;
+    // Segment data runs one slice ahead: while a slice is processed, the
+    // offset window of the next unit and the first-offset index of the one
+    // after it are in flight.
+    auto load_window = [&](uint32_t sf) -> uint64_t {
+        const uint32_t si = sf + lane;
+        return si <= P.n_seg ? __ldg(P.seg + si) : ~0ull;
+    };
+    uint64_t seg_o = ~0ull;  // this lane's offset of the current unit's window
+    uint32_t sf_n = 0;       // first offset index after the next unit's start
+    if (multi && gw < n_units) {
+        seg_o = load_window(__ldg(P.unit_seg + unit_of(0)));
+        if (gw + gstride < n_units) sf_n = __ldg(P.unit_seg + unit_of(1));
+    }
     uint32_t qn = 0;  // queued entries (warp-uniform)
     uint32_t i_fail = 0;
     bool failed = false;
@@ -791,11 +891,11 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
         uint32_t lima = rem, limb = rem;
         bool general_lims = false;
         if (multi) {
-            const uint32_t sf = __ldg(P.unit_seg + u);
-            const uint32_t si = sf + lane;
+            const uint64_t o = seg_o;
+            seg_o = gw + (i + 1) * gstride < n_units ? load_window(sf_n) : ~0ull;
+            if (gw + (i + 2) * gstride < n_units) sf_n = __ldg(P.unit_seg + unit_of(i + 2));
             uint32_t wv = LIM_MAX;
-            if (si <= P.n_seg) {
-                const uint64_t o = __ldg(P.seg + si);
+            if (o != ~0ull) {
                 const uint64_t r = o > ustart ? o - ustart : 0;
                 wv = r < rem ? (uint32_t)r : rem;
             }
@@ -843,23 +943,32 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
         } else {
             // tile_m / tile_k start at zero; the slice's last entry sets its
             // record count when resolved
-            uint32_t got = 0;
+            int ar = AP_DONE;
             if (cnt) {
-                got = gather_append<BPS>(P, A.q, qn, QCAP - qn, cand, rootm, 0xFFFFFFFFu, bs, sb,
-                                         staged, u, lima, limb, general_lims, ustart, rem, Fs, Cs,
-                                         Ms, lane);
-                if (got > (uint32_t)QCAP - qn && qn > 0) {
-                    // the queue is full: resolve it, then append again
+                AppendState ast{0u, 0u, false};
+                for (;;) {
+                    ar = append_slice<BPS>(P, A.q, qn, ast, cand, rootm, 0xFFFFFFFFu, bs, sb,
+                                           staged, u, lima, limb, general_lims, ustart, rem, Fs, Cs,
+                                           Ms, lane);
+                    if (ar != AP_FLUSH) break;
+                    // resolve the queue, move the slice's entries to its front
                     flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
+                    for (uint32_t e0 = 0; e0 < ast.kept; e0 += 32) {
+                        const uint32_t e = e0 + lane;
+                        QEntry t;
+                        if (e < ast.kept) t = A.q[qn + e];
+                        __syncwarp();
+                        if (e < ast.kept) A.q[e] = t;
+                        __syncwarp();
+                    }
                     qn = 0;
-                    got = gather_append<BPS>(P, A.q, 0, QCAP, cand, rootm, 0xFFFFFFFFu, bs, sb,
-                                             staged, u, lima, limb, general_lims, ustart, rem, Fs,
-                                             Cs, Ms, lane);
                 }
+                if (ar == AP_DONE) qn += ast.kept;
             }
-            if (got > (uint32_t)QCAP - qn) {
-                // more survivors than the queue holds: count now, emit later
-                const uint64_t keys = resolve_slice<W, BPS, VAR>(P, A.q + qn, cand, rootm, bs, sb,
+            if (ar == AP_OVER) {
+                // more survivors than the (now empty) queue holds: count now,
+                // emit later
+                const uint64_t keys = resolve_slice<W, BPS, VAR>(P, A.q, cand, rootm, bs, sb,
                                                                  staged, u, lima, limb,
                                                                  general_lims, ustart, rem, Fs,
                                                                  Cs, Es, Ms, lane, false);
@@ -868,8 +977,6 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
                     P.tile_k[u] = keys;
                     P.ovf_list[atomicAdd(&P.hdr->ovf_count, 1u)] = u;
                 }
-            } else {
-                qn += got;
             }
         }
         // the stage is consumed: refill it with the unit QRING ahead

@@ -306,6 +306,16 @@ static double load_wavefronts(int rep) {
     return wf[rep < 0 ? 0 : (rep > 5 ? 5 : rep)];
 }
 
+// Estimated warp instructions per 512-byte slice of a first stage that
+// passes a share `dens` of the positions (measured orders of magnitude:
+// ~9 per tested position row, 2 more for hashing, bank-conflict replays,
+// ~90 for a slice with any candidate and ~12 per candidate).
+static double first_stage_cost(double dens, int rep, bool hashed) {
+    const double cand = dens * 512.0;
+    return (hashed ? 176.0 : 144.0) + 48.0 * (load_wavefronts(rep) - 1.0) +
+           90.0 * (1.0 - exp(-cand)) + 12.0 * cand;
+}
+
 static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl) {
     const DevTable &T = t->dev;
     memset(pl, 0, sizeof(*pl));
@@ -339,6 +349,11 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     const uint32_t masks = opts && opts->child_masks ? opts->child_masks
                                                     : (use_tuned ? t->tuned_masks : 0u);
     if (masks > 2) return set_error(PFAC_EINVAL, "pfac_match: child_masks %u", masks);
+    const bool have_m = T.M[k] != nullptr;
+    const uint32_t mw = T.m_words[k];  // words of the packed child masks
+    if (masks == 2 && !have_m)
+        return set_error(PFAC_EINVAL, "pfac_match: depth %u keeps no child masks (too many "
+                         "entries for shared memory)", k);
     const uint32_t gram = opts && opts->gram_filter ? opts->gram_filter
                                                    : (use_tuned ? t->tuned_gram : 0u);
     if (gram > 2) return set_error(PFAC_EINVAL, "pfac_match: gram_filter %u", gram);
@@ -371,8 +386,8 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     }
     const uint32_t e_f = var_f == VAR_FE ? ew : 0u;
     // child masks: with them if they fit (or on request), then the most copies
-    const bool m_f = masks == 2 || (masks == 0 && best_rep(e_f + ew) >= 0);
-    int rep_f = best_rep(e_f + (m_f ? ew : 0u));
+    const bool m_f = have_m && (masks == 2 || (masks == 0 && best_rep(e_f + mw) >= 0));
+    int rep_f = best_rep(e_f + (m_f ? mw : 0u));
     if (want >= 0 && want <= rep_f) rep_f = want;
     else if (want >= 0) rep_f = -2;  // the requested copies do not fit
     const double dens_f = (double)ew / (double)ent;
@@ -381,37 +396,49 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     // exact test of survivors), the filter folded (adjacent words OR-ed)
     // until the chosen copies fit
     bool use_g = false;
-    int var_g = var, rep_g = -1;
+    int var_g = 0, rep_g = -1;
     uint32_t fold_g = 0;
     bool m_g = false;
     double cost_g = 1e30;
     if (T.g_len && gram != 1) {
         const uint32_t hb = T.g_bits;
         const uint64_t gw0 = (1ull << hb) / 32;
-        if (var_g == 0) var_g = queued_smem(fw + cw + ew + (gw0 >> (hb - GRAM_MIN_BITS))) <= SMEM_LIMIT
-                                    ? VAR_FE : VAR_F;
-        const uint32_t e_g = var_g == VAR_FE ? ew : 0u;
-        m_g = masks == 2 || (masks == 0 && queued_smem(fw + cw + e_g + ew +
-                                                       (gw0 >> (hb - GRAM_MIN_BITS))) <= SMEM_LIMIT);
-        const uint64_t base = fw + cw + e_g + (m_g ? ew : 0u);
-        for (int r = 0; r <= 5; r++) {
-            if (want >= 0 && r != want) continue;
-            for (uint32_t f = 0; hb - f >= GRAM_MIN_BITS; f++) {
-                if (queued_smem(base + ((gw0 >> f) << r)) > SMEM_LIMIT) continue;
-                // expected share of positions through the first stage
-                const double dens = 1.0 - exp(-(double)T.g_set / (double)(1ull << (hb - f)));
-                const double c = load_wavefronts(r) + 100.0 * dens;
-                if (c < cost_g) {
-                    cost_g = c;
-                    rep_g = r;
-                    fold_g = f;
+        // entries and child masks in shared memory compete with the filter's
+        // bits: every allowed combination is costed, keeping them when that
+        // costs little
+        for (int vv = VAR_FE; vv >= VAR_F; vv--) {
+            if (var != 0 && var != vv) continue;
+            for (int mm = 1; mm >= 0; mm--) {
+                const bool mon = mm == 1;
+                if (mon && !(have_m && masks != 1)) continue;
+                if (!mon && masks == 2) continue;
+                const uint64_t base = fw + cw + (vv == VAR_FE ? ew : 0u) + (mon ? mw : 0u);
+                // a small preference for what keeps the walks short
+                const double bias = (vv == VAR_FE ? 1.0 : 1.05) * (mon ? 1.0 : 1.1);
+                for (int r = 0; r <= 5; r++) {
+                    if (want >= 0 && r != want) continue;
+                    for (uint32_t f = 0; hb - f >= GRAM_MIN_BITS; f++) {
+                        if (queued_smem(base + ((gw0 >> f) << r)) > SMEM_LIMIT) continue;
+                        // expected share of positions through the first stage
+                        const double dens =
+                            1.0 - exp(-(double)T.g_set / (double)(1ull << (hb - f)));
+                        const double c = first_stage_cost(dens, r, true) * bias;
+                        if ((gram == 2 || dens < 0.5) && c < cost_g) {
+                            cost_g = c;
+                            rep_g = r;
+                            fold_g = f;
+                            var_g = vv;
+                            m_g = mon;
+                        }
+                        break;  // the least folding that fits
+                    }
                 }
-                break;  // the least folding that fits
             }
         }
         if (rep_g >= 0) {
-            const double cost_f = rep_f >= 0 ? load_wavefronts(rep_f) + 100.0 * dens_f : 1e30;
-            use_g = gram == 2 || cost_g < 0.8 * cost_f;
+            const double cost_f =
+                rep_f >= 0 ? first_stage_cost(dens_f, rep_f, false) * (m_f ? 1.0 : 1.1) : 1e30;
+            use_g = gram == 2 || cost_g < cost_f;
         } else if (gram == 2) {
             return set_error(PFAC_EINVAL, "pfac_match: the gram filter does not fit in shared "
                              "memory with depth %u%s", k, want >= 0 ? " and these copies" : "");
@@ -422,7 +449,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
         pl->rep_log2 = 0;
         pl->tbl_words = fw;
         pl->tbl_e_words = var == VAR_FE ? ew : 0u;
-        pl->tbl_m_words = m_g ? ew : 0u;
+        pl->tbl_m_words = m_g ? mw : 0u;
         pl->g_rep = (uint32_t)rep_g;
         pl->g_fold = fold_g;
         pl->tbl_g_words = (uint32_t)((((1ull << T.g_bits) / 32) >> fold_g) << rep_g);
@@ -437,7 +464,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
         pl->rep_log2 = (uint32_t)rep_f;
         pl->tbl_words = (uint32_t)((uint64_t)fw << rep_f);
         pl->tbl_e_words = e_f;
-        pl->tbl_m_words = m_f ? ew : 0u;
+        pl->tbl_m_words = m_f ? mw : 0u;
     }
     pl->var = var;
     pl->k = k;

@@ -45,6 +45,7 @@
 namespace pfac {
 
 constexpr int KMAX = 16;                 // largest prefix depth held
+constexpr uint64_t MASKS_MAX_BYTES = 96 * 1024;  // child masks kept up to this size
 constexpr uint32_t META_ALL_LEAF = 0x80000000u;
 constexpr uint32_t META_BASE_MASK = 0x7FFFFFFFu;
 constexpr uint32_t D_CONT = 0x80000000u;  // prefix entry: continue at record
@@ -70,6 +71,12 @@ constexpr uint32_t GRAM_MUL = 0x9E3779B1u;
 constexpr uint32_t GRAM_MIN_BITS = 10, GRAM_MAX_BITS = 20;
 __host__ __device__ inline uint32_t gram_word(uint32_t y, uint32_t hb) { return y >> (37 - hb); }
 
+// Bits per child mask: 4 for alphabets of up to 4 symbols, 8 up to 8, else
+// 32 (an all-ones mask: the entry reports output, or has every child).
+__host__ __device__ inline uint32_t mask_bits(uint32_t sigma) {
+    return sigma <= 4 ? 4u : (sigma <= 8 ? 8u : 32u);
+}
+
 // Bit of symbol c in a child mask: exact for alphabets of up to 32 symbols.
 __host__ __device__ inline uint32_t child_hash(uint32_t c, uint32_t sigma) {
     return sigma <= 32 ? c : ((c ^ (c >> 5)) & 31u);
@@ -93,8 +100,10 @@ struct DevTable {
     const uint32_t *C[KMAX + 1];   // set bits of F_k before each group of 2^c_shift words
     uint32_t c_shift[KMAX + 1];    // 0 (a count per word) or 3 (per 8 words)
     const uint32_t *E[KMAX + 1];   // entries of the set bits of F_k
-    const uint32_t *M[KMAX + 1];   // per entry: hashed symbols its state continues with
+    const uint32_t *M[KMAX + 1];   // per entry: hashed symbols its state continues with,
+                                   // packed (nullptr when too large to be used)
     uint32_t n_e[KMAX + 1];        // number of entries of depth k
+    uint32_t m_words[KMAX + 1];    // words of M_k (mask_bits(sigma) bits per entry)
     const uint32_t *G;             // gram filter (nullptr when none)
     uint32_t g_len;                // g: symbols per gram
     uint32_t g_bits;               // hb: log2 of the bits of G
