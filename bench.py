@@ -272,6 +272,8 @@ def run_ours(args):
         user_opt["child_masks"] = args.masks
     if args.gram:
         user_opt["gram_filter"] = args.gram
+    if args.bytes:
+        user_opt["prefix_bytes"] = args.bytes
     tune = None
     if not args.no_autotune and not user_opt:
         # the autotuner on a bounded prefix sample of the input (whole
@@ -534,6 +536,7 @@ def main():
     ap.add_argument("--copies", type=int, default=0, help="prefix-bitmap copies in smem")
     ap.add_argument("--masks", type=int, default=0, help="child masks: 1 off, 2 on")
     ap.add_argument("--gram", type=int, default=0, help="gram filter first stage: 1 off, 2 on")
+    ap.add_argument("--bytes", type=int, default=0, help="prefix bytes first stage: 1 off, 2 on")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip pfac_autotune on a sample of the input (it runs by default "
                          "when no scan option is given)")

@@ -106,7 +106,14 @@ typedef struct {
                               library expects it to pass fewer positions,
                               1 = off, 2 = required.  With it, bitmap_copies
                               counts copies of the gram filter. */
-    uint32_t reserved[2];
+    uint32_t prefix_bytes; /* first on-chip stage over one byte per prefix
+                              index (prefix nodes of at most 16 index bits):
+                              nonzero for indices with an entry, with a
+                              bucket mask of the next symbols that can follow
+                              as a cheap second stage.  0 = library choice,
+                              1 = off, 2 = required (one copy; excludes the
+                              gram filter and bitmap_copies > 1) */
+    uint32_t reserved[1];
 } pfac_match_opts;
 
 typedef struct {
@@ -170,7 +177,7 @@ typedef struct {
     uint32_t gram_filter;    /* 1 = off, 2 = on */
     uint32_t gram_bits;      /* log2 of the bits of one shared copy of the gram filter */
     uint32_t smem_bytes;     /* dynamic shared memory per CTA of the scan kernel */
-    uint32_t reserved;
+    uint32_t prefix_bytes;   /* 1 = off, 2 = on */
 } pfac_plan_info;
 int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts, pfac_plan_info *out);
 
@@ -270,6 +277,7 @@ typedef struct {
     float default_ms;    /* scan-kernel time of the library default */
     int from_cache;
     uint32_t gram_filter; /* 1 = off, 2 = on */
+    uint32_t prefix_bytes; /* 1 = off, 2 = on */
 } pfac_tune_result;
 
 int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,

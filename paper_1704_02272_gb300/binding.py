@@ -47,7 +47,7 @@ class MatchOpts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("bitmap_copies", ctypes.c_uint32),
                 ("ev_scan_begin", ctypes.c_void_p), ("ev_scan_end", ctypes.c_void_p),
                 ("child_masks", ctypes.c_uint32), ("gram_filter", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("prefix_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
 
 
 class TableInfo(ctypes.Structure):
@@ -67,14 +67,15 @@ class TuneResult(ctypes.Structure):
                 ("bitmap_copies", ctypes.c_uint32), ("child_masks", ctypes.c_uint32),
                 ("n_tried", ctypes.c_uint32),
                 ("scan_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
-                ("from_cache", ctypes.c_int), ("gram_filter", ctypes.c_uint32)]
+                ("from_cache", ctypes.c_int), ("gram_filter", ctypes.c_uint32),
+                ("prefix_bytes", ctypes.c_uint32)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
                 ("bitmap_copies", ctypes.c_uint32), ("child_masks", ctypes.c_uint32),
                 ("gram_filter", ctypes.c_uint32), ("gram_bits", ctypes.c_uint32),
-                ("smem_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("smem_bytes", ctypes.c_uint32), ("prefix_bytes", ctypes.c_uint32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -161,10 +162,11 @@ def _stream(stream) -> int:
 
 
 def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,
-          gram_filter=0, scan_events=None):
+          gram_filter=0, prefix_bytes=0, scan_events=None):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
     o.bitmap_copies, o.child_masks, o.gram_filter = bitmap_copies, child_masks, gram_filter
+    o.prefix_bytes = prefix_bytes
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event
@@ -251,7 +253,7 @@ def plan(table: Table, **opt) -> dict:
     o = _opts(**opt)
     r = PlanInfo()
     _check(LIB.pfac_match_plan(table.handle, ctypes.byref(o), ctypes.byref(r)))
-    return {f: getattr(r, f) for f, _ in PlanInfo._fields_ if f != "reserved"}
+    return {f: getattr(r, f) for f, _ in PlanInfo._fields_}
 
 
 def match_async(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,

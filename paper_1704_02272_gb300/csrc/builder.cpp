@@ -289,9 +289,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         // prefix node of depth k: bitmap, block counts, entries (Eq. 1 on the
         // collapsed first k levels)
         std::vector<uint32_t> Fv[KMAX + 1], Cv[KMAX + 1], Ev[KMAX + 1], Mv[KMAX + 1];
+        std::vector<uint8_t> Bv[KMAX + 1];
         uint32_t cshift[KMAX + 1] = {0};
         uint64_t sz_F[KMAX + 1] = {0}, sz_C[KMAX + 1] = {0}, sz_E[KMAX + 1] = {0},
-                 sz_M[KMAX + 1] = {0};
+                 sz_M[KMAX + 1] = {0}, sz_B[KMAX + 1] = {0};
         if (!dense)
             for (uint32_t k = kmin; k <= kmax; k++) {
                 const uint64_t ent = 1ull << (k * bps);
@@ -303,6 +304,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 Fv[k].assign(fw, 0);
                 Cv[k].assign((fw + (1ull << cs) - 1) >> cs, 0);
                 cshift[k] = cs;
+                const bool with_b = k * bps <= BYTES_MAX_BITS;
+                if (with_b) Bv[k].assign(ent < 4 ? 4 : ent, 0);
                 for (uint64_t x = 0; x < ent; x++) {
                     uint32_t v = 0, e = 0;
                     bool stopped = false;
@@ -315,7 +318,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                         }
                         v = (uint32_t)ch;
                     }
-                    uint32_t mask = 0xFFFFFFFFu;
+                    uint32_t mask = 0xFFFFFFFFu, bucket = 0xFFu;
                     if (!stopped) {
                         if (nodes[v].n_child == 0) {
                             e = fin_code[v];  // a leaf ends the walk
@@ -323,9 +326,12 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                             e = D_CONT | rec_of[v];
                             if (fin_code[v] == 0) {
                                 mask = 0;
+                                bucket = 0;
                                 for (uint32_t c = 0; c < sigma; c++)
-                                    if ((bm[(uint64_t)v * W + (c >> 5)] >> (c & 31)) & 1)
+                                    if ((bm[(uint64_t)v * W + (c >> 5)] >> (c & 31)) & 1) {
                                         mask |= 1u << child_hash(c, sigma);
+                                        bucket |= 1u << byte_bucket(c, sigma);
+                                    }
                             }
                         }
                     }
@@ -333,6 +339,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                         Fv[k][x >> 5] |= 1u << (x & 31);
                         Ev[k].push_back(e);
                         Mv[k].push_back(mask);
+                        if (with_b) Bv[k][x] = (uint8_t)bucket;
                     }
                 }
                 uint32_t run = 0;
@@ -362,6 +369,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 // entries could never fit there
                 if (Mv[k].size() * 4 > MASKS_MAX_BYTES) Mv[k].clear();
                 sz_M[k] = Mv[k].size() * 4;
+                sz_B[k] = Bv[k].size();
             }
         // ---- gram filter over g = kmax + 1 symbols (see table.h) -----------
         uint32_t g_len = 0, g_bits = 0;
@@ -491,13 +499,14 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         uint64_t o_rec = place(sz_rec), o_fin = place(sz_fin), o_leaf = place(sz_leaf),
                  o_pool = place(sz_pool);
         uint64_t o_F[KMAX + 1] = {0}, o_C[KMAX + 1] = {0}, o_E[KMAX + 1] = {0},
-                 o_M[KMAX + 1] = {0};
+                 o_M[KMAX + 1] = {0}, o_B[KMAX + 1] = {0};
         if (!dense)
             for (uint32_t k = kmin; k <= kmax; k++) {
                 o_F[k] = place(sz_F[k]);
                 o_C[k] = place(sz_C[k]);
                 o_E[k] = place(sz_E[k]);
                 o_M[k] = place(sz_M[k]);
+                o_B[k] = place(sz_B[k]);
             }
         const uint64_t o_G = place(sz_G);
         uint64_t o_stt = place(sz_stt), o_dfin = place(sz_dfin);
@@ -518,6 +527,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 put(o_C[k], Cv[k].data(), sz_C[k]);
                 put(o_E[k], Ev[k].data(), sz_E[k]);
                 put(o_M[k], Mv[k].data(), sz_M[k]);
+                put(o_B[k], Bv[k].data(), sz_B[k]);
             }
         put(o_G, Gv.data(), sz_G);
         if (dense) {
@@ -582,6 +592,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 dv.c_shift[k] = cshift[k];
                 dv.n_e[k] = (uint32_t)Ev[k].size();
                 dv.m_words[k] = (uint32_t)Mv[k].size();
+                dv.B[k] = sz_B[k] ? (const uint8_t *)(B + o_B[k]) : nullptr;
             }
         dv.G = g_len ? (const uint32_t *)(B + o_G) : nullptr;
         dv.g_len = g_len;

@@ -95,6 +95,8 @@ struct MatchParams {
     uint32_t g_fold;      // gram filter words OR-ed together per shared word (log2)
     uint32_t g_hb;        // log2 of the shared gram filter's bits per copy
     uint32_t kf;          // symbols the first stage tests: k, or g with the gram filter
+    const uint8_t *Bt;    // prefix bytes of depth k
+    uint32_t tbl_b_words; // prefix bytes in shared memory as the first stage (0 = not used)
     uint32_t dense_rows;  // dense layout: states whose rows live in shared memory
 };
 

@@ -310,7 +310,7 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
                                              uint32_t lima, uint32_t limb, bool general_lims,
                                              const uint64_t *__restrict__ gseg, uint64_t ustart,
                                              const uint32_t *Fs, const uint32_t *Gs,
-                                             uint32_t lane, uint32_t &surv,
+                                             const uint32_t *Bs, uint32_t lane, uint32_t &surv,
                                              uint32_t &rootm, uint32_t (&bs)[BPS + 1]) {
     const uint32_t p0 = lane * QBPT;
     const uint32_t k = P.kf, rep = P.rep_log2;
@@ -325,7 +325,14 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
     const uint4 b = *reinterpret_cast<const uint4 *>(sb + p0 + 16);
     const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     pack_symbols<BPS>(x, bs);
-    if (P.tbl_g_words == 0) {
+    if (P.tbl_b_words) {
+        // prefix bytes: one byte per index, nonzero when the index has an entry
+        const uint32_t kmask = (1u << (BPS * k)) - 1u;
+        const uint8_t *Bb = reinterpret_cast<const uint8_t *>(Bs);
+#pragma unroll
+        for (int j = 0; j < QBPT; j++)
+            if (Bb[symbols_at<BPS>(bs, j) & kmask]) surv |= 1u << j;
+    } else if (P.tbl_g_words == 0) {
         const uint32_t kmask = (1u << (BPS * k)) - 1u;  // k * BPS >= 5
         // Byte offset of the word of index t in copy `copy`:
         // ((((t & kmask) >> 5) << rep) | copy) * 4.  Rotating t right by
@@ -455,9 +462,11 @@ __device__ __forceinline__ uint32_t symbols_dyn(const uint32_t (&bs)[BPS + 1], u
     return __funnelshift_r(lo, hi, bit & 31);
 }
 
-// Second on-chip stage for one survivor.  With the gram filter as the first
-// stage, the prefix index must be set in F_k (the filter may let other
-// positions through).  With child masks, a survivor whose depth-k state
+// Second on-chip stage for one survivor.  With prefix bytes as the first
+// stage, the next symbol's bucket must be set in the index's byte (or the
+// byte is 0xFF).  With the gram filter as the first stage, the prefix index
+// must be set in F_k (the filter may let other positions through).  With
+// child masks, a survivor whose depth-k state
 // reports nothing and has no child on the next symbol (read from the staged
 // slice) stops there silently and is dropped: an entry that reports output
 // has an all-ones mask and is kept whatever follows; a byte outside the
@@ -467,6 +476,15 @@ __device__ __forceinline__ bool mask_keep(const MatchParams &P, uint32_t x, uint
                                           uint32_t lim, const uint8_t *sb, uint32_t staged,
                                           const uint32_t *Fs, const uint32_t *Cs,
                                           const uint32_t *Ms) {
+    if (P.tbl_b_words) {
+        // the prefix byte's bucket of the next symbol (shared memory offset 0)
+        const uint32_t qb = p + P.k, sigma = P.T.sigma;
+        if (qb < staged && qb < lim) {
+            extern __shared__ __align__(128) uint8_t smem[];
+            const uint32_t v = smem[x], cs = sb[qb];
+            if (v != 0xFFu && (cs >= sigma || !((v >> byte_bucket(cs, sigma)) & 1u))) return false;
+        }
+    }
     if (P.tbl_g_words) {
         const uint32_t fwd = Fs[(x >> 5) << P.rep_log2];
         if (!((fwd >> (x & 31)) & 1u)) return false;
@@ -580,7 +598,7 @@ __device__ __forceinline__ int append_slice(const MatchParams &P, QEntry *q, uin
     const uint32_t m = ((lanes >> lane) & 1u) ? cand : 0u;
     const uint32_t c = __popc(m);
     const uint32_t k = P.k, kmask = (1u << (BPS * k)) - 1u;
-    const bool stage2 = P.tbl_m_words != 0 || P.tbl_g_words != 0;
+    const bool stage2 = P.tbl_m_words != 0 || P.tbl_g_words != 0 || P.tbl_b_words != 0;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t p0 = lane * QBPT;
     uint32_t inc = c;
@@ -810,14 +828,15 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
     const uint32_t gw = blockIdx.x * QW + warp, gstride = gridDim.x * QW;
     if (blockIdx.x * QW >= n_units) return;  // the whole CTA has no unit
 
-    uint32_t *Fs = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *Bs = reinterpret_cast<uint32_t *>(smem);  // prefix bytes, at offset 0
+    uint32_t *Fs = Bs + P.tbl_b_words;
     uint32_t *Cs = Fs + P.tbl_words;
     uint32_t *Es = Cs + P.tbl_c_words;
     uint32_t *Ms = Es + P.tbl_e_words;
     uint32_t *Gs = Ms + P.tbl_m_words;
     WarpArea *areas = reinterpret_cast<WarpArea *>(
-        smem + ((((size_t)P.tbl_words + P.tbl_c_words + P.tbl_e_words + P.tbl_m_words +
-                  P.tbl_g_words) * 4 + 127) &
+        smem + ((((size_t)P.tbl_b_words + P.tbl_words + P.tbl_c_words + P.tbl_e_words +
+                  P.tbl_m_words + P.tbl_g_words) * 4 + 127) &
                 ~(size_t)127));
     {
         const uint32_t rep = P.rep_log2;
@@ -826,6 +845,8 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
         if (VAR == VAR_FE)
             for (uint32_t i = threadIdx.x; i < P.tbl_e_words; i += QTHREADS) Es[i] = __ldg(P.E + i);
         for (uint32_t i = threadIdx.x; i < P.tbl_m_words; i += QTHREADS) Ms[i] = __ldg(P.M + i);
+        const uint32_t *bsrc = reinterpret_cast<const uint32_t *>(P.Bt);
+        for (uint32_t i = threadIdx.x; i < P.tbl_b_words; i += QTHREADS) Bs[i] = __ldg(bsrc + i);
         // gram filter: word w of each copy is the OR of 2^g_fold table words
         const uint32_t gr = P.g_rep, gf = P.g_fold;
         for (uint32_t i = threadIdx.x; i < P.tbl_g_words; i += QTHREADS) {
@@ -933,7 +954,7 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
         const uint8_t *sb = A.ring[s];
         uint32_t surv, rootm, bs[BPS + 1];
         filter_slice<BPS>(P, sb, staged, valid, rem, lima, limb, general_lims, P.seg, ustart, Fs,
-                          Gs, lane, surv, rootm, bs);
+                          Gs, Bs, lane, surv, rootm, bs);
         const uint32_t cand = surv | rootm;
         const uint32_t cnt = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(cand));
 

@@ -231,6 +231,7 @@ struct Plan {
     uint32_t tbl_words, tbl_c_words, tbl_e_words, tbl_m_words;
     uint32_t rep_log2;
     uint32_t tbl_g_words, g_rep, g_fold;  // gram filter: words (all copies), copies, fold
+    uint32_t tbl_b_words;                 // prefix bytes as the first stage
     uint32_t dense_rows;
     uint32_t unit_shift, unit_cap;
     void *kernel;       // scan pass
@@ -359,6 +360,15 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     if (gram > 2) return set_error(PFAC_EINVAL, "pfac_match: gram_filter %u", gram);
     if (gram == 2 && !T.g_len)
         return set_error(PFAC_EINVAL, "pfac_match: the table has no gram filter");
+    const uint32_t pbytes = opts && opts->prefix_bytes ? opts->prefix_bytes
+                                                      : (use_tuned ? t->tuned_bytes : 0u);
+    if (pbytes > 2) return set_error(PFAC_EINVAL, "pfac_match: prefix_bytes %u", pbytes);
+    if (pbytes == 2 && !T.B[k])
+        return set_error(PFAC_EINVAL, "pfac_match: depth %u has no prefix bytes (more than %u "
+                         "index bits)", k, BYTES_MAX_BITS);
+    if (pbytes == 2 && gram == 2)
+        return set_error(PFAC_EINVAL, "pfac_match: prefix bytes and the gram filter exclude "
+                         "each other");
     const uint32_t copies = opts && opts->bitmap_copies ? opts->bitmap_copies
                                                        : (use_tuned ? t->tuned_copies : 0u);
     int want = -1;
@@ -444,7 +454,43 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                              "memory with depth %u%s", k, want >= 0 ? " and these copies" : "");
         }
     }
-    if (use_g) {
+    // ---- prefix bytes as the first stage (one copy): the prefix bitmap once
+    // for ranks, then entries and child masks as they fit.  By default for
+    // prefix nodes whose bitmap passes at least 1% of the positions (where
+    // the cheaper second stage pays), unless the gram filter is chosen.
+    bool use_b = false;
+    int var_b = 0;
+    bool m_b = false;
+    if (T.B[k] && pbytes != 1 && gram != 2 && (want <= 0)) {
+        const uint64_t bw = ent / 4;
+        for (int vv = VAR_FE; vv >= VAR_F && !use_b; vv--) {
+            if (var != 0 && var != vv) continue;
+            for (int mm = 1; mm >= 0; mm--) {
+                const bool mon = mm == 1;
+                if (mon && !(have_m && masks != 1)) continue;
+                if (!mon && masks == 2) continue;
+                if (queued_smem(bw + fw + cw + (vv == VAR_FE ? ew : 0u) + (mon ? mw : 0u)) <=
+                    SMEM_LIMIT) {
+                    var_b = vv;
+                    m_b = mon;
+                    use_b = pbytes == 2 || (!use_g && dens_f >= 0.01);
+                    break;
+                }
+            }
+        }
+        if (pbytes == 2 && !use_b)
+            return set_error(PFAC_EINVAL, "pfac_match: prefix bytes of depth %u do not fit in "
+                             "shared memory", k);
+    }
+    if (use_b) {
+        use_g = false;
+        var = var_b;
+        pl->rep_log2 = 0;
+        pl->tbl_words = fw;
+        pl->tbl_e_words = var == VAR_FE ? ew : 0u;
+        pl->tbl_m_words = m_b ? mw : 0u;
+        pl->tbl_b_words = (uint32_t)(ent / 4);
+    } else if (use_g) {
         var = var_g;
         pl->rep_log2 = 0;
         pl->tbl_words = fw;
@@ -471,8 +517,8 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     pl->tbl_c_words = cw;
     pl->kernel = scan_kernel_for(T.bps, var, 0);
     pl->kernel_emit = scan_kernel_for(T.bps, var, 1);
-    pl->smem = queued_smem((uint64_t)pl->tbl_words + pl->tbl_c_words + pl->tbl_e_words +
-                           pl->tbl_m_words + pl->tbl_g_words);
+    pl->smem = queued_smem((uint64_t)pl->tbl_b_words + pl->tbl_words + pl->tbl_c_words +
+                           pl->tbl_e_words + pl->tbl_m_words + pl->tbl_g_words);
     pl->unit_shift = SLICE_SHIFT;
     pl->unit_cap = SCAP;
     pl->queued = true;
@@ -544,6 +590,7 @@ extern "C" int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts,
     out->child_masks = pl.tbl_m_words ? 2u : 1u;
     out->gram_filter = g ? 2u : 1u;
     out->gram_bits = g ? t->dev.g_bits - pl.g_fold : 0u;
+    out->prefix_bytes = pl.tbl_b_words ? 2u : 1u;
     return PFAC_OK;
 }
 
@@ -614,6 +661,8 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.g_fold = pl.g_fold;
     P.g_hb = pl.tbl_g_words ? t->dev.g_bits - pl.g_fold : 0u;
     P.kf = pl.tbl_g_words ? t->dev.g_len : pl.k;
+    P.Bt = pl.k ? t->dev.B[pl.k] : nullptr;
+    P.tbl_b_words = pl.tbl_b_words;
     P.tbl_words = pl.tbl_words;
     P.tbl_c_words = pl.tbl_c_words;
     P.tbl_e_words = pl.tbl_e_words;

@@ -77,6 +77,15 @@ __host__ __device__ inline uint32_t mask_bits(uint32_t sigma) {
     return sigma <= 4 ? 4u : (sigma <= 8 ? 8u : 32u);
 }
 
+// Prefix bytes (an optional first stage for prefix indices of at most 16
+// bits): B_k[x] = 0 when index x has no entry; 0xFF when the entry reports
+// output (or the state has children in every bucket); else bit byte_bucket(c)
+// set for every child symbol c of the depth-k state.
+constexpr uint32_t BYTES_MAX_BITS = 16;
+__host__ __device__ inline uint32_t byte_bucket(uint32_t c, uint32_t sigma) {
+    return sigma <= 8 ? c : ((c ^ (c >> 3) ^ (c >> 6)) & 7u);
+}
+
 // Bit of symbol c in a child mask: exact for alphabets of up to 32 symbols.
 __host__ __device__ inline uint32_t child_hash(uint32_t c, uint32_t sigma) {
     return sigma <= 32 ? c : ((c ^ (c >> 5)) & 31u);
@@ -104,6 +113,7 @@ struct DevTable {
                                    // packed (nullptr when too large to be used)
     uint32_t n_e[KMAX + 1];        // number of entries of depth k
     uint32_t m_words[KMAX + 1];    // words of M_k (mask_bits(sigma) bits per entry)
+    const uint8_t *B[KMAX + 1];    // prefix bytes of depth k (nullptr when k * bps > 16)
     const uint32_t *G;             // gram filter (nullptr when none)
     uint32_t g_len;                // g: symbols per gram
     uint32_t g_bits;               // hb: log2 of the bits of G

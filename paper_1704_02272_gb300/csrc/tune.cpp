@@ -1,8 +1,8 @@
 // Autotuner of the scan configuration (pfac_autotune).  For a built table
 // and a device-resident sample it times the scan kernel for each candidate
 // (prefix depth resolved in shared memory x entries in shared memory or not x
-// child masks on or off x the gram filter or the prefix bitmap as the first
-// stage x copies of that bitmap over the banks), keeps the fastest as the
+// child masks on or off x the first stage (prefix bitmap, gram filter or
+// prefix bytes) x copies of that bitmap over the banks), keeps the fastest as the
 // table's default, and can remember the choice in a small text cache keyed by
 // the table's shape and the GPU.
 #include <cuda_runtime.h>
@@ -37,17 +37,18 @@ std::string cache_key(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments
 }
 
 bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_t *k,
-                  uint32_t *c, uint32_t *mk, uint32_t *gf, float *ms) {
+                  uint32_t *c, uint32_t *mk, uint32_t *gf, uint32_t *pb, float *ms) {
     FILE *f = fopen(path, "r");
     if (!f) return false;
     char line[512];
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char kbuf[300];
-        uint32_t a, b, d, g, h;
+        uint32_t a, b, d, g, h, y;
         float e;
-        if (sscanf(line, "%299s %u %u %u %u %u %f", kbuf, &a, &b, &d, &g, &h, &e) == 7 &&
+        if (sscanf(line, "%299s %u %u %u %u %u %u %f", kbuf, &a, &b, &d, &g, &h, &y, &e) == 8 &&
             key == kbuf) {
+            *pb = y;
             *v = a;
             *k = b;
             *c = d;
@@ -74,10 +75,12 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     memset(&res, 0, sizeof res);
     const std::string key = cache_key(t, n_bytes, n_segments);
     if (cache_path) {
-        uint32_t v, k, c, mk, gf;
+        uint32_t v, k, c, mk, gf, pb;
         float ms;
-        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &ms) && k >= t->kmin &&
-            k <= t->kmax && (gf != 2 || t->dev.g_len)) {
+        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &ms) && k >= t->kmin &&
+            k <= t->kmax && (gf != 2 || t->dev.g_len) && (pb != 2 || t->dev.B[k])) {
+            t->tuned_bytes = pb;
+            res.prefix_bytes = pb;
             t->tuned_variant = v;
             t->tuned_k = k;
             t->tuned_copies = c;
@@ -97,20 +100,23 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // forget an earlier choice so the default is measured as the library's own
     t->tuned_variant = t->tuned_k = t->tuned_copies = t->tuned_masks = t->tuned_gram = 0;
+    t->tuned_bytes = 0;
 
     struct Cand {
-        uint32_t var, k, copies, masks, gram;
+        uint32_t var, k, copies, masks, gram, bytes;
         float ms;
     };
     std::vector<Cand> cands;
-    cands.push_back({0, 0, 0, 0, 0, 0.f});  // library default
+    cands.push_back({0, 0, 0, 0, 0, 0, 0.f});  // library default
     const uint32_t gmax = t->dev.g_len ? 2u : 1u;
     for (uint32_t k = t->kmin; k <= t->kmax; k++)
         for (uint32_t var = 1; var <= 2; var++)
-            for (uint32_t masks = 1; masks <= 2; masks++)
+            for (uint32_t masks = 1; masks <= 2; masks++) {
                 for (uint32_t gram = 1; gram <= gmax; gram++)
                     for (uint32_t copies = 32; copies >= 1; copies >>= 1)
-                        cands.push_back({var, k, copies, masks, gram, 0.f});
+                        cands.push_back({var, k, copies, masks, gram, 1, 0.f});
+                if (t->dev.B[k]) cands.push_back({var, k, 1, masks, 1, 2, 0.f});
+            }
 
     uint64_t ws_max = 0;
     std::vector<Cand> ok;
@@ -122,6 +128,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.bitmap_copies = c.copies;
         o.child_masks = c.masks;
         o.gram_filter = c.gram;
+        o.prefix_bytes = c.bytes;
         uint64_t b = 0;
         if (pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b) != PFAC_OK) continue;
         ws_max = std::max(ws_max, b);
@@ -152,6 +159,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.bitmap_copies = c.copies;
         o.child_masks = c.masks;
         o.gram_filter = c.gram;
+        o.prefix_bytes = c.bytes;
         uint64_t b = 0;
         pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b);
         // warm-up, then the median of three timed scans
@@ -203,18 +211,20 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         t->tuned_copies = best.copies;
         t->tuned_masks = best.masks;
         t->tuned_gram = best.gram;
+        t->tuned_bytes = best.bytes;
     }
     res.variant = best.var;
     res.prefix_depth = best.k;
     res.bitmap_copies = best.copies;
     res.child_masks = best.masks;
     res.gram_filter = best.gram;
+    res.prefix_bytes = best.bytes;
     res.scan_ms = best.ms;
     if (cache_path && best.var) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k, best.copies,
-                    best.masks, best.gram, best.ms);
+            fprintf(f, "%s %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k, best.copies,
+                    best.masks, best.gram, best.bytes, best.ms);
             fclose(f);
         }
     }

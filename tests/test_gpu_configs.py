@@ -117,3 +117,13 @@ def test_gram_filter_full_size(kind, sigma, n):
             torch.cuda.synchronize()
             assert kg.numel() == kd.numel() and torch.equal(kg, kd), f"gram_filter={gram}"
             del kg
+        # prefix bytes at the deepest depth of at most 16 index bits
+        b = 1
+        while (1 << b) < w.sigma:
+            b += 1
+        k = min(t.info()["prefix_depth"], 16 // b)
+        if k >= max(1, t.info()["prefix_depth"] - 2):
+            kb = pfac.match(t, text, seg, prefix_bytes=2, prefix_depth=k)
+            torch.cuda.synchronize()
+            assert kb.numel() == kd.numel() and torch.equal(kb, kd), "prefix_bytes=2"
+            del kb

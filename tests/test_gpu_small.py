@@ -111,6 +111,40 @@ def test_gram_filter_forced(case):
     assert ran >= 2
 
 
+def bits_per_symbol(sigma):
+    b = 1
+    while (1 << b) < sigma:
+        b += 1
+    return b
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"s{c[0]}-sig{c[1]}" for c in CASES])
+def test_prefix_bytes_forced(case):
+    # prefix bytes as the first stage (bucket test second) at every depth of
+    # at most 16 index bits the table holds, child masks on and off
+    seed, sigma, n, lo, hi, N, S, plants, ts = case
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, N, n_segments=S, n_plants=plants,
+                            text_sigma=ts)
+    ref = oracle_keys(w)
+    with pfac.Table(w.patterns, w.sigma, host_only=True) as th:
+        kdef = th.info()["prefix_depth"]
+    b = bits_per_symbol(w.sigma)
+    ran = 0
+    for k in range(max(1, kdef - 2), kdef + 1):
+        if k * b > 16 or k * b < 5:
+            continue
+        for masks in (1, 2):
+            try:
+                got = run(w, prefix_depth=k, prefix_bytes=2, child_masks=masks)
+            except pfac.PfacError as e:  # does not fit, or no masks kept
+                assert e.status == -1, str(e)
+                continue
+            assert_same(got, ref, f"prefix bytes depth {k} masks {masks}")
+            ran += 1
+    if sigma >= 8:
+        assert ran >= 1
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_prefix_heavy(seed):
     w = workloads.prefix_heavy_case(seed, 3 + seed, 200_000, n_segments=1 + 30 * (seed % 2))
