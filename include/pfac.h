@@ -113,7 +113,14 @@ typedef struct {
                               as a cheap second stage.  0 = library choice,
                               1 = off, 2 = required (one copy; excludes the
                               gram filter and bitmap_copies > 1) */
-    uint32_t reserved[1];
+    uint32_t reserved0;
+    uint64_t starts_end;   /* 0 = every input position starts a walk; else
+                              only positions below it do (at most n_bytes;
+                              the bytes after it are still read by walks, as
+                              the halo of a shard or chunk) */
+    uint64_t position_base; /* added to every reported position (a shard's
+                              or chunk's global offset); position_base +
+                              n_bytes must stay below 2^40 */
 } pfac_match_opts;
 
 typedef struct {
@@ -217,6 +224,39 @@ int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
                const uint64_t *d_seg_offsets, uint32_t n_segments, uint64_t *d_out_keys,
                uint64_t out_capacity, uint64_t *n_out, const pfac_match_opts *opts,
                void *cuda_stream);
+
+/*
+ * pfac_match_host - pfac_match for a text and a result in HOST memory
+ * (Section 2.3 semantics; library extension for end-to-end use: the paper
+ * does not say how the text reaches the GPU or how results return).  The
+ * text is cut into chunks of chunk_bytes start positions (0 = 32 MiB;
+ * rounded up to 256) plus a read halo of max_len - 1 bytes; chunk i's copy
+ * to the device, the matching of chunk i - 1 and the copy back of chunk
+ * i - 2's keys overlap on three streams.  Each chunk is matched with
+ * starts_end / position_base (pfac_match_opts), so the keys arrive in
+ * global order without filtering.  Pinned host buffers (cudaHostAlloc /
+ * cudaHostRegister) make the copies asynchronous; pageable ones work but
+ * serialise.
+ *
+ *   h_input          n_bytes symbols (host; the caller keeps ownership)
+ *   h_seg_offsets    n_segments + 1 uint64 offsets (host), same rules as
+ *                    pfac_match (checked on the host: PFAC_EINVAL)
+ *   h_out_keys       room for out_capacity keys (host); the first
+ *                    min(count, out_capacity) sorted keys are written
+ *   n_out            host: the total count; PFAC_ENOSPC when it exceeds
+ *                    out_capacity (two-call convention as pfac_match)
+ *   opts             as pfac_match; starts_end and position_base must be 0
+ *   cuda_stream      the stream the matching runs on (copies use two more
+ *                    streams of the library's own); the call returns after
+ *                    all work completed
+ *
+ * Device memory for two chunks (inputs, workspaces, keys) is taken from the
+ * stream-ordered allocator and released before returning.
+ */
+int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint64_t n_bytes,
+                    const uint64_t *h_seg_offsets, uint32_t n_segments, uint64_t *h_out_keys,
+                    uint64_t out_capacity, uint64_t *n_out, uint64_t chunk_bytes,
+                    const pfac_match_opts *opts, void *cuda_stream);
 
 /*
  * pfac_match_noalloc - pfac_match_async for callers that cannot allocate

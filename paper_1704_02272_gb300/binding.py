@@ -47,7 +47,8 @@ class MatchOpts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("bitmap_copies", ctypes.c_uint32),
                 ("ev_scan_begin", ctypes.c_void_p), ("ev_scan_end", ctypes.c_void_p),
                 ("child_masks", ctypes.c_uint32), ("gram_filter", ctypes.c_uint32),
-                ("prefix_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
+                ("prefix_bytes", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("starts_end", ctypes.c_uint64), ("position_base", ctypes.c_uint64)]
 
 
 class TableInfo(ctypes.Structure):
@@ -106,6 +107,9 @@ def _load():
                                          ctypes.POINTER(u64)]
     lib.pfac_match_plan.restype = ctypes.c_int
     lib.pfac_match_plan.argtypes = [vp, ctypes.POINTER(MatchOpts), ctypes.POINTER(PlanInfo)]
+    lib.pfac_match_host.restype = ctypes.c_int
+    lib.pfac_match_host.argtypes = [vp, vp, u64, vp, u32, vp, u64, ctypes.POINTER(u64), u64,
+                                    ctypes.POINTER(MatchOpts), vp]
     lib.pfac_match_async.restype = ctypes.c_int
     lib.pfac_match_async.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp, vp, u64,
                                      ctypes.POINTER(MatchOpts), vp]
@@ -162,11 +166,11 @@ def _stream(stream) -> int:
 
 
 def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,
-          gram_filter=0, prefix_bytes=0, scan_events=None):
+          gram_filter=0, prefix_bytes=0, starts_end=0, position_base=0, scan_events=None):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
     o.bitmap_copies, o.child_masks, o.gram_filter = bitmap_copies, child_masks, gram_filter
-    o.prefix_bytes = prefix_bytes
+    o.prefix_bytes, o.starts_end, o.position_base = prefix_bytes, starts_end, position_base
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event
@@ -254,6 +258,24 @@ def plan(table: Table, **opt) -> dict:
     r = PlanInfo()
     _check(LIB.pfac_match_plan(table.handle, ctypes.byref(o), ctypes.byref(r)))
     return {f: getattr(r, f) for f, _ in PlanInfo._fields_}
+
+
+def match_host(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,
+               chunk_bytes: int = 0, stream=None, **opt) -> int:
+    """pfac_match_host: text (uint8), segment offsets (int64) and the key
+    buffer (int64) in host memory (pinned for overlapped copies); returns the
+    total count (raises PfacError with status PFAC_ENOSPC when it exceeds
+    out.numel(), as pfac_match)."""
+    for x in (text, seg, out):
+        if x.device.type != "cpu" or not x.is_contiguous():
+            raise ValueError("match_host takes contiguous host tensors")
+    n = ctypes.c_uint64(0)
+    o = _opts(**opt)
+    rc = LIB.pfac_match_host(table.handle, _ptr(text), text.numel(), _ptr(seg),
+                             max(seg.numel() - 1, 0), _ptr(out), out.numel(), ctypes.byref(n),
+                             chunk_bytes, ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    _check(rc)
+    return n.value
 
 
 def match_async(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,

@@ -96,6 +96,8 @@ struct MatchParams {
     uint32_t g_hb;        // log2 of the shared gram filter's bits per copy
     uint32_t kf;          // symbols the first stage tests: k, or g with the gram filter
     const uint8_t *Bt;    // prefix bytes of depth k
+    uint64_t starts_end;  // positions at or past it start no walk (<= n)
+    uint64_t pos_base;    // added to every reported position
     uint32_t tbl_b_words; // prefix bytes in shared memory as the first stage (0 = not used)
     uint32_t dense_rows;  // dense layout: states whose rows live in shared memory
 };
@@ -305,7 +307,7 @@ __device__ __forceinline__ void thread_positions_dense(const MatchParams &P, con
     if (p0 >= valid) return;
     const uint32_t lim = seg_limit(segs, p0, rem, P.seg, P.n_seg, tile_start);
     const uint32_t span = p0 + BPT;
-    if (span <= lim && span <= staged) {
+    if (span <= lim && span <= staged && span <= valid) {
         const uint4 a = *reinterpret_cast<const uint4 *>(sin + p0);
         const uint32_t x[4] = {a.x, a.y, a.z, a.w};
         uint32_t s1[BPT];
@@ -457,7 +459,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_scan_dense(const MatchParams P,
         const uint64_t tile_start = (uint64_t)t * TILE;
         const uint64_t remain = P.n - tile_start;
         const uint32_t rem = remain < 0xFFFFFFF0ull ? (uint32_t)remain : 0xFFFFFFF0u;
-        const uint32_t valid = rem < (uint32_t)TILE ? rem : (uint32_t)TILE;
+        uint32_t valid = rem < (uint32_t)TILE ? rem : (uint32_t)TILE;
+        {
+            const uint64_t sl = P.starts_end > tile_start ? P.starts_end - tile_start : 0;
+            if (sl < valid) valid = (uint32_t)sl;
+        }
         const uint32_t staged = (rem < (uint32_t)(TILE + HALO) ? rem : (uint32_t)(TILE + HALO)) & ~15u;
         const uint8_t *sin = st_in + s * STAGE_IN;
         const uint32_t *segs = st_seg + s * SEGW;
@@ -503,7 +509,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_scan_dense(const MatchParams P,
                 if (!f) continue;
                 const uint32_t L = fin_len(P.T.pool, f);
                 const uint32_t *ids = fin_ids(P.T.pool, f);
-                const uint64_t pk = (tile_start + p0 + j) << PFAC_ID_BITS;
+                const uint64_t pk = (P.pos_base + tile_start + p0 + j) << PFAC_ID_BITS;
                 for (uint32_t e = 0; e < L; e++, o++)
                     if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
             }

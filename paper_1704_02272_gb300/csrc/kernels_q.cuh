@@ -383,7 +383,7 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
     }
     // every position's window is available (the window limits are exact
     // only when the slice's segment ends fit the lane's window)
-    if (!general_lims && p0 + QBPT - 1 + k <= lim0 && badb == 0) return;
+    if (!general_lims && p0 + QBPT - 1 + k <= lim0 && p0 + QBPT <= valid && badb == 0) return;
     // fv: positions whose whole window lies in their segment and the stage;
     // ex: positions inside their segment (the others start no walk)
     uint32_t fv = 0, ex = 0;
@@ -804,7 +804,7 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
             const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
             if (emit && L) {
                 const uint32_t *ids = fin_ids(P.T.pool, fin[u]);
-                const uint64_t pk = (ustart + (pos[u] & 0x3FFu)) << PFAC_ID_BITS;
+                const uint64_t pk = (P.pos_base + ustart + (pos[u] & 0x3FFu)) << PFAC_ID_BITS;
                 uint64_t o = obase + keys + inc - L;
                 for (uint32_t e = 0; e < L; e++, o++)
                     if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
@@ -905,7 +905,11 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
         const uint64_t ustart = (uint64_t)u << SLICE_SHIFT;
         const uint64_t remain = P.n - ustart;
         const uint32_t rem = remain < LIM_MAX ? (uint32_t)remain : LIM_MAX;
-        const uint32_t valid = rem < (uint32_t)SLICE ? rem : (uint32_t)SLICE;
+        uint32_t valid = rem < (uint32_t)SLICE ? rem : (uint32_t)SLICE;
+        {
+            const uint64_t sl = P.starts_end > ustart ? P.starts_end - ustart : 0;
+            if (sl < valid) valid = (uint32_t)sl;
+        }
         const uint32_t staged = (rem < (uint32_t)QSTAGE ? rem : (uint32_t)QSTAGE) & ~15u;
 
         // segment ends of this slice: a window of 32 offsets after its start

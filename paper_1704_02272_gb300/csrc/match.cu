@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
             const uint64_t r = rr[i];
             const uint32_t L = fin_len(pool, (uint32_t)r);
             const uint32_t *ids = fin_ids(pool, (uint32_t)r);
-            const uint64_t pk = (tile_start + (r >> 32)) << PFAC_ID_BITS;
+            const uint64_t pk = (P.pos_base + tile_start + (r >> 32)) << PFAC_ID_BITS;
             for (uint32_t e = 0; e < L; e++, o++)
                 if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
         }
@@ -612,6 +612,14 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     if (n_bytes && n_segments == 0)
         return set_error(PFAC_EINVAL, "pfac_match: a non-empty input needs a segment");
     if (out_capacity && !d_out_keys) return set_error(PFAC_EINVAL, "pfac_match: NULL output");
+    const uint64_t starts_end = opts && opts->starts_end ? opts->starts_end : n_bytes;
+    const uint64_t pos_base = opts ? opts->position_base : 0;
+    if (starts_end > n_bytes)
+        return set_error(PFAC_EINVAL, "pfac_match: starts_end %llu beyond the input",
+                         (unsigned long long)starts_end);
+    if ((pos_base + n_bytes) >> (64 - PFAC_ID_BITS) || pos_base + n_bytes < pos_base)
+        return set_error(PFAC_EINVAL, "pfac_match: position_base + n_bytes reaches 2^%d",
+                         64 - PFAC_ID_BITS);
     Plan pl;
     int rc = make_plan(t, opts, &pl);
     if (rc) return rc;
@@ -632,7 +640,11 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.n = n_bytes;
     P.seg = d_seg_offsets;
     P.n_seg = n_segments;
-    P.n_tiles = L.n_tiles;
+    // units holding a start position (the rest of the input is halo)
+    const uint64_t ub = 1ull << pl.unit_shift;
+    P.n_tiles = (uint32_t)((starts_end + ub - 1) >> pl.unit_shift);
+    P.starts_end = starts_end;
+    P.pos_base = pos_base;
     P.out = d_out_keys;
     P.cap = out_capacity;
     P.d_count = d_count;
@@ -642,7 +654,7 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.tile_k = (uint64_t *)(W + L.tile_k);
     P.key_off = (uint64_t *)(W + L.key_off);
     P.chunk = (uint64_t *)(W + L.chunk);
-    P.n_chunks = L.n_chunks;
+    P.n_chunks = (uint32_t)((P.n_tiles + CHUNK - 1) / CHUNK);
     P.ovf_list = (uint32_t *)(W + L.ovf);
     P.recs = (uint64_t *)(W + L.recs);
     P.tile_bounds = (uint32_t *)(W + L.bounds);
@@ -676,17 +688,17 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     cudaError_t e = cudaMemsetAsync(P.hdr, 0, pl.queued ? L.key_off : sizeof(WsHeader), st);
     const int nsm = sm_count();
     const uint32_t cps = opts && opts->ctas_per_sm ? opts->ctas_per_sm : 1;
-    if (e == cudaSuccess && n_segments > 1 && L.n_tiles) {
+    if (e == cudaSuccess && n_segments > 1 && P.n_tiles) {
         if (pl.queued) k_unitseg<<<nsm * 4, 256, 0, st>>>(P);
         else k_bounds<<<nsm * 2, 256, 0, st>>>(P);
         e = cudaGetLastError();
     }
     // persistent grid: one CTA per SM (fewer when there are few units)
-    const uint64_t want = ((uint64_t)L.n_tiles + units_per_cta - 1) / units_per_cta;
+    const uint64_t want = ((uint64_t)P.n_tiles + units_per_cta - 1) / units_per_cta;
     const uint32_t grid = (uint64_t)nsm * cps < want ? (uint32_t)nsm * cps : (uint32_t)want;
     if (e == cudaSuccess && opts && opts->ev_scan_begin)
         e = cudaEventRecord((cudaEvent_t)opts->ev_scan_begin, st);
-    if (e == cudaSuccess && L.n_tiles) {
+    if (e == cudaSuccess && P.n_tiles) {
         int emit = 0;
         void *args[] = {&P, &emit};
         e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(nthreads), args, pl.smem, st);
@@ -694,20 +706,20 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     if (e == cudaSuccess && opts && opts->ev_scan_end)
         e = cudaEventRecord((cudaEvent_t)opts->ev_scan_end, st);
     if (e == cudaSuccess) {
-        k_reduce<<<L.n_chunks ? L.n_chunks : 1, RT, 0, st>>>(P);
+        k_reduce<<<P.n_chunks ? P.n_chunks : 1, RT, 0, st>>>(P);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && L.n_tiles) {
-        k_offsets<<<L.n_chunks, RT, 0, st>>>(P);
+    if (e == cudaSuccess && P.n_tiles) {
+        k_offsets<<<P.n_chunks, RT, 0, st>>>(P);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && L.n_tiles) {
+    if (e == cudaSuccess && P.n_tiles) {
         int emit = 1;
         void *args[] = {&P, &emit};
         e = cudaLaunchKernel(pl.kernel_emit, dim3(grid), dim3(nthreads), args, pl.smem, st);
     }
     if (e == cudaSuccess) {
-        const uint64_t units = L.n_tiles ? L.n_tiles : 1;
+        const uint64_t units = P.n_tiles ? P.n_tiles : 1;
         uint64_t blocks = (units + 255) / 256;
         const uint64_t maxb = (uint64_t)nsm * 8;
         if (blocks > maxb) blocks = maxb;

@@ -60,13 +60,15 @@ def own(keys, shard: Shard, id_bits: int = 24):
 
 
 def match_shard_gpu(table, text_dev, shard: Shard, **opt):
-    """This rank's share of the matches, with global positions (device)."""
+    """This rank's share of the matches, with global positions (device): the
+    library starts walks only below the shard's stop and adds its start to
+    every reported position, so the keys need no filtering."""
     import torch
 
     from . import binding
     seg = torch.from_numpy(shard.seg.astype(np.int64)).to(text_dev.device)
-    keys = binding.match(table, text_dev[shard.start:shard.read_end], seg, **opt)
-    return own(keys, shard)
+    return binding.match(table, text_dev[shard.start:shard.read_end], seg,
+                         starts_end=shard.stop - shard.start, position_base=shard.start, **opt)
 
 
 def gather(keys, group=None):

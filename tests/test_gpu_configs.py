@@ -73,6 +73,15 @@ def test_ids_packets_config():
     assert plants_present(w, ref) > 6000
 
 
+@pytest.mark.parametrize("n", [1, 10, 100, 1000])
+def test_letters_shape(n):
+    # the paper's throughput-experiment shape (52 letters, 20-symbol
+    # patterns), at 8 MiB: the whole list against the oracle
+    w = workloads.letters(n, n_bytes=8 << 20, n_plants=200)
+    ref = full_check(w)
+    assert plants_present(w, ref) >= 150
+
+
 SWEEP = [(s, n) for s in workloads.CONFIG4_SIGMAS for n in workloads.CONFIG4_COUNTS]
 
 

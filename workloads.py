@@ -232,6 +232,18 @@ def config4(sigma, n_patterns, seed=None, n_bytes=512 << 20) -> Workload:
                     single_segment(n_bytes))
 
 
+def letters(n_patterns, seed=None, n_bytes=100 << 20, n_plants=1000) -> Workload:
+    """The throughput experiments' shape (Section 4, Fig. 7-9): an alphabet of
+    52 letters (codes 0..51), patterns of 20 symbols, uniform random 100 MiB
+    text as one segment; a few plants so matches exist."""
+    rs = np.random.RandomState(seed_for(6, 52, n_patterns) if seed is None else seed)
+    pats = uniform_patterns(rs, n_patterns, 52, 20, 20)
+    text = uniform_symbols(rs, n_bytes, 52)
+    off = single_segment(n_bytes)
+    plants = plant_into(rs, text, pats, off, np.zeros(n_plants, np.int64)) if pats else None
+    return Workload(f"letters-52x{n_patterns}-{n_bytes >> 20}MiB", 52, pats, text, off, plants)
+
+
 def config5_patterns(seed=None, n_patterns=50000) -> list:
     rs = np.random.RandomState(seed_for(5) if seed is None else seed)
     return ids_patterns(rs, n_patterns)
