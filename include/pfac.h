@@ -250,13 +250,19 @@ int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
  *                    streams of the library's own); the call returns after
  *                    all work completed
  *
- * Device memory for two chunks (inputs, workspaces, keys) is taken from the
- * stream-ordered allocator and released before returning.
+ * Device memory for two chunks (inputs, workspaces, keys), the two copy
+ * streams and pinned staging are kept per device between calls and grown on
+ * demand; pfac_match_host_release frees them.  Calls from several host
+ * threads are serialised.  chunk_bytes = 0 uses 32 MiB.
  */
 int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint64_t n_bytes,
                     const uint64_t *h_seg_offsets, uint32_t n_segments, uint64_t *h_out_keys,
                     uint64_t out_capacity, uint64_t *n_out, uint64_t chunk_bytes,
                     const pfac_match_opts *opts, void *cuda_stream);
+
+/* pfac_match_host_release - free the buffers pfac_match_host keeps for the
+ * current device (waits for the device first).  Library extension. */
+void pfac_match_host_release(void);
 
 /*
  * pfac_match_noalloc - pfac_match_async for callers that cannot allocate

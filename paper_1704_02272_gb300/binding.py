@@ -110,6 +110,8 @@ def _load():
     lib.pfac_match_host.restype = ctypes.c_int
     lib.pfac_match_host.argtypes = [vp, vp, u64, vp, u32, vp, u64, ctypes.POINTER(u64), u64,
                                     ctypes.POINTER(MatchOpts), vp]
+    lib.pfac_match_host_release.restype = None
+    lib.pfac_match_host_release.argtypes = []
     lib.pfac_match_async.restype = ctypes.c_int
     lib.pfac_match_async.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp, vp, u64,
                                      ctypes.POINTER(MatchOpts), vp]

@@ -47,7 +47,87 @@ struct Slot {
     cudaEvent_t h2d = nullptr, done = nullptr, d2h = nullptr;
 };
 
+// Streams, events and device buffers of one device, kept between calls and
+// grown on demand (mapping fresh device memory per call costs milliseconds).
+struct HostCtx {
+    bool init = false;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    Slot sl[2];
+    uint64_t in_cap = 0, seg_cap = 0, ws_cap = 0, keys_cap = 0;
+    uint64_t keys_hint = 0;  // largest chunk key count seen (keys)
+};
+constexpr int MAX_DEV = 64;
+HostCtx g_ctx[MAX_DEV];
+
+cudaError_t grow(void **p, uint64_t &cap, uint64_t want) {
+    if (cap >= want && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(p, want);
+    if (e == cudaSuccess) cap = want;
+    return e;
+}
+
+cudaError_t ctx_prepare(HostCtx &c, uint64_t in_b, uint64_t seg_b, uint64_t ws_b,
+                        uint64_t keys_b) {
+    cudaError_t e = cudaSuccess;
+    if (!c.init) {
+        e = cudaStreamCreateWithFlags(&c.h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.d2h, cudaStreamNonBlocking);
+        for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+            e = cudaEventCreateWithFlags(&c.sl[s].h2d, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.sl[s].done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.sl[s].d2h, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&c.sl[s].small, 16);
+        }
+        if (e != cudaSuccess) return e;
+        c.init = true;
+    }
+    // every slot is sized alike, so one capacity per buffer kind
+    uint64_t cap[4];
+    const uint64_t want[4] = {in_b, seg_b, ws_b, keys_b};
+    const uint64_t have[4] = {c.in_cap, c.seg_cap, c.ws_cap, c.keys_cap};
+    for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+        void **bufs[4] = {(void **)&c.sl[s].in, (void **)&c.sl[s].seg, &c.sl[s].ws,
+                          (void **)&c.sl[s].keys};
+        for (int b = 0; b < 4 && e == cudaSuccess; b++) {
+            cap[b] = have[b];
+            e = grow(bufs[b], cap[b], std::max(want[b], have[b]));
+        }
+    }
+    if (e == cudaSuccess) {
+        c.in_cap = cap[0];
+        c.seg_cap = cap[1];
+        c.ws_cap = cap[2];
+        c.keys_cap = cap[3];
+    }
+    return e;
+}
+
 }  // namespace
+
+extern "C" void pfac_match_host_release(void) {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return;
+    HostCtx &c = g_ctx[dev];
+    if (!c.init) return;
+    cudaDeviceSynchronize();
+    for (int s = 0; s < 2; s++) {
+        cudaFree(c.sl[s].in);
+        cudaFree(c.sl[s].seg);
+        cudaFree(c.sl[s].ws);
+        cudaFree(c.sl[s].keys);
+        cudaFree(c.sl[s].small);
+        cudaEventDestroy(c.sl[s].h2d);
+        cudaEventDestroy(c.sl[s].done);
+        cudaEventDestroy(c.sl[s].d2h);
+    }
+    cudaStreamDestroy(c.h2d);
+    cudaStreamDestroy(c.d2h);
+    c = HostCtx();
+}
 
 extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint64_t n_bytes,
                                const uint64_t *h_seg, uint32_t n_segments, uint64_t *h_out_keys,
@@ -102,9 +182,6 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
     uint64_t ws_bytes = 0;
     int rc = pfac_workspace_bytes(t, C + H, (uint32_t)(max_local - 1), &o, &ws_bytes);
     if (rc) return rc;
-    // keys per chunk held on the device; a chunk with more is matched again
-    // on its own afterwards
-    const uint64_t K = std::max<uint64_t>(1ull << 20, C / 4);
 
     std::lock_guard<std::mutex> lk(g_host_mu);
     if (!g_pin_small && cudaHostAlloc((void **)&g_pin_small, 64, cudaHostAllocDefault) != cudaSuccess) {
@@ -114,24 +191,26 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
     if (!g_pin_small || !pin_reserve(0, max_local) || !pin_reserve(1, max_local))
         return set_error(PFAC_ENOMEM, "pfac_match_host: pinned staging of %zu offsets", max_local);
 
-    cudaStream_t comp = (cudaStream_t)cuda_stream, h2d = nullptr, d2h = nullptr;
-    Slot sl[2];
-    cudaError_t ce = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking);
-    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking);
-    for (int s = 0; s < 2 && ce == cudaSuccess; s++) {
-        ce = cudaMallocAsync((void **)&sl[s].in, C + H + 16, comp);
-        if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&sl[s].seg, max_local * 8, comp);
-        if (ce == cudaSuccess) ce = cudaMallocAsync(&sl[s].ws, ws_bytes, comp);
-        if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&sl[s].keys, K * 8, comp);
-        if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&sl[s].small, 16, comp);
-        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&sl[s].h2d, cudaEventDisableTiming);
-        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&sl[s].done, cudaEventDisableTiming);
-        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&sl[s].d2h, cudaEventDisableTiming);
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess || dev < 0 || dev >= MAX_DEV)
+        return set_error(PFAC_ECUDA, "pfac_match_host: no usable device");
+    HostCtx &cx = g_ctx[dev];
+    // keys per chunk held on the device (at least the most an earlier call
+    // met, up to 2^28); a chunk with more is matched again alone afterwards
+    const uint64_t hint = std::min<uint64_t>(cx.keys_hint, 1ull << 28);
+    const uint64_t K = std::max<uint64_t>(std::max<uint64_t>(1ull << 20, C / 4), hint);
+    ce = ctx_prepare(cx, C + H + 16, max_local * 8, ws_bytes, K * 8);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ce == cudaErrorMemoryAllocation ? PFAC_ENOMEM : PFAC_ECUDA,
+                         "pfac_match_host: device buffers: %s", cudaGetErrorString(ce));
     }
-    // the buffers exist on comp; the copy streams wait for that
-    cudaEvent_t ready = nullptr;
-    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    if (ce == cudaSuccess) ce = cudaEventRecord(ready, comp);
+    cudaStream_t comp = (cudaStream_t)cuda_stream, h2d = cx.h2d, d2h = cx.d2h;
+    Slot *sl = cx.sl;
+    // the caller's stream may have work the chunks depend on (the table)
+    cudaEvent_t ready = sl[0].h2d;
+    ce = cudaEventRecord(ready, comp);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(h2d, ready, 0);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(d2h, ready, 0);
 
@@ -152,6 +231,7 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
         if (st != PFAC_OK && status == PFAC_OK) status = st;
         if (c > K) {
             redo.push_back({j, total, c});
+            cx.keys_hint = std::max(cx.keys_hint, c + c / 8);
         } else if (total < out_capacity && c) {
             const uint64_t m = std::min(c, out_capacity - total);
             if (cudaMemcpyAsync(h_out_keys + total, sl[s].keys, m * 8, cudaMemcpyDeviceToHost,
@@ -232,22 +312,10 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(comp);
     }
 
-    // release (after the streams drained)
-    cudaStreamSynchronize(comp);
-    for (int s = 0; s < 2; s++) {
-        if (sl[s].in) cudaFreeAsync(sl[s].in, comp);
-        if (sl[s].seg) cudaFreeAsync(sl[s].seg, comp);
-        if (sl[s].ws) cudaFreeAsync(sl[s].ws, comp);
-        if (sl[s].keys) cudaFreeAsync(sl[s].keys, comp);
-        if (sl[s].small) cudaFreeAsync(sl[s].small, comp);
-        if (sl[s].h2d) cudaEventDestroy(sl[s].h2d);
-        if (sl[s].done) cudaEventDestroy(sl[s].done);
-        if (sl[s].d2h) cudaEventDestroy(sl[s].d2h);
-    }
-    if (ready) cudaEventDestroy(ready);
+    // the buffers stay for the next call; wait until every stream drained
     cudaError_t ce2 = cudaStreamSynchronize(comp);
-    if (h2d) cudaStreamDestroy(h2d);
-    if (d2h) cudaStreamDestroy(d2h);
+    if (ce2 == cudaSuccess) ce2 = cudaStreamSynchronize(h2d);
+    if (ce2 == cudaSuccess) ce2 = cudaStreamSynchronize(d2h);
     if (rc != PFAC_OK) return rc;
     if (ce == cudaSuccess) ce = ce2;
     if (ce != cudaSuccess) {
