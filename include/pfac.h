@@ -75,7 +75,13 @@ typedef struct {
                               else at most 20 / b and at least 5 / b rounded
                               up, b = bits per symbol (PFAC_EINVAL otherwise) */
     uint32_t flags;        /* PFAC_BUILD_* bits */
-    uint32_t reserved[5];
+    uint32_t truncate_depth; /* prefix matching (Section 2.4): 0 = exact
+                              table; d > 0 = the trie holds every pattern's
+                              first d symbols, so pfac_match reports the
+                              candidates (p, j) whose first min(|P_j|, d)
+                              symbols occur at p; pfac_verify keeps the exact
+                              ones (the table then also keeps the patterns) */
+    uint32_t reserved[4];
 } pfac_build_opts;
 
 /* Build flag: build the table on the host only (no device memory, no CUDA
@@ -259,6 +265,26 @@ int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint64_t n_byte
                     const uint64_t *h_seg_offsets, uint32_t n_segments, uint64_t *h_out_keys,
                     uint64_t out_capacity, uint64_t *n_out, uint64_t chunk_bytes,
                     const pfac_match_opts *opts, void *cuda_stream);
+
+/*
+ * pfac_verify - the secondary process of prefix matching (Section 2.4): for a
+ * table built with truncate_depth d, keeps the candidate keys (p, j) whose
+ * whole pattern P_j occurs at p inside p's segment (patterns of at most d
+ * symbols are exact already), in the candidates' order.  The paper leaves
+ * that process unspecified; this is the library's.
+ *
+ *   d_input, n_bytes, d_seg_offsets, n_segments   the text the candidates
+ *                    came from (device; positions relative to d_input)
+ *   d_keys, n_keys   candidate keys (device), as pfac_match wrote them
+ *   d_out            room for n_keys keys (device); must not alias d_keys
+ *   d_count          device uint64: the number of exact matches
+ *
+ * Stream-ordered; its scratch (about 1 byte per candidate) comes from the
+ * stream-ordered allocator.  PFAC_EINVAL for a table without truncation.
+ */
+int pfac_verify(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
+                const uint64_t *d_seg_offsets, uint32_t n_segments, const uint64_t *d_keys,
+                uint64_t n_keys, uint64_t *d_out, uint64_t *d_count, void *cuda_stream);
 
 /* pfac_match_host_release - free the buffers pfac_match_host keeps for the
  * current device (waits for the device first).  Library extension. */

@@ -7,6 +7,7 @@ its thin Python binding; importing it fails when the library is not built.
 """
 from .binding import (ID_BITS, LAYOUT_COMPRESSED, LAYOUT_DENSE, VARIANT_DEFAULT,  # noqa: F401
                       VARIANT_DSMEM, VARIANT_FILTER, PfacError, Server, Table, autotune,
-                      match, match_async, match_host, match_into, match_noalloc, plan, single_segment, unpack,
+                      match, match_async, match_host, match_into, match_noalloc, plan, single_segment, unpack, verify,
+                      verify_into,
                       version,
                       workspace_bytes)

@@ -36,7 +36,8 @@ class PfacError(RuntimeError):
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("flags", ctypes.c_uint32), ("truncate_depth", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 BUILD_HOST_ONLY = 1
@@ -110,6 +111,8 @@ def _load():
     lib.pfac_match_host.restype = ctypes.c_int
     lib.pfac_match_host.argtypes = [vp, vp, u64, vp, u32, vp, u64, ctypes.POINTER(u64), u64,
                                     ctypes.POINTER(MatchOpts), vp]
+    lib.pfac_verify.restype = ctypes.c_int
+    lib.pfac_verify.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp, vp]
     lib.pfac_match_host_release.restype = None
     lib.pfac_match_host_release.argtypes = []
     lib.pfac_match_async.restype = ctypes.c_int
@@ -187,7 +190,8 @@ class Table:
     """A built matching table (pfac_build); device memory owned by libpfac."""
 
     def __init__(self, patterns, alphabet_size: int, layout: int = LAYOUT_COMPRESSED,
-                 prefix_depth: int = 0, stream=None, host_only: bool = False):
+                 prefix_depth: int = 0, stream=None, host_only: bool = False,
+                 truncate_depth: int = 0):
         n = len(patterns)
         bufs = [ctypes.create_string_buffer(bytes(p), len(p)) for p in patterns]
         arr = (ctypes.POINTER(ctypes.c_uint8) * max(n, 1))()
@@ -198,6 +202,7 @@ class Table:
         o = BuildOpts()
         o.layout, o.prefix_depth = layout, prefix_depth
         o.flags = BUILD_HOST_ONLY if host_only else 0
+        o.truncate_depth = truncate_depth
         h = ctypes.c_void_p()
         st = 0 if host_only else _stream(stream)
         _check(LIB.pfac_build(arr, lens, n, alphabet_size, ctypes.byref(o),
@@ -278,6 +283,29 @@ def match_host(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.T
                              chunk_bytes, ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     _check(rc)
     return n.value
+
+
+def verify_into(table: Table, text: torch.Tensor, seg: torch.Tensor, cand: torch.Tensor,
+                out: torch.Tensor, cnt: torch.Tensor, stream=None) -> None:
+    """pfac_verify, stream-ordered: the exact matches among the candidates go
+    to out (room for cand.numel() keys), their number to cnt (device int64)."""
+    _check(LIB.pfac_verify(table.handle, _ptr(text), text.numel(), _ptr(seg),
+                           max(seg.numel() - 1, 0), _ptr(cand), cand.numel(), _ptr(out), _ptr(cnt),
+                           ctypes.c_void_p(_stream(stream))))
+
+
+def verify(table: Table, text: torch.Tensor, seg: torch.Tensor, cand: torch.Tensor,
+           stream=None) -> torch.Tensor:
+    """pfac_verify: the exact matches among prefix-matching candidates of a
+    table built with truncate_depth (all on the device)."""
+    out = torch.empty(max(cand.numel(), 1), dtype=torch.int64, device=cand.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=cand.device)
+    verify_into(table, text, seg, cand, out, cnt, stream=stream)
+    if stream is not None:
+        stream.synchronize()
+    else:
+        torch.cuda.synchronize(cand.device)
+    return out[:int(cnt.item())]
 
 
 def match_async(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,

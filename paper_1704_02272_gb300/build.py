@@ -31,7 +31,7 @@ def nvcc() -> str:
 
 def sources():
     srcs = ["builder.cpp", "tune.cpp", "serve.cpp", "host.cpp", "match.cu", "noalloc.cu",
-            "scan_dense.cu"] + [f"scan_bps{i}.cu" for i in range(1, 9)]
+            "verify.cu", "scan_dense.cu"] + [f"scan_bps{i}.cu" for i in range(1, 9)]
     return [os.path.join(CSRC, s) for s in srcs]
 
 

@@ -43,7 +43,7 @@ struct BNode {
     uint32_t parent;
     uint32_t first_child;  // node index of the first child (valid if n_child)
     uint32_t n_child;
-    int32_t final_id;      // pattern ending here, or -1
+    uint32_t fin_lo, fin_hi;  // sorted-order range of the patterns ending here
 };
 
 struct Pat {
@@ -153,23 +153,30 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 return set_error(PFAC_EDUP, "pfac_build: patterns %u and %u are equal",
                                  std::min(order[i - 1], order[i]), std::max(order[i - 1], order[i]));
         }
+        // with truncation (prefix matching, Section 2.4) the trie holds every
+        // pattern's first `trunc` symbols; patterns sharing them end at one node
+        const uint32_t trunc = o.truncate_depth;
         auto sym_at = [&](uint32_t sorted_i, uint32_t d) { return pats[order[sorted_i]].p[d]; };
-        auto len_at = [&](uint32_t sorted_i) { return pats[order[sorted_i]].len; };
+        auto len_at = [&](uint32_t sorted_i) {
+            const uint32_t L = pats[order[sorted_i]].len;
+            return trunc && L > trunc ? trunc : L;
+        };
 
         // ---- breadth-first trie -----------------------------------------
         const uint32_t W = sigma <= 32 ? 1 : (sigma <= 64 ? 2 : 8);
         std::vector<BNode> nodes;
         std::vector<uint32_t> bm;  // W words per node
         nodes.reserve(total + 1);
-        nodes.push_back(BNode{0, n_patterns, 0, 0, 0, 0, -1});
+        nodes.push_back(BNode{0, n_patterns, 0, 0, 0, 0, 0, 0});
         bm.assign(W, 0);
         for (size_t v = 0; v < nodes.size(); v++) {
             uint32_t lo = nodes[v].lo, hi = nodes[v].hi, d = nodes[v].depth;
             uint32_t i = lo;
-            if (i < hi && len_at(i) == d) {  // the pattern equal to the prefix sorts first
-                nodes[v].final_id = (int32_t)order[i];
-                i++;
-            }
+            // the patterns equal to the prefix sort first (several only when
+            // truncated)
+            nodes[v].fin_lo = i;
+            while (i < hi && len_at(i) == d) i++;
+            nodes[v].fin_hi = i;
             while (i < hi) {
                 uint8_t c = sym_at(i, d);
                 uint32_t k = i;
@@ -178,7 +185,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 if (nodes[v].n_child == 0) nodes[v].first_child = idx;
                 nodes[v].n_child++;
                 bm[v * W + (c >> 5)] |= 1u << (c & 31);
-                nodes.push_back(BNode{i, k, d + 1, (uint32_t)v, 0, 0, -1});
+                nodes.push_back(BNode{i, k, d + 1, (uint32_t)v, 0, 0, 0, 0});
                 bm.resize(bm.size() + W, 0);
                 i = k;
             }
@@ -192,13 +199,13 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         uint64_t n_lists = 0;
         for (uint64_t v = 1; v < Q; v++) {
             uint32_t pc = fin_code[nodes[v].parent];
-            if (nodes[v].final_id < 0) {
+            if (nodes[v].fin_lo == nodes[v].fin_hi) {
                 fin_code[v] = pc;
                 continue;
             }
             get_list(pool, pc, ids);
-            ids.insert(std::upper_bound(ids.begin(), ids.end(), (uint32_t)nodes[v].final_id),
-                       (uint32_t)nodes[v].final_id);
+            for (uint32_t f = nodes[v].fin_lo; f < nodes[v].fin_hi; f++)
+                ids.insert(std::upper_bound(ids.begin(), ids.end(), order[f]), order[f]);
             if (put_list(pool, ids, &fin_code[v]))
                 return set_error(PFAC_ENOMEM, "pfac_build: output lists exceed %u words",
                                  FIN_MAX_OFF);
@@ -439,6 +446,17 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
             }
         }
         const uint64_t sz_G = Gv.size() * 4;
+        // truncated tables keep the patterns for verification
+        std::vector<uint32_t> pat_off;
+        std::vector<uint8_t> pat_bytes;
+        if (o.truncate_depth) {
+            pat_off.resize((size_t)n_patterns + 1, 0);
+            for (uint32_t i = 0; i < n_patterns; i++) pat_off[i + 1] = pat_off[i] + pats[i].len;
+            pat_bytes.resize(std::max<uint64_t>(pat_off[n_patterns], 4));
+            for (uint32_t i = 0; i < n_patterns; i++)
+                memcpy(pat_bytes.data() + pat_off[i], pats[i].p, pats[i].len);
+        }
+        const uint64_t sz_po = pat_off.size() * 4, sz_pb = pat_bytes.size();
 
         uint64_t sz_stt = dense ? Q * sigma * 4 : 0;
         uint64_t sz_dfin = dense ? Q * 4 : 0;
@@ -509,6 +527,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 o_B[k] = place(sz_B[k]);
             }
         const uint64_t o_G = place(sz_G);
+        const uint64_t o_po = place(sz_po), o_pb = place(sz_pb);
         uint64_t o_stt = place(sz_stt), o_dfin = place(sz_dfin);
         const uint64_t blob = std::max<uint64_t>(off, 256);
 
@@ -530,6 +549,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 put(o_B[k], Bv[k].data(), sz_B[k]);
             }
         put(o_G, Gv.data(), sz_G);
+        put(o_po, pat_off.data(), sz_po);
+        put(o_pb, pat_bytes.data(), sz_pb);
         if (dense) {
             uint32_t *S = (uint32_t *)(host.data() + o_stt);
             uint32_t *DF = (uint32_t *)(host.data() + o_dfin);
@@ -595,6 +616,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 dv.B[k] = sz_B[k] ? (const uint8_t *)(B + o_B[k]) : nullptr;
             }
         dv.G = g_len ? (const uint32_t *)(B + o_G) : nullptr;
+        dv.trunc = o.truncate_depth;
+        dv.n_pat = n_patterns;
+        dv.pat_off = sz_po ? (const uint32_t *)(B + o_po) : nullptr;
+        dv.pat = sz_pb ? (const uint8_t *)(B + o_pb) : nullptr;
         dv.g_len = g_len;
         dv.g_bits = g_bits;
         dv.g_set = g_set;

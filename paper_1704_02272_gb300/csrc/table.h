@@ -118,6 +118,10 @@ struct DevTable {
     uint32_t g_len;                // g: symbols per gram
     uint32_t g_bits;               // hb: log2 of the bits of G
     uint64_t g_set;                // strings whose bit is set
+    uint32_t trunc;           // truncation depth (0: exact table)
+    const uint8_t *pat;       // truncated tables: the patterns' bytes,
+    const uint32_t *pat_off;  //   pattern j at pat[pat_off[j] .. pat_off[j + 1])
+    uint32_t n_pat;
     const uint32_t *stt;      // dense layout
     const uint32_t *dfin;
 };

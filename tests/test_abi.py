@@ -158,3 +158,17 @@ def test_prefix_depth_too_small_rejected():
     with pytest.raises(pfac.PfacError) as ei:
         host_table([b"\x01\x02"], 4, prefix_depth=2)
     assert ei.value.status == -1
+
+
+@pytest.mark.parametrize("seed,sigma,n,lo,hi,d", [(21, 52, 300, 20, 20, 5), (22, 4, 500, 3, 16, 6),
+                                                  (23, 256, 800, 1, 12, 2)])
+def test_truncated_trie_counts(seed, sigma, n, lo, hi, d):
+    # prefix matching (Section 2.4): the truncated trie is the trie of the
+    # patterns cut to d symbols; its lists hold each distinct cut string
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, 0)
+    cut = [bytes(p[:d]) for p in w.patterns]
+    with host_table(w.patterns, sigma, truncate_depth=d) as t:
+        info = t.info()
+    assert info["trie_nodes"] == trie.prefix_set_count(cut)
+    assert info["output_lists"] == len(set(cut))
+    assert info["n_patterns"] == len(w.patterns)
