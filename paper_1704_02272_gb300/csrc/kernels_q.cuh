@@ -767,7 +767,7 @@ __device__ __forceinline__ int append_slice(const MatchParams &P, QEntry *q, uin
 // candidates each).  emit == 0: returns the slice's key count.  emit == 1:
 // writes the slice's keys at key_off[unit] and returns the count.
 template <int W, int BPS, int VAR>
-__device__ __noinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *q, uint32_t cand,
+__device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *q, uint32_t cand,
                                                   uint32_t rootm, const uint32_t (&bs)[BPS + 1],
                                                   const uint8_t *sb, uint32_t staged,
                                                   uint32_t unitid, uint32_t lima, uint32_t limb,
@@ -820,8 +820,7 @@ __device__ __noinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *q, 
 // pass over the slices listed in ovf_list.  The int argument is unused (the
 // launch signature is shared with the uncompressed kernel).
 template <int W, int BPS, int VAR, int EMIT>
-__global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const __grid_constant__ MatchParams P,
-                                                        const int) {
+__global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, const int) {
     constexpr bool emit = EMIT != 0;
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
