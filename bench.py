@@ -297,7 +297,7 @@ def run_ours(args):
             opt["scan_events"] = (sc_b[i], sc_e[i])
         pfac.match_async(tbl, text, seg, out, cnt, st, ws, stream=stream, **opt)
 
-    use_graph = args.graph or args.workload == "ids"
+    use_graph = not args.no_graph
     graph = None
     if use_graph:
         # the whole call (workspace clear, segment pass, scan, ordering kernels)
@@ -566,8 +566,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip pfac_autotune on a sample of the input (it runs by default "
                          "when no scan option is given)")
-    ap.add_argument("--graph", action="store_true",
-                    help="time CUDA-graph replays of the match call (default for packets)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every step's kernels directly instead of replaying the "
+                         "captured CUDA graph of one call")
     ap.add_argument("--loads", default="10,25,50,100,200,300,400")
     ap.add_argument("--serve-batches", type=int, default=48)
     ap.add_argument("--serve-slots", type=int, default=4)

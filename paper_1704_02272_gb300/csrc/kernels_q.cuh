@@ -225,12 +225,12 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
         nt += __popc(b);
     }
     __syncwarp();
-    // ---- outputs of the walks that ended in phases A and B
+    // ---- outputs of the walks that ended in phases A and B: loaded now,
+    // stored after phase D so the loads' latency overlaps the long walks
 #pragma unroll
     for (int u = 0; u < QU; u++) {
         if (state[u] == 1) fin[u] = __ldg(P.T.fin + st[u]);
         else if (state[u] == 2) fin[u] = __ldg(P.T.leaf_fin + st[u]);
-        if (state[u] >= 1) q[e0 + lane + 32u * u].x = fin[u];
     }
     // ---- phase D: the long walks, one per lane
     for (uint32_t t0 = 0; t0 < nt; t0 += 32) {
@@ -285,6 +285,9 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
             q[e].x = f;
         }
     }
+#pragma unroll
+    for (int u = 0; u < QU; u++)
+        if (state[u] >= 1) q[e0 + lane + 32u * u].x = fin[u];
     __syncwarp();
 }
 
@@ -924,6 +927,13 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
                 const uint64_t r = o > ustart ? o - ustart : 0;
                 wv = r < rem ? (uint32_t)r : rem;
             }
+            const uint32_t w0 = __shfl_sync(0xFFFFFFFFu, wv, 0);
+            const uint32_t w1 = __shfl_sync(0xFFFFFFFFu, wv, 1);
+            if (w0 >= (uint32_t)QSTAGE) {
+                // no segment end inside the stage: one limit for every lane
+                lima = w0 < rem ? w0 : rem;
+                limb = w1 < rem ? w1 : rem;
+            } else {
             const uint32_t p0 = lane * QBPT;
             uint32_t j = 0;
 #pragma unroll
@@ -946,6 +956,7 @@ __global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, cons
             const bool need = (last < (uint32_t)SLICE && last < rem) ||
                               (lima < p0 + QBPT && limb < p0 + QBPT);
             general_lims = __any_sync(0xFFFFFFFFu, need);
+            }
         }
 
         const uint32_t s = i % QRING;

@@ -300,3 +300,26 @@ def test_bitmap_copies_option(copies):
     w = workloads.tiny_case(410, 256, 1000, 2, 10, 1 << 20, n_plants=1000)
     ref = oracle_keys(w)
     assert_same(run(w, variant=pfac.VARIANT_FILTER, bitmap_copies=copies), ref, f"copies {copies}")
+
+
+@pytest.mark.parametrize("sigma,pattern", [(256, b"\x07"), (256, bytes(range(100))),
+                                           (4, b"\x01\x02\x03\x00\x01"), (2, b"\x01" * 33)])
+def test_single_pattern(sigma, pattern):
+    # one pattern: its occurrences are the positions where it is planted (and
+    # where the random text happens to hold it)
+    rs = np.random.RandomState(len(pattern) * 7 + sigma)
+    text = rs.randint(0, sigma, size=300_000).astype(np.uint8)
+    for p in rs.randint(0, text.size - len(pattern), size=200):
+        text[p:p + len(pattern)] = np.frombuffer(pattern, np.uint8)
+    w = workloads.Workload("single", sigma, [pattern], text, workloads.single_segment(text.size))
+    ref = check_all_variants(w, f"single pattern sigma {sigma}")
+    assert ref.size >= 150
+
+
+def test_patterns_longer_than_the_input():
+    # no walk can complete; short inputs and segments shorter than every pattern
+    pats = [bytes([1, 2, 3] * 20), bytes([2] * 70)]
+    text = np.tile(np.array([1, 2, 3], np.uint8), 15)
+    w = workloads.Workload("long-pats", 4, pats, text, workloads.single_segment(text.size))
+    ref = check_all_variants(w, "patterns longer than the input")
+    assert ref.size == 0
