@@ -119,7 +119,10 @@ typedef struct {
                               as a cheap second stage.  0 = library choice,
                               1 = off, 2 = required (one copy; excludes the
                               gram filter and bitmap_copies > 1) */
-    uint32_t reserved0;
+    uint32_t warps_per_cta; /* warps per CTA of the scan kernel: 0 = library
+                              choice (16, or the autotuner's), 16, or 24 (80
+                              registers a thread; only where the tables leave
+                              shared memory for 24 warps' buffers) */
     uint64_t starts_end;   /* 0 = every input position starts a walk; else
                               only positions below it do (at most n_bytes;
                               the bytes after it are still read by walks, as
@@ -191,6 +194,8 @@ typedef struct {
     uint32_t gram_bits;      /* log2 of the bits of one shared copy of the gram filter */
     uint32_t smem_bytes;     /* dynamic shared memory per CTA of the scan kernel */
     uint32_t prefix_bytes;   /* 1 = off, 2 = on */
+    uint32_t warps_per_cta;  /* warps per CTA of the scan kernel (0: uncompressed) */
+    uint32_t reserved;
 } pfac_plan_info;
 int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts, pfac_plan_info *out);
 
@@ -350,6 +355,7 @@ typedef struct {
     int from_cache;
     uint32_t gram_filter; /* 1 = off, 2 = on */
     uint32_t prefix_bytes; /* 1 = off, 2 = on */
+    uint32_t warps_per_cta;
 } pfac_tune_result;
 
 int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,

@@ -48,7 +48,7 @@ class MatchOpts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("bitmap_copies", ctypes.c_uint32),
                 ("ev_scan_begin", ctypes.c_void_p), ("ev_scan_end", ctypes.c_void_p),
                 ("child_masks", ctypes.c_uint32), ("gram_filter", ctypes.c_uint32),
-                ("prefix_bytes", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("prefix_bytes", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
                 ("starts_end", ctypes.c_uint64), ("position_base", ctypes.c_uint64)]
 
 
@@ -70,14 +70,15 @@ class TuneResult(ctypes.Structure):
                 ("n_tried", ctypes.c_uint32),
                 ("scan_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
                 ("from_cache", ctypes.c_int), ("gram_filter", ctypes.c_uint32),
-                ("prefix_bytes", ctypes.c_uint32)]
+                ("prefix_bytes", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_uint32), ("prefix_depth", ctypes.c_uint32),
                 ("bitmap_copies", ctypes.c_uint32), ("child_masks", ctypes.c_uint32),
                 ("gram_filter", ctypes.c_uint32), ("gram_bits", ctypes.c_uint32),
-                ("smem_bytes", ctypes.c_uint32), ("prefix_bytes", ctypes.c_uint32)]
+                ("smem_bytes", ctypes.c_uint32), ("prefix_bytes", ctypes.c_uint32),
+                ("warps_per_cta", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -171,11 +172,13 @@ def _stream(stream) -> int:
 
 
 def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,
-          gram_filter=0, prefix_bytes=0, starts_end=0, position_base=0, scan_events=None):
+          gram_filter=0, prefix_bytes=0, starts_end=0, position_base=0, warps_per_cta=0,
+          scan_events=None):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
     o.bitmap_copies, o.child_masks, o.gram_filter = bitmap_copies, child_masks, gram_filter
     o.prefix_bytes, o.starts_end, o.position_base = prefix_bytes, starts_end, position_base
+    o.warps_per_cta = warps_per_cta
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event
@@ -264,7 +267,7 @@ def plan(table: Table, **opt) -> dict:
     o = _opts(**opt)
     r = PlanInfo()
     _check(LIB.pfac_match_plan(table.handle, ctypes.byref(o), ctypes.byref(r)))
-    return {f: getattr(r, f) for f, _ in PlanInfo._fields_}
+    return {f: getattr(r, f) for f, _ in PlanInfo._fields_ if f != "reserved"}
 
 
 def match_host(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,

@@ -22,6 +22,7 @@ struct pfac_table {
     uint32_t tuned_masks = 0;
     uint32_t tuned_gram = 0;
     uint32_t tuned_bytes = 0;
+    uint32_t tuned_nw = 0;
 };
 
 namespace pfac {

@@ -27,8 +27,8 @@
 
 namespace pfac {
 
-constexpr int QW = 16;                   // warps per CTA
-constexpr int QTHREADS = QW * 32;
+constexpr int QW = 16;                   // warps per CTA (default; 24 is the other choice)
+constexpr int QW_WIDE = 24;
 constexpr int QBPT = 16;                 // start positions per lane per slice
 constexpr int SLICE = 32 * QBPT;         // 512 start positions per slice
 constexpr int SLICE_SHIFT = 9;
@@ -820,16 +820,19 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
 }
 
 // EMIT == 0: the scan pass (records and key counts).  EMIT == 1: the emit
-// pass over the slices listed in ovf_list.  The int argument is unused (the
+// pass over the slices listed in ovf_list.  NW warps per CTA: 16 (up to 128
+// registers a thread) or 24 (up to 80; more warps to hide latency where the
+// tables leave room in shared memory).  The int argument is unused (the
 // launch signature is shared with the uncompressed kernel).
-template <int W, int BPS, int VAR, int EMIT>
-__global__ void __launch_bounds__(QTHREADS, 1) k_scanq(const MatchParams P, const int) {
+template <int W, int BPS, int VAR, int EMIT, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_scanq(const MatchParams P, const int) {
+    constexpr uint32_t QTHREADS = NW * 32;
     constexpr bool emit = EMIT != 0;
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n_units = emit ? *(volatile uint32_t *)&P.hdr->ovf_count : P.n_tiles;
-    const uint32_t gw = blockIdx.x * QW + warp, gstride = gridDim.x * QW;
-    if (blockIdx.x * QW >= n_units) return;  // the whole CTA has no unit
+    const uint32_t gw = blockIdx.x * NW + warp, gstride = gridDim.x * NW;
+    if (blockIdx.x * NW >= n_units) return;  // the whole CTA has no unit
 
     uint32_t *Bs = reinterpret_cast<uint32_t *>(smem);  // prefix bytes, at offset 0
     uint32_t *Fs = Bs + P.tbl_b_words;

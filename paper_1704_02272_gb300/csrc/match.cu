@@ -13,14 +13,14 @@
 
 namespace pfac {
 
-void *scan_kernel_bps1(int, int);
-void *scan_kernel_bps2(int, int);
-void *scan_kernel_bps3(int, int);
-void *scan_kernel_bps4(int, int);
-void *scan_kernel_bps5(int, int);
-void *scan_kernel_bps6(int, int);
-void *scan_kernel_bps7(int, int);
-void *scan_kernel_bps8(int, int);
+void *scan_kernel_bps1(int, int, int);
+void *scan_kernel_bps2(int, int, int);
+void *scan_kernel_bps3(int, int, int);
+void *scan_kernel_bps4(int, int, int);
+void *scan_kernel_bps5(int, int, int);
+void *scan_kernel_bps6(int, int, int);
+void *scan_kernel_bps7(int, int, int);
+void *scan_kernel_bps8(int, int, int);
 void *scan_kernel_dense();
 
 constexpr int CHUNK = 1024;      // tiles per chunk of the key-count scan
@@ -232,6 +232,7 @@ struct Plan {
     uint32_t rep_log2;
     uint32_t tbl_g_words, g_rep, g_fold;  // gram filter: words (all copies), copies, fold
     uint32_t tbl_b_words;                 // prefix bytes as the first stage
+    uint32_t nw;                          // warps per CTA of the queued kernel
     uint32_t dense_rows;
     uint32_t unit_shift, unit_cap;
     void *kernel;       // scan pass
@@ -273,16 +274,16 @@ static WsLayout ws_layout(uint64_t n_bytes, uint32_t n_seg, const Plan &pl) {
     return L;
 }
 
-static void *scan_kernel_for(uint32_t bps, int var, int emit) {
+static void *scan_kernel_for(uint32_t bps, int var, int emit, int nw) {
     switch (bps) {
-        case 1: return scan_kernel_bps1(var, emit);
-        case 2: return scan_kernel_bps2(var, emit);
-        case 3: return scan_kernel_bps3(var, emit);
-        case 4: return scan_kernel_bps4(var, emit);
-        case 5: return scan_kernel_bps5(var, emit);
-        case 6: return scan_kernel_bps6(var, emit);
-        case 7: return scan_kernel_bps7(var, emit);
-        case 8: return scan_kernel_bps8(var, emit);
+        case 1: return scan_kernel_bps1(var, emit, nw);
+        case 2: return scan_kernel_bps2(var, emit, nw);
+        case 3: return scan_kernel_bps3(var, emit, nw);
+        case 4: return scan_kernel_bps4(var, emit, nw);
+        case 5: return scan_kernel_bps5(var, emit, nw);
+        case 6: return scan_kernel_bps6(var, emit, nw);
+        case 7: return scan_kernel_bps7(var, emit, nw);
+        case 8: return scan_kernel_bps8(var, emit, nw);
         default: return nullptr;
     }
 }
@@ -295,9 +296,9 @@ static size_t dense_smem(uint32_t tbl_words) {
 
 constexpr size_t SMEM_LIMIT = 232448;  // per-CTA dynamic shared memory on sm_103a
 
-static size_t queued_smem(uint64_t words) {
+static size_t queued_smem(uint64_t words, uint32_t nw = QW) {
     const size_t tbl = ((size_t)words * 4 + 127) & ~(size_t)127;
-    return tbl + QW * sizeof(WarpArea);
+    return tbl + nw * sizeof(WarpArea);
 }
 
 // Shared-memory wavefronts of one warp-wide bitmap load with 2^rep copies
@@ -347,6 +348,10 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     // the table's tuned choice applies only when the caller picks neither the
     // variant nor the depth
     const bool use_tuned = !(opts && (opts->variant || opts->prefix_depth));
+    const uint32_t nwant = opts && opts->warps_per_cta ? opts->warps_per_cta
+                                                      : (use_tuned && t->tuned_nw ? t->tuned_nw : QW);
+    if (nwant != QW && nwant != QW_WIDE)
+        return set_error(PFAC_EINVAL, "pfac_match: warps_per_cta %u (16 or 24)", nwant);
     const uint32_t masks = opts && opts->child_masks ? opts->child_masks
                                                     : (use_tuned ? t->tuned_masks : 0u);
     if (masks > 2) return set_error(PFAC_EINVAL, "pfac_match: child_masks %u", masks);
@@ -386,7 +391,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     auto best_rep = [&](uint64_t extra) -> int {
         int rep = -1;
         for (int r = 0; r <= 5; r++)
-            if (queued_smem(((uint64_t)fw << r) + cw + extra) <= SMEM_LIMIT) rep = r;
+            if (queued_smem(((uint64_t)fw << r) + cw + extra, nwant) <= SMEM_LIMIT) rep = r;
         return rep;
     };
     int var_f = var;
@@ -428,7 +433,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                 for (int r = 0; r <= 5; r++) {
                     if (want >= 0 && r != want) continue;
                     for (uint32_t f = 0; hb - f >= GRAM_MIN_BITS; f++) {
-                        if (queued_smem(base + ((gw0 >> f) << r)) > SMEM_LIMIT) continue;
+                        if (queued_smem(base + ((gw0 >> f) << r), nwant) > SMEM_LIMIT) continue;
                         // expected share of positions through the first stage
                         const double dens =
                             1.0 - exp(-(double)T.g_set / (double)(1ull << (hb - f)));
@@ -469,8 +474,8 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                 const bool mon = mm == 1;
                 if (mon && !(have_m && masks != 1)) continue;
                 if (!mon && masks == 2) continue;
-                if (queued_smem(bw + fw + cw + (vv == VAR_FE ? ew : 0u) + (mon ? mw : 0u)) <=
-                    SMEM_LIMIT) {
+                if (queued_smem(bw + fw + cw + (vv == VAR_FE ? ew : 0u) + (mon ? mw : 0u),
+                                nwant) <= SMEM_LIMIT) {
                     var_b = vv;
                     m_b = mon;
                     use_b = pbytes == 2 || (!use_g && dens_f >= 0.01);
@@ -515,10 +520,15 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     pl->var = var;
     pl->k = k;
     pl->tbl_c_words = cw;
-    pl->kernel = scan_kernel_for(T.bps, var, 0);
-    pl->kernel_emit = scan_kernel_for(T.bps, var, 1);
-    pl->smem = queued_smem((uint64_t)pl->tbl_b_words + pl->tbl_words + pl->tbl_c_words +
-                           pl->tbl_e_words + pl->tbl_m_words + pl->tbl_g_words);
+    // a wider CTA on request, when the tables leave room for its warps
+    const uint64_t tw = (uint64_t)pl->tbl_b_words + pl->tbl_words + pl->tbl_c_words +
+                        pl->tbl_e_words + pl->tbl_m_words + pl->tbl_g_words;
+    if (queued_smem(tw, nwant) > SMEM_LIMIT)
+        return set_error(PFAC_EINVAL, "pfac_match: %u warps do not fit next to the tables", nwant);
+    pl->nw = nwant;
+    pl->kernel = scan_kernel_for(T.bps, var, 0, (int)nwant);
+    pl->kernel_emit = scan_kernel_for(T.bps, var, 1, (int)nwant);
+    pl->smem = queued_smem(tw, nwant);
     pl->unit_shift = SLICE_SHIFT;
     pl->unit_cap = SCAP;
     pl->queued = true;
@@ -591,6 +601,7 @@ extern "C" int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts,
     out->gram_filter = g ? 2u : 1u;
     out->gram_bits = g ? t->dev.g_bits - pl.g_fold : 0u;
     out->prefix_bytes = pl.tbl_b_words ? 2u : 1u;
+    out->warps_per_cta = pl.nw;
     return PFAC_OK;
 }
 
@@ -680,8 +691,8 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.tbl_e_words = pl.tbl_e_words;
     P.rep_log2 = pl.rep_log2;
     P.dense_rows = pl.dense_rows;
-    const uint32_t nthreads = pl.queued ? QTHREADS : NTHREADS;
-    const uint32_t units_per_cta = pl.queued ? QW : 1;
+    const uint32_t nthreads = pl.queued ? pl.nw * 32 : NTHREADS;
+    const uint32_t units_per_cta = pl.queued ? pl.nw : 1;
 
     // header, and for the queued kernel the per-unit record and key counts
     // (the scan pass writes them only for units with kept survivors)

@@ -11,14 +11,21 @@ namespace pfac {
 static constexpr int kBps = PFAC_SCAN_BPS;
 static constexpr int kW = kBps <= 5 ? 1 : (kBps == 6 ? 2 : 8);
 
-void *PFAC_CAT(scan_kernel_bps, PFAC_SCAN_BPS)(int var, int emit) {
+template <int NW>
+static void *scan_kernel_nw(int var, int emit) {
     switch (var * 2 + (emit ? 1 : 0)) {
-        case VAR_F * 2: return (void *)k_scanq<kW, kBps, VAR_F, 0>;
-        case VAR_F * 2 + 1: return (void *)k_scanq<kW, kBps, VAR_F, 1>;
-        case VAR_FE * 2: return (void *)k_scanq<kW, kBps, VAR_FE, 0>;
-        case VAR_FE * 2 + 1: return (void *)k_scanq<kW, kBps, VAR_FE, 1>;
+        case VAR_F * 2: return (void *)k_scanq<kW, kBps, VAR_F, 0, NW>;
+        case VAR_F * 2 + 1: return (void *)k_scanq<kW, kBps, VAR_F, 1, NW>;
+        case VAR_FE * 2: return (void *)k_scanq<kW, kBps, VAR_FE, 0, NW>;
+        case VAR_FE * 2 + 1: return (void *)k_scanq<kW, kBps, VAR_FE, 1, NW>;
         default: return nullptr;
     }
+}
+
+void *PFAC_CAT(scan_kernel_bps, PFAC_SCAN_BPS)(int var, int emit, int nw) {
+    if (nw == QW) return scan_kernel_nw<QW>(var, emit);
+    if (nw == QW_WIDE) return scan_kernel_nw<QW_WIDE>(var, emit);
+    return nullptr;
 }
 
 }  // namespace pfac

@@ -37,18 +37,21 @@ std::string cache_key(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments
 }
 
 bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_t *k,
-                  uint32_t *c, uint32_t *mk, uint32_t *gf, uint32_t *pb, float *ms) {
+                  uint32_t *c, uint32_t *mk, uint32_t *gf, uint32_t *pb, uint32_t *nw,
+                  float *ms) {
     FILE *f = fopen(path, "r");
     if (!f) return false;
     char line[512];
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char kbuf[300];
-        uint32_t a, b, d, g, h, y;
+        uint32_t a, b, d, g, h, y, z;
         float e;
-        if (sscanf(line, "%299s %u %u %u %u %u %u %f", kbuf, &a, &b, &d, &g, &h, &y, &e) == 8 &&
+        if (sscanf(line, "%299s %u %u %u %u %u %u %u %f", kbuf, &a, &b, &d, &g, &h, &y, &z,
+                   &e) == 9 &&
             key == kbuf) {
             *pb = y;
+            *nw = z;
             *v = a;
             *k = b;
             *c = d;
@@ -75,12 +78,14 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     memset(&res, 0, sizeof res);
     const std::string key = cache_key(t, n_bytes, n_segments);
     if (cache_path) {
-        uint32_t v, k, c, mk, gf, pb;
+        uint32_t v, k, c, mk, gf, pb, nw;
         float ms;
-        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &ms) && k >= t->kmin &&
+        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &nw, &ms) && k >= t->kmin &&
             k <= t->kmax && (gf != 2 || t->dev.g_len) && (pb != 2 || t->dev.B[k])) {
             t->tuned_bytes = pb;
+            t->tuned_nw = nw;
             res.prefix_bytes = pb;
+            res.warps_per_cta = nw;
             t->tuned_variant = v;
             t->tuned_k = k;
             t->tuned_copies = c;
@@ -101,22 +106,24 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     // forget an earlier choice so the default is measured as the library's own
     t->tuned_variant = t->tuned_k = t->tuned_copies = t->tuned_masks = t->tuned_gram = 0;
     t->tuned_bytes = 0;
+    t->tuned_nw = 0;
 
     struct Cand {
-        uint32_t var, k, copies, masks, gram, bytes;
+        uint32_t var, k, copies, masks, gram, bytes, nw;
         float ms;
     };
     std::vector<Cand> cands;
-    cands.push_back({0, 0, 0, 0, 0, 0, 0.f});  // library default
+    cands.push_back({0, 0, 0, 0, 0, 0, 0, 0.f});  // library default
     const uint32_t gmax = t->dev.g_len ? 2u : 1u;
-    for (uint32_t k = t->kmin; k <= t->kmax; k++)
-        for (uint32_t var = 1; var <= 2; var++)
-            for (uint32_t masks = 1; masks <= 2; masks++) {
-                for (uint32_t gram = 1; gram <= gmax; gram++)
-                    for (uint32_t copies = 32; copies >= 1; copies >>= 1)
-                        cands.push_back({var, k, copies, masks, gram, 1, 0.f});
-                if (t->dev.B[k]) cands.push_back({var, k, 1, masks, 1, 2, 0.f});
-            }
+    for (uint32_t nw : {16u, 24u})
+        for (uint32_t k = t->kmin; k <= t->kmax; k++)
+            for (uint32_t var = 1; var <= 2; var++)
+                for (uint32_t masks = 1; masks <= 2; masks++) {
+                    for (uint32_t gram = 1; gram <= gmax; gram++)
+                        for (uint32_t copies = 32; copies >= 1; copies >>= 1)
+                            cands.push_back({var, k, copies, masks, gram, 1, nw, 0.f});
+                    if (t->dev.B[k]) cands.push_back({var, k, 1, masks, 1, 2, nw, 0.f});
+                }
 
     uint64_t ws_max = 0;
     std::vector<Cand> ok;
@@ -129,6 +136,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.child_masks = c.masks;
         o.gram_filter = c.gram;
         o.prefix_bytes = c.bytes;
+        o.warps_per_cta = c.nw;
         uint64_t b = 0;
         if (pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b) != PFAC_OK) continue;
         ws_max = std::max(ws_max, b);
@@ -160,6 +168,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.child_masks = c.masks;
         o.gram_filter = c.gram;
         o.prefix_bytes = c.bytes;
+        o.warps_per_cta = c.nw;
         uint64_t b = 0;
         pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b);
         // warm-up, then the median of three timed scans
@@ -212,6 +221,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         t->tuned_masks = best.masks;
         t->tuned_gram = best.gram;
         t->tuned_bytes = best.bytes;
+        t->tuned_nw = best.nw;
     }
     res.variant = best.var;
     res.prefix_depth = best.k;
@@ -219,12 +229,13 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     res.child_masks = best.masks;
     res.gram_filter = best.gram;
     res.prefix_bytes = best.bytes;
+    res.warps_per_cta = best.nw;
     res.scan_ms = best.ms;
     if (cache_path && best.var) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k, best.copies,
-                    best.masks, best.gram, best.bytes, best.ms);
+            fprintf(f, "%s %u %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k,
+                    best.copies, best.masks, best.gram, best.bytes, best.nw, best.ms);
             fclose(f);
         }
     }

@@ -323,3 +323,25 @@ def test_patterns_longer_than_the_input():
     w = workloads.Workload("long-pats", 4, pats, text, workloads.single_segment(text.size))
     ref = check_all_variants(w, "patterns longer than the input")
     assert ref.size == 0
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"s{c[0]}-sig{c[1]}" for c in CASES])
+def test_wide_cta(case):
+    # 24 warps per CTA (80 registers a thread) wherever the tables leave room
+    seed, sigma, n, lo, hi, N, S, plants, ts = case
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, N, n_segments=S, n_plants=plants,
+                            text_sigma=ts)
+    ref = oracle_keys(w)
+    with pfac.Table(w.patterns, w.sigma, host_only=True) as th:
+        kdef = th.info()["prefix_depth"]
+    ran = 0
+    for k in (kdef, max(1, kdef - 2)):
+        for extra in ({}, {"gram_filter": 2}, {"child_masks": 2}):
+            try:
+                got = run(w, prefix_depth=k, warps_per_cta=24, **extra)
+            except pfac.PfacError as e:  # does not fit
+                assert e.status == -1, str(e)
+                continue
+            assert_same(got, ref, f"24 warps depth {k} {extra}")
+            ran += 1
+    assert ran >= 1
