@@ -441,6 +441,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                     // planner folds it down to fit shared memory)
                     g_bits = GRAM_MIN_BITS;
                     while (g_bits < GRAM_MAX_BITS && (1ull << g_bits) < 64 * g_set) g_bits++;
+                    // larger pattern sets get room for a sparse first stage even
+                    // when few strings are set (the planner folds it as needed)
+                    const uint32_t floor_bits = n_patterns >= 1000 ? 20u : (n_patterns >= 100 ? 18u : 0u);
+                    if (g_bits < floor_bits) g_bits = floor_bits;
                     Gv.assign((1ull << g_bits) / 32, 0);
                 }
             }
