@@ -278,6 +278,8 @@ def run_ours(args):
         user_opt["gram_filter"] = args.gram
     if args.bytes:
         user_opt["prefix_bytes"] = args.bytes
+    if args.warps:
+        user_opt["warps_per_cta"] = args.warps
     tune = None
     if not args.no_autotune and not user_opt:
         # the autotuner on a bounded prefix sample of the input (whole
@@ -560,6 +562,7 @@ def main():
     ap.add_argument("--masks", type=int, default=0, help="child masks: 1 off, 2 on")
     ap.add_argument("--gram", type=int, default=0, help="gram filter first stage: 1 off, 2 on")
     ap.add_argument("--bytes", type=int, default=0, help="prefix bytes first stage: 1 off, 2 on")
+    ap.add_argument("--warps", type=int, default=0, help="scan-kernel warps per CTA: 16 or 24")
     ap.add_argument("--truncate", type=int, default=0,
                     help="prefix matching (Section 2.4): tables hold the patterns cut to this "
                          "many symbols; the timed step yields candidates, verified after")
