@@ -4,22 +4,27 @@
 // * Work unit: a 512-byte slice of the input.  Slice g goes to global warp
 //   g mod (warps in the grid); every warp streams its own slices with
 //   cp.async.bulk into a private 4-stage ring of 528-byte stages (slice plus
-//   a 16-byte halo), each stage with its own mbarrier.
-// * Filter: each lane owns 16 start positions of the slice.  For each it
-//   forms the index of the next k symbols and tests the depth-k prefix
-//   bitmap F_k held in shared memory (replicated over bank groups so a
-//   warp's 32 random lookups conflict little).  Positions whose k-symbol
-//   window is not available (segment end, input end, symbol outside the
-//   packed range) become "root" survivors that walk from the root.
-// * Survivors go to a per-warp queue in shared memory.  When it is nearly
-//   full the warp resolves it in one batch: four queue entries per lane, all
-//   advanced in lockstep, so each lane keeps several independent loads in
-//   flight.  Resolution ranks the prefix index in F_k (block counts C_k plus
-//   popcounts, Eq. 1 applied to the prefix level) to read its entry E_k (the
-//   state at depth k or the output of a walk that stopped earlier), then walks
-//   the records through L2 one level per round.
+//   a 16-byte halo), each stage with its own mbarrier.  CTAs have 16 or 24
+//   warps.
+// * First stage: each lane owns 16 start positions of the slice and tests
+//   each against a table in shared memory: the depth-k prefix bitmap F_k
+//   (replicated over bank groups so a warp's 32 random lookups conflict
+//   little), the prefix bytes B_k (one byte per index), or the hashed gram
+//   filter G over the next g symbols.  Positions whose window is not
+//   available (segment end, input end, symbol outside the packed range)
+//   become "root" survivors that walk from the root.
+// * Second stage, per candidate: the exact F_k bit (after G), the bucket of
+//   the next symbol (after B_k), the child mask of the entry (M_k).
+// * Survivors go to a per-warp queue in shared memory.  When a slice's do
+//   not fit, the warp resolves the queue in one batch: four queue entries
+//   per lane, all advanced in lockstep, so each lane keeps several
+//   independent loads in flight.  Resolution ranks the prefix index in F_k
+//   (block counts C_k plus popcounts, Eq. 1 applied to the prefix level) to
+//   read its entry E_k (the state at depth k or the output of a walk that
+//   stopped earlier), walks the records through L2 one level per round, and
+//   finishes long walks one per lane along consecutive chain records.
 // * Output: per slice, the survivors' (position, fin) records in position
-//   order plus the slice's key count; slices with more survivors than their
+//   order plus the slice's key count; slices with more matches than their
 //   record space are resolved immediately in quarters (counting only) and
 //   re-run by the emit pass, which writes their keys directly.
 #pragma once
