@@ -241,9 +241,9 @@ int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
  * (Section 2.3 semantics; library extension for end-to-end use: the paper
  * does not say how the text reaches the GPU or how results return).  The
  * text is cut into chunks of chunk_bytes start positions (0 = 32 MiB;
- * rounded up to 256) plus a read halo of max_len - 1 bytes; chunk i's copy
- * to the device, the matching of chunk i - 1 and the copy back of chunk
- * i - 2's keys overlap on three streams.  Each chunk is matched with
+ * rounded up to 256) plus a read halo of max_len - 1 bytes; three chunks are
+ * in flight at once: copies to the device, matching and the copy back of
+ * keys overlap on three streams.  Each chunk is matched with
  * starts_end / position_base (pfac_match_opts), so the keys arrive in
  * global order without filtering.  Pinned host buffers (cudaHostAlloc /
  * cudaHostRegister) make the copies asynchronous; pageable ones work but
@@ -261,7 +261,7 @@ int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t n_bytes,
  *                    streams of the library's own); the call returns after
  *                    all work completed
  *
- * Device memory for two chunks (inputs, workspaces, keys), the two copy
+ * Device memory for three chunks (inputs, workspaces, keys), the two copy
  * streams and pinned staging are kept per device between calls and grown on
  * demand; pfac_match_host_release frees them.  Calls from several host
  * threads are serialised.  chunk_bytes = 0 uses 32 MiB.

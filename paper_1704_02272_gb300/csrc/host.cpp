@@ -2,9 +2,9 @@
 // copies pipelined against the matching.  The text is cut into chunks of
 // start positions; chunk i is matched on the caller's stream over its bytes
 // plus a read halo of max_len - 1 (starts_end / position_base keep its keys
-// to its own starts, in global positions), while chunk i + 1 is copied in on
-// one library stream and chunk i - 1's keys are copied out on another.  Two
-// slots of device buffers alternate.
+// to its own starts, in global positions), while later chunks are copied in
+// on one library stream and earlier chunks' keys are copied out on another.
+// Three slots of device buffers rotate.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -21,8 +21,9 @@ namespace {
 // Pinned staging for the chunks' local segment offsets, kept between calls
 // (allocating pinned memory per call costs more than the copies it serves).
 std::mutex g_host_mu;
-uint64_t *g_pin[2] = {nullptr, nullptr};
-size_t g_pin_words[2] = {0, 0};
+constexpr int NSLOT = 3;  // chunks in flight: copy in, match, copy out
+uint64_t *g_pin[NSLOT] = {nullptr, nullptr, nullptr};
+size_t g_pin_words[NSLOT] = {0, 0, 0};
 uint64_t *g_pin_small = nullptr;  // per slot: count, status
 
 bool pin_reserve(int s, size_t words) {
@@ -52,7 +53,7 @@ struct Slot {
 struct HostCtx {
     bool init = false;
     cudaStream_t h2d = nullptr, d2h = nullptr;
-    Slot sl[2];
+    Slot sl[NSLOT];
     uint64_t in_cap = 0, seg_cap = 0, ws_cap = 0, keys_cap = 0;
     uint64_t keys_hint = 0;  // largest chunk key count seen (keys)
 };
@@ -75,7 +76,7 @@ cudaError_t ctx_prepare(HostCtx &c, uint64_t in_b, uint64_t seg_b, uint64_t ws_b
     if (!c.init) {
         e = cudaStreamCreateWithFlags(&c.h2d, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.d2h, cudaStreamNonBlocking);
-        for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+        for (int s = 0; s < NSLOT && e == cudaSuccess; s++) {
             e = cudaEventCreateWithFlags(&c.sl[s].h2d, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.sl[s].done, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.sl[s].d2h, cudaEventDisableTiming);
@@ -88,7 +89,7 @@ cudaError_t ctx_prepare(HostCtx &c, uint64_t in_b, uint64_t seg_b, uint64_t ws_b
     uint64_t cap[4];
     const uint64_t want[4] = {in_b, seg_b, ws_b, keys_b};
     const uint64_t have[4] = {c.in_cap, c.seg_cap, c.ws_cap, c.keys_cap};
-    for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+    for (int s = 0; s < NSLOT && e == cudaSuccess; s++) {
         void **bufs[4] = {(void **)&c.sl[s].in, (void **)&c.sl[s].seg, &c.sl[s].ws,
                           (void **)&c.sl[s].keys};
         for (int b = 0; b < 4 && e == cudaSuccess; b++) {
@@ -114,7 +115,7 @@ extern "C" void pfac_match_host_release(void) {
     HostCtx &c = g_ctx[dev];
     if (!c.init) return;
     cudaDeviceSynchronize();
-    for (int s = 0; s < 2; s++) {
+    for (int s = 0; s < NSLOT; s++) {
         cudaFree(c.sl[s].in);
         cudaFree(c.sl[s].seg);
         cudaFree(c.sl[s].ws);
@@ -188,7 +189,8 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
         cudaGetLastError();
         g_pin_small = nullptr;
     }
-    if (!g_pin_small || !pin_reserve(0, max_local) || !pin_reserve(1, max_local))
+    if (!g_pin_small || !pin_reserve(0, max_local) || !pin_reserve(1, max_local) ||
+        !pin_reserve(2, max_local))
         return set_error(PFAC_ENOMEM, "pfac_match_host: pinned staging of %zu offsets", max_local);
 
     int dev = 0;
@@ -218,13 +220,13 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
         uint64_t chunk, off, count;
     };
     std::vector<Redo> redo;
-    uint64_t *hcnt[2] = {g_pin_small, g_pin_small + 2};  // count, status (pinned copies)
+    uint64_t *hcnt[NSLOT] = {g_pin_small, g_pin_small + 2, g_pin_small + 4};  // count, status
     uint64_t total = 0;
     int status = PFAC_OK;
 
     // copies out the keys of chunk j once its count is known
     auto finish = [&](uint64_t j) -> bool {
-        const int s = (int)(j & 1);
+        const int s = (int)(j % NSLOT);
         if (cudaEventSynchronize(sl[s].done) != cudaSuccess) return false;
         const uint64_t c = hcnt[s][0];
         const int32_t st = (int32_t)(uint32_t)hcnt[s][1];
@@ -244,26 +246,26 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
     };
 
     for (uint64_t i = 0; i < n_chunks && ce == cudaSuccess && rc == PFAC_OK; i++) {
-        const int s = (int)(i & 1);
+        const int s = (int)(i % NSLOT);
         uint64_t a, b, e;
         const uint64_t *lo, *hi;
         bounds(i, a, b, e, lo, hi);
         // the slot's staging is free once the copies of chunk i - 2 are done
-        if (i >= 2) ce = cudaEventSynchronize(sl[s].h2d);
+        if (i >= NSLOT) ce = cudaEventSynchronize(sl[s].h2d);
         if (ce != cudaSuccess) break;
         uint64_t *loc = g_pin[s];
         size_t nl = 0;
         loc[nl++] = 0;
         for (const uint64_t *p = lo; p < hi; p++) loc[nl++] = *p - a;
         loc[nl++] = e - a;
-        if (i >= 2) ce = cudaStreamWaitEvent(h2d, sl[s].done, 0);  // chunk i - 2 read its input
+        if (i >= NSLOT) ce = cudaStreamWaitEvent(h2d, sl[s].done, 0);  // chunk i - 3 read its input
         if (ce == cudaSuccess)
             ce = cudaMemcpyAsync(sl[s].in, h_input + a, e - a, cudaMemcpyHostToDevice, h2d);
         if (ce == cudaSuccess)
             ce = cudaMemcpyAsync(sl[s].seg, loc, nl * 8, cudaMemcpyHostToDevice, h2d);
         if (ce == cudaSuccess) ce = cudaEventRecord(sl[s].h2d, h2d);
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(comp, sl[s].h2d, 0);
-        if (ce == cudaSuccess && i >= 2) ce = cudaStreamWaitEvent(comp, sl[s].d2h, 0);
+        if (ce == cudaSuccess && i >= NSLOT) ce = cudaStreamWaitEvent(comp, sl[s].d2h, 0);
         if (ce != cudaSuccess) break;
         o.starts_end = b - a;
         o.position_base = a;
@@ -273,9 +275,12 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
         if (rc != PFAC_OK) break;
         ce = cudaMemcpyAsync(hcnt[s], sl[s].small, 16, cudaMemcpyDeviceToHost, comp);
         if (ce == cudaSuccess) ce = cudaEventRecord(sl[s].done, comp);
-        if (ce == cudaSuccess && i >= 1 && !finish(i - 1)) ce = cudaErrorUnknown;
+        // the host waits for the oldest chunk in flight, two behind
+        if (ce == cudaSuccess && i >= NSLOT - 1 && !finish(i - (NSLOT - 1))) ce = cudaErrorUnknown;
     }
-    if (ce == cudaSuccess && rc == PFAC_OK && !finish(n_chunks - 1)) ce = cudaErrorUnknown;
+    for (uint64_t j = n_chunks > NSLOT - 1 ? n_chunks - (NSLOT - 1) : 0;
+         j < n_chunks && ce == cudaSuccess && rc == PFAC_OK; j++)
+        if (!finish(j)) ce = cudaErrorUnknown;
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(d2h);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h2d);
 
