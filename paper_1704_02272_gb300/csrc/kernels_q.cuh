@@ -143,7 +143,7 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                                              const uint32_t *Es, uint32_t *tail,
                                              uint32_t lane) {
     constexpr int QU = walks_per_lane(W);
-    constexpr int LOCK_ROUNDS = 2;
+    constexpr int LOCK_ROUNDS = 3;
     const uint32_t sigma = P.T.sigma, k = P.k, rep = P.rep_log2;
     const uint32_t *__restrict__ rec = P.T.rec;
     uint32_t st[QU], qq[QU], lim[QU], fin[QU], unit[QU];
@@ -351,13 +351,17 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
         const uint32_t wmask = (kmask >> 5) << (rep + 2);
         const uint32_t c4 = (lane & ((1u << rep) - 1u)) << 2;
         const uint8_t *Fb = reinterpret_cast<const uint8_t *>(Fs);
+        // Each test rotates bit t & 31 of its word to bit 0 and shifts it in
+        // at the top of acc (one funnel shift): position j ends at bit 16 + j.
+        uint32_t acc = 0;
 #pragma unroll
         for (int j = 0; j < QBPT; j++) {
             const uint32_t t = symbols_at<BPS>(bs, j);
             const uint32_t w = *reinterpret_cast<const uint32_t *>(
                 Fb + ((__funnelshift_r(t, t, ramt) & wmask) | c4));
-            surv |= (__funnelshift_r(w, w, t) & 1u) << j;  // bit t & 31 of the word
+            acc = __funnelshift_r(acc, __funnelshift_r(w, w, t), 1);
         }
+        surv = acc >> (32 - QBPT);
     } else {
         // gram filter: y = x * GRAM_MUL for the g-symbol string x; word =
         // top hbw bits of y, bit = y & 31 (table.h), copies interleaved
@@ -367,13 +371,15 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
         const uint32_t gwm = ((1u << hbw) - 1u) << (gr + 2);
         const uint32_t c4 = (lane & ((1u << gr) - 1u)) << 2;
         const uint8_t *Gb = reinterpret_cast<const uint8_t *>(Gs);
+        uint32_t acc = 0;  // as for the bitmap: position j ends at bit 16 + j
 #pragma unroll
         for (int j = 0; j < QBPT; j++) {
             const uint32_t y = (symbols_at<BPS>(bs, j) & gmask) * GRAM_MUL;
             const uint32_t w =
                 *reinterpret_cast<const uint32_t *>(Gb + (((y >> gsh) & gwm) | c4));
-            surv |= (__funnelshift_r(w, w, y) & 1u) << j;  // bit y & 31 of the word
+            acc = __funnelshift_r(acc, __funnelshift_r(w, w, y), 1);  // bit y & 31
         }
+        surv = acc >> (32 - QBPT);
     }
     // positions whose k-symbol window is available in this segment and stage
     const uint32_t lim0 = lima < staged ? lima : staged;
@@ -609,14 +615,6 @@ __device__ __forceinline__ int append_slice(const MatchParams &P, QEntry *q, uin
     const bool stage2 = P.tbl_m_words != 0 || P.tbl_g_words != 0 || P.tbl_b_words != 0;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t p0 = lane * QBPT;
-    uint32_t inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-        if (lane >= (uint32_t)o) inc += nb;
-    }
-    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-    const uint32_t excl = inc - c;
     auto entry = [&](uint32_t p, uint32_t x, uint32_t lim, uint32_t slot, bool last) {
         QEntry en;
         en.unit = unit;
@@ -661,6 +659,14 @@ __device__ __forceinline__ int append_slice(const MatchParams &P, QEntry *q, uin
         return AP_DONE;
     }
 
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += nb;
+    }
+    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    const uint32_t excl = inc - c;
     if (tot <= (uint32_t)QCAP) {
         // Each lane parks its candidates in the scratch as one word: position
         // (9 bits), prefix index (21 bits; narrow symbols only, wide ones
