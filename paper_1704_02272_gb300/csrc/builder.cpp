@@ -394,9 +394,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                         g_set += n;
                         return;
                     }
+                    const uint32_t gm = gram_mul(bps * g_len);
                     for (uint64_t y = 0; y < n; y++) {
-                        const uint32_t h = (x | (uint32_t)(y << (bps * d))) * GRAM_MUL;
-                        Gv[gram_word(h, g_bits)] |= 1u << (h & 31);
+                        const uint32_t s = x | (uint32_t)(y << (bps * d));
+                        Gv[gram_word(s * gm, g_bits)] |= 1u << (s & 31);
                     }
                 };
                 std::vector<std::pair<uint32_t, uint32_t>> stack;  // node, packed prefix

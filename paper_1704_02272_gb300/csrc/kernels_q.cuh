@@ -363,9 +363,10 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
         }
         surv = acc >> (32 - QBPT);
     } else {
-        // gram filter: y = x * GRAM_MUL for the g-symbol string x; word =
-        // top hbw bits of y, bit = y & 31 (table.h), copies interleaved
-        const uint32_t gmask = BPS * k >= 32 ? 0xFFFFFFFFu : (1u << (BPS * k)) - 1u;
+        // gram filter: y = t * gram_mul(g * BPS) for the window t (its bits
+        // above the g symbols drop out of y); word = top hbw bits of y, bit
+        // = t & 31 (table.h), copies interleaved
+        const uint32_t gm = gram_mul(BPS * k);
         const uint32_t gr = P.g_rep, hbw = P.g_hb - 5;
         const uint32_t gsh = 30u - hbw - gr;  // y >> gsh puts the word at bit gr + 2
         const uint32_t gwm = ((1u << hbw) - 1u) << (gr + 2);
@@ -374,10 +375,11 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
         uint32_t acc = 0;  // as for the bitmap: position j ends at bit 16 + j
 #pragma unroll
         for (int j = 0; j < QBPT; j++) {
-            const uint32_t y = (symbols_at<BPS>(bs, j) & gmask) * GRAM_MUL;
+            const uint32_t t = symbols_at<BPS>(bs, j);
+            const uint32_t y = t * gm;
             const uint32_t w =
                 *reinterpret_cast<const uint32_t *>(Gb + (((y >> gsh) & gwm) | c4));
-            acc = __funnelshift_r(acc, __funnelshift_r(w, w, y), 1);  // bit y & 31
+            acc = __funnelshift_r(acc, __funnelshift_r(w, w, t), 1);  // bit t & 31
         }
         surv = acc >> (32 - QBPT);
     }

@@ -64,11 +64,17 @@ constexpr uint32_t FIN_MAX_OFF = (1u << (31 - FIN_LEN_BITS)) - 1;
 //           words before each word, one byte per word)
 __host__ __device__ constexpr int rec_words(int W) { return W == 1 ? 2 : (W == 2 ? 4 : 12); }
 
-// Gram filter hash: y = x * GRAM_MUL (Knuth's multiplicative hashing with
-// the golden-ratio constant); the word is the top hb - 5 bits of y, the bit
-// within the word its low 5 bits.
+// Gram filter hash of a string x of n = g * bps <= 32 bits: y = x * m with
+// m = GRAM_MUL << (32 - n) (Knuth's multiplicative hashing with the
+// golden-ratio constant, on an n-bit word); the word is the top hb - 5 bits
+// of y, the bit within the word the low 5 bits of x.  Because the low
+// 32 - n bits of m are zero, y ignores the bits of x above n: a 32-bit
+// window holding the string in its low bits hashes without a mask.
 constexpr uint32_t GRAM_MUL = 0x9E3779B1u;
 constexpr uint32_t GRAM_MIN_BITS = 10, GRAM_MAX_BITS = 20;
+__host__ __device__ inline uint32_t gram_mul(uint32_t n) {
+    return n >= 32 ? GRAM_MUL : GRAM_MUL << (32 - n);
+}
 __host__ __device__ inline uint32_t gram_word(uint32_t y, uint32_t hb) { return y >> (37 - hb); }
 
 // Bits per child mask: 4 for alphabets of up to 4 symbols, 8 up to 8, else
