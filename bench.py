@@ -42,13 +42,13 @@ SCAN_KERNELS_PER_STEP = 5  # scan, key-count reduce, offsets, overflow re-scan, 
 # ncu capture per workload (summaries under profiles/), with the digest of the
 # kernel sources it was taken on; reported only while the sources still match
 MEASURED_TRAFFIC = {
-    "dna": (306737664, "ab16ddd27fc8bc9e",
+    "dna": (306780928, "dc8525eacb2c3b8e",
             {"variant": 1, "prefix_depth": 10, "bitmap_copies": 1, "child_masks": 1,
              "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 16}),
-    "sweep-256-1000": (547242496, "ab16ddd27fc8bc9e",
+    "sweep-256-1000": (546757632, "dc8525eacb2c3b8e",
                        {"variant": 2, "prefix_depth": 2, "bitmap_copies": 1, "child_masks": 1,
                         "gram_filter": 2, "prefix_bytes": 1, "warps_per_cta": 24}),
-    "ids": (1293339136, "ab16ddd27fc8bc9e",
+    "ids": (1292476160, "dc8525eacb2c3b8e",
             {"variant": 1, "prefix_depth": 2, "bitmap_copies": 1, "child_masks": 2,
              "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 24}),
 }
