@@ -569,7 +569,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dna")
     ap.add_argument("--traffic", type=float, default=None,
-                    help="dram bytes per scan launch from an ncu capture of this build")
+                    help="dram bytes per scan launch from an ncu capture of the current kernel sources")
     ap.add_argument("--ref-sample-mib", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="1: entries via L2, 2: entries in smem")
