@@ -501,6 +501,7 @@ def run_serving(args):
     each level runs 10 s of arrivals or 10,000 batches, whichever is fewer.
     Reports p50/p99 latency (completion minus scheduled arrival) and the
     sustained throughput per load level, one JSON line per level."""
+    import gc
     import threading
     import torch
     import paper_1704_02272_gb300 as pfac
@@ -524,6 +525,10 @@ def run_serving(args):
             srv.wait(rid, 60)
             srv.release(rid)
         for load in loads:
+            # the load generator's own garbage collection would stall both of
+            # its threads mid-level: collect between levels, not during them
+            gc.collect()
+            gc.disable()
             rate = load * 1e9 / 8.0 / mean_bytes  # batches per second
             n = int(min(max(args.serve_min, rate * args.serve_seconds), args.serve_max))
             arr = workloads.poisson_arrivals(np.random.RandomState(int(load)), rate, n)
@@ -557,6 +562,7 @@ def run_serving(args):
                 assert r["status"] == 0
                 lat.append(r["t_done"] - at)
                 srv.release(rid)
+            gc.enable()
             t_end = max(done[i]["t_done"] for i in ids)
             line = {"impl": "ours", "mode": "serving", "offered_gbps": load,
                     "sustained_gbps": round(8.0 * sum(sizes) / (t_end - start) / 1e9, 3),
