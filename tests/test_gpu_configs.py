@@ -7,7 +7,8 @@ launch configuration the benchmark times.
 * sweep cells (512 MiB each, up to 1.2e9 matches): the compressed and
   uncompressed kernels agree on the whole list, and both agree with the
   oracle on sampled 1 MiB windows (start, end and random offsets), which the
-  oracle computes one window at a time.
+  oracle computes one window at a time.  Every cell is also compared with the
+  oracle over the whole input, 32 MiB of start positions at a time.
 """
 import numpy as np
 import pytest
@@ -106,6 +107,23 @@ def test_sweep_cell(sigma, n):
         ref = oracle_keys(w, lo=a, hi=a + win, ac=ac)
         assert_same(window(kc, a, a + win), ref, f"{w.name} window {a}")
     ac.close()
+
+
+@pytest.mark.parametrize("sigma,n", SWEEP, ids=[f"sig{s}-n{n}" for s, n in SWEEP])
+def test_sweep_cell_whole_list(sigma, n):
+    # every key of the cell against the oracle, chunk by chunk (the oracle's
+    # keys of one chunk at a time fit in host memory)
+    w = workloads.config4(sigma, n)
+    text, seg = to_device(w)
+    kc = device_keys(w, text, seg, pfac.LAYOUT_COMPRESSED)
+    ac = oracle.ACOracle(w.patterns)
+    chunk, total = 32 << 20, 0
+    for a in range(0, w.n_bytes, chunk):
+        ref = oracle_keys(w, lo=a, hi=min(a + chunk, w.n_bytes), ac=ac)
+        assert_same(window(kc, a, a + chunk), ref, f"{w.name} chunk at {a}")
+        total += ref.shape[0]
+    ac.close()
+    assert total == kc.numel()
 
 
 GRAM_CELLS = [("ids", 0, 0), ("sweep", 256, 10000), ("sweep", 256, 100000), ("sweep", 20, 100000),
