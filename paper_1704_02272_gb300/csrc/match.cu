@@ -384,6 +384,9 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
             return set_error(PFAC_EINVAL, "pfac_match: bitmap_copies %u is not 1, 2, 4, .., 32",
                              copies);
     }
+    if (pbytes == 2 && copies > 1)
+        return set_error(PFAC_EINVAL, "pfac_match: prefix bytes take one bitmap copy (%u asked)",
+                         copies);
     if (var != 0 && var != VAR_F && var != VAR_FE)
         return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
 

@@ -1,0 +1,81 @@
+"""Host logic of the scan planner (pfac_match_plan, no GPU needed): over a
+grid of tables and every combination of the tuning options, a plan either
+fits the 232,448-byte shared-memory limit of an sm_103a CTA and honours every
+option the caller fixed, or the call fails cleanly with PFAC_EINVAL."""
+import itertools
+
+import pytest
+
+import workloads
+
+pfac = pytest.importorskip("paper_1704_02272_gb300")
+
+SMEM_LIMIT = 232448
+EINVAL = -1
+GRID = [(s, n) for s in (4, 20, 64, 256) for n in (100, 1000, 10000)]
+
+
+def host_table(sigma, n):
+    w = workloads.config4(sigma, n, n_bytes=1 << 12)
+    return pfac.Table(w.patterns, w.sigma, host_only=True)
+
+
+def held_depths(t):
+    ks = []
+    for k in range(1, 21):
+        try:
+            pfac.plan(t, prefix_depth=k)
+            ks.append(k)
+        except pfac.PfacError as e:
+            assert e.status == EINVAL
+    return ks
+
+
+@pytest.mark.parametrize("sigma,n", GRID, ids=[f"sig{s}-n{n}" for s, n in GRID])
+def test_plans_fit_and_honour_options(sigma, n):
+    with host_table(sigma, n) as t:
+        info = t.info()
+        ks = held_depths(t)
+        assert ks and ks == list(range(ks[0], ks[-1] + 1)) and len(ks) <= 3
+        assert info["prefix_depth"] in ks
+        default = pfac.plan(t)
+        assert default["smem_bytes"] <= SMEM_LIMIT
+        n_ok = 0
+        for k, var, masks, gram, pbytes, nw, copies in itertools.product(
+                ks, (0, 1, 2), (0, 1, 2), (0, 1, 2), (0, 1, 2), (0, 16, 24), (0, 1, 2, 32)):
+            opt = dict(prefix_depth=k, variant=var, child_masks=masks, gram_filter=gram,
+                       prefix_bytes=pbytes, warps_per_cta=nw, bitmap_copies=copies)
+            try:
+                p = pfac.plan(t, **opt)
+            except pfac.PfacError as e:
+                assert e.status == EINVAL, opt
+                continue
+            n_ok += 1
+            assert p["smem_bytes"] <= SMEM_LIMIT, (opt, p)
+            assert p["prefix_depth"] == k
+            if var:
+                assert p["variant"] == var
+            assert p["warps_per_cta"] == (nw or 16)  # an untuned table defaults to 16
+            if masks:
+                assert p["child_masks"] == masks, (opt, p)
+            if gram:
+                assert p["gram_filter"] == gram, (opt, p)
+            if pbytes:
+                assert p["prefix_bytes"] == pbytes, (opt, p)
+            assert not (p["gram_filter"] == 2 and p["prefix_bytes"] == 2)
+            if copies:
+                assert p["bitmap_copies"] == copies, (opt, p)
+            if p["gram_filter"] == 2:
+                assert info["gram_len"] > 0 and 10 <= p["gram_bits"] <= info["gram_bits"]
+        assert n_ok > 0
+
+
+def test_invalid_options_rejected():
+    with host_table(256, 1000) as t:
+        for opt in (dict(warps_per_cta=20), dict(child_masks=3), dict(gram_filter=3),
+                    dict(prefix_bytes=3), dict(bitmap_copies=3), dict(variant=7),
+                    dict(prefix_bytes=2, gram_filter=2), dict(prefix_bytes=2, bitmap_copies=2),
+                    dict(prefix_depth=21)):
+            with pytest.raises(pfac.PfacError) as e:
+                pfac.plan(t, **opt)
+            assert e.value.status == EINVAL, opt
