@@ -175,7 +175,9 @@ int pfac_build(const uint8_t *const *patterns, const uint32_t *lengths, uint32_t
 
 /*
  * pfac_workspace_bytes - device scratch needed by pfac_match_async for an
- * input of n_bytes split into n_segments segments.  Writes *bytes.
+ * input of n_bytes split into n_segments segments.  Writes *bytes.  No
+ * device work.  PFAC_EINVAL for n_bytes >= 2^40 (positions take 40 bits of
+ * a key) or options no plan satisfies (as pfac_match).
  */
 int pfac_workspace_bytes(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments,
                          const pfac_match_opts *opts, uint64_t *bytes);

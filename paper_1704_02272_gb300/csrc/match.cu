@@ -579,6 +579,9 @@ using namespace pfac;
 extern "C" int pfac_workspace_bytes(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments,
                                     const pfac_match_opts *opts, uint64_t *bytes) {
     if (!t || !bytes) return set_error(PFAC_EINVAL, "pfac_workspace_bytes: NULL argument");
+    if (n_bytes >> (64 - PFAC_ID_BITS))
+        return set_error(PFAC_EINVAL, "pfac_workspace_bytes: input longer than 2^%d bytes",
+                         64 - PFAC_ID_BITS);
     Plan pl;
     const int rc = make_plan(t, opts, &pl);
     if (rc) return rc;

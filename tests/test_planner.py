@@ -79,3 +79,17 @@ def test_invalid_options_rejected():
             with pytest.raises(pfac.PfacError) as e:
                 pfac.plan(t, **opt)
             assert e.value.status == EINVAL, opt
+
+
+def test_workspace_grows_with_the_input_and_stops_at_2_40():
+    with host_table(256, 1000) as t:
+        sizes = [0, 1, 511, 512, 513, 1 << 20, 1 << 30, (1 << 40) - 1]
+        for S in (1, 2, 1000):
+            ws = [pfac.workspace_bytes(t, n, S) for n in sizes]
+            assert all(a <= b for a, b in zip(ws, ws[1:])), (S, ws)
+            assert all(w % 256 == 0 for w in ws)
+        assert pfac.workspace_bytes(t, 1 << 20, 1000) >= pfac.workspace_bytes(t, 1 << 20, 1)
+        for n in (1 << 40, 1 << 41):
+            with pytest.raises(pfac.PfacError) as e:
+                pfac.workspace_bytes(t, n, 1)
+            assert e.value.status == EINVAL
