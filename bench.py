@@ -214,8 +214,9 @@ def dist_setup(n_gpus):
 
 
 def run_reference(args):
-    rank, world, _ = dist_setup(args.gpus)
-    if rank != 0:
+    # the CPU oracle runs on rank 0 alone; the other ranks leave without
+    # work (no process group: nothing is exchanged)
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     w = load_workload(args.workload, 0)
     import oracle
