@@ -98,8 +98,17 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
             res.gram_filter = gf;
             res.scan_ms = ms;
             res.from_cache = 1;
-            if (out) *out = res;
-            return PFAC_OK;
+            // a cached choice that no longer makes a plan (an edited or
+            // foreign cache line) is dropped and the table tuned afresh
+            pfac_plan_info pi;
+            const bool sane = (nw == 16 || nw == 24) && v <= 2 && mk <= 2 && gf <= 2 &&
+                              pb <= 2 && c <= 32 && (c & (c - 1)) == 0;
+            if (sane && pfac_match_plan(t, nullptr, &pi) == PFAC_OK) {
+                if (out) *out = res;
+                return PFAC_OK;
+            }
+            clear_error();
+            memset(&res, 0, sizeof res);
         }
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
