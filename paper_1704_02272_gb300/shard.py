@@ -65,6 +65,10 @@ def match_shard_gpu(table, text_dev, shard: Shard, **opt):
     every reported position, so the keys need no filtering."""
     import torch
 
+    if shard.stop <= shard.start:
+        # an empty share (inputs shorter than the ranks' alignment): no call,
+        # since starts_end = 0 would mean every position of the halo
+        return torch.empty(0, dtype=torch.int64, device=text_dev.device)
     from . import binding
     seg = torch.from_numpy(shard.seg.astype(np.int64)).to(text_dev.device)
     return binding.match(table, text_dev[shard.start:shard.read_end], seg,

@@ -76,3 +76,18 @@ def test_plan_halo_and_segments():
     assert plan[0].read_end == 1280 + 49 and plan[2].read_end == 4000
     assert plan[0].seg.tolist() == [0, 10, 10, 700, 1000, 1329]
     assert plan[1].seg.tolist() == [0, 2560 + 49 - 1280]
+
+
+def test_tiny_input_leaves_empty_shares_that_start_no_walk():
+    # 1000 bytes over 8 ranks: the 256-byte alignment leaves some shares
+    # empty; the shares still tile the input and an empty one yields nothing
+    seg = np.array([0, 1000], dtype=np.uint64)
+    plan = shard.plan(1000, seg, 8, 50)
+    assert plan[0].start == 0 and plan[-1].stop == 1000
+    assert all(plan[i].stop == plan[i + 1].start for i in range(7))
+    empty = [p for p in plan if p.stop == p.start]
+    assert empty
+    text = torch.zeros(1000, dtype=torch.uint8)
+    for p in empty:
+        assert shard.match_shard_gpu(None, text, p).numel() == 0
+        assert shard.own(np.array([0, 5 << 24], dtype=np.uint64), p).size == 0
