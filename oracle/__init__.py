@@ -11,7 +11,9 @@ Contents
 ``pyref``         the same definition as a tiny pure-Python loop for
                   exhaustive small cases.
 ``trie``          the paper's storage model (Section 3.1) and node-count
-                  closed forms (Eq. 1, Eq. 2), used to pin table statistics.
+                  closed forms (Eq. 1, Eq. 2), used to pin table statistics;
+                  reduction step 2 (Section 3.2) as a DAG with an id side
+                  channel, and a walker over it.
 
 The result all matchers compute: distinct non-empty patterns P_j, text T and
 segment offsets o_0 = 0 <= ... <= o_S = N; the sorted list of (p, j) with

@@ -151,3 +151,123 @@ def paper_layout_bytes(q: int, sigma: int) -> int:
 def dense_stt_bytes(q: int, sigma: int) -> int:
     """One 4-byte next state per (node, symbol)."""
     return q * 4 * sigma
+
+
+# --------------------------------------------------------------------------
+# Section 3.2, step 2: merging the last levels of the trie
+# --------------------------------------------------------------------------
+#
+# Reading: a node's subtree is "in the last three levels" when it is at most
+# three levels tall (height 0 = a leaf, height <= 2).  Two such nodes merge
+# when their subtrees are equal: same finality and the same children on the
+# same symbols, the children compared after merging (bottom up).  With
+# ``levels = 1`` only leaves merge, which is step 1 (Eq. 2).  The merged
+# structure is a DAG; a merged final node stands for several patterns, so it
+# no longer names one: a walk reports (start, length) and the id comes from
+# a side channel keyed by the matched bytes (one table per pattern length).
+#
+# Node counts follow the paper's accounting (nodes x bytes per node).  Shared
+# children are not contiguous for every parent, so the Eq. 1 layout would need
+# an indirection for them; the counts ignore that, as the paper does.
+
+
+@dataclass
+class DagTrie:
+    sigma: int
+    children: list    # per node: dict symbol -> node
+    final: list       # per node: bool
+
+    @property
+    def n_nodes(self) -> int:
+        return len(self.children)
+
+
+def heights(trie: PaperTrie) -> list:
+    """Height of every node (0 for a leaf), children before parents: nodes
+    are numbered breadth-first, so a reverse scan sees children first."""
+    h = [0] * trie.n_nodes
+    for v in range(trie.n_nodes - 1, -1, -1):
+        bm, o = trie.bitmap[v], trie.offset[v]
+        k = bin(bm).count("1")
+        if k:
+            h[v] = 1 + max(h[o + i] for i in range(k))
+    return h
+
+
+def suffix_merge(trie: PaperTrie, levels: int = 3) -> DagTrie:
+    """Merge equal subtrees at most ``levels`` levels tall (Section 3.2)."""
+    h = heights(trie)
+    n = trie.n_nodes
+    new_id = [-1] * n
+    sig_to_id = {}
+    children, final = [], []
+
+    def kids(v):
+        bm, o = trie.bitmap[v], trie.offset[v]
+        syms = [c for c in range(trie.sigma) if (bm >> c) & 1]
+        return [(c, o + i) for i, c in enumerate(syms)]
+
+    # bottom up: a node's children get their ids first
+    for v in sorted(range(n), key=lambda x: h[x]):
+        ks = tuple((c, new_id[u]) for c, u in kids(v))
+        fin = trie.final_id[v] >= 0
+        if h[v] < levels and v != 0:
+            key = (fin, ks)
+            if key in sig_to_id:
+                new_id[v] = sig_to_id[key]
+                continue
+            sig_to_id[key] = len(children)
+        new_id[v] = len(children)
+        children.append(dict(ks))
+        final.append(fin)
+    # the root first, as in the breadth-first array
+    root = new_id[0]
+    order = [root] + [i for i in range(len(children)) if i != root]
+    pos = {old: i for i, old in enumerate(order)}
+    return DagTrie(trie.sigma, [{c: pos[u] for c, u in children[old].items()} for old in order],
+                   [final[old] for old in order])
+
+
+def dag_strings(dag: DagTrie) -> set:
+    """Every string the DAG accepts (paths from the root to a final node)."""
+    out = set()
+    stack = [(0, b"")]
+    while stack:
+        v, s = stack.pop()
+        if dag.final[v] and s:
+            out.add(s)
+        for c, u in dag.children[v].items():
+            stack.append((u, s + bytes([c])))
+    return out
+
+
+def side_channel(patterns) -> dict:
+    """Pattern id by length and bytes: the id a merged final node cannot
+    hold."""
+    t = {}
+    for j, p in enumerate(patterns):
+        t.setdefault(len(p), {})[bytes(p)] = j
+    return t
+
+
+def dag_walk_matches(dag: DagTrie, side: dict, text, seg_offsets):
+    """Failure-less matching over the merged DAG: a walk from the root at
+    every start position; a final node reached after L symbols reports the
+    pattern the side channel names for the L matched bytes."""
+    text = bytes(text)
+    seg = [int(x) for x in seg_offsets]
+    out = []
+    for k in range(len(seg) - 1):
+        a, b = seg[k], seg[k + 1]
+        for p in range(a, b):
+            v, q = 0, p
+            while q < b:
+                nxt = dag.children[v].get(text[q])
+                if nxt is None:
+                    break
+                v = nxt
+                q += 1
+                if dag.final[v]:
+                    out.append((p, side[q - p][text[p:q]]))
+    out.sort()
+    return out
