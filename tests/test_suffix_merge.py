@@ -92,3 +92,24 @@ def test_last_levels_collapse_to_at_most_1_plus_sigma_plus_sigma_squared():
     h = T.heights(t)
     tall = sum(1 for v in range(t.n_nodes) if h[v] >= 3 or v == 0)
     assert T.suffix_merge(t, 3).n_nodes - tall == 1 + 4 + 16
+
+
+@pytest.mark.parametrize("sigma,n", [(4, 20), (4, 60), (52, 1000)])
+def test_distinct_two_symbol_chains_follow_the_occupancy_law(sigma, n):
+    # Section 3.2's expected-reduction model counts the r = sigma^2 chains of
+    # two symbols before the final node (Eq. 3; Eq. 4 is garbled).  For
+    # random patterns the merged height-2 subtrees are the distinct last two
+    # symbols, whose expected count is the occupancy law r(1 - (1 - 1/r)^n).
+    r = sigma * sigma
+    expect = r * (1.0 - (1.0 - 1.0 / r) ** n)
+    counts = []
+    for seed in range(30):
+        pats = workloads.uniform_patterns(np.random.RandomState(seed), n, sigma, 20, 20)
+        t = T.build_paper_trie(pats, sigma)
+        h = T.heights(t)
+        counts.append(len({serial(t, v) for v in range(1, t.n_nodes) if h[v] == 2}))
+        # every pattern's chain is single below depth 17, so the height-2
+        # subtrees are exactly its last two symbols
+        assert counts[-1] == len({p[-2:] for p in pats})
+    mean, se = np.mean(counts), np.std(counts) / np.sqrt(len(counts))
+    assert abs(mean - expect) < 4 * se + 0.01 * expect, (mean, expect, se)
