@@ -338,6 +338,14 @@ def match_into(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.T
                stream=None, **opt) -> int:
     """pfac_match: writes min(count, capacity) sorted keys into ``out`` and
     returns the total count (PfacError PFAC_ENOSPC when it does not fit)."""
+    if text.device.type != "cuda":
+        raise ValueError("match takes the text on a CUDA device (match_host takes host buffers)")
+    for x, name, dt in ((text, "text", torch.uint8), (seg, "segment offsets", torch.int64),
+                        (out, "output", torch.int64)):
+        if x is None and name == "output":
+            continue
+        if x.dtype != dt or not x.is_contiguous() or x.device != text.device:
+            raise ValueError(f"match: {name} must be a contiguous {dt} tensor on {text.device}")
     o = _opts(**opt)
     n = ctypes.c_uint64()
     n_seg = max(seg.numel() - 1, 0)

@@ -172,3 +172,14 @@ def test_truncated_trie_counts(seed, sigma, n, lo, hi, d):
     assert info["trie_nodes"] == trie.prefix_set_count(cut)
     assert info["output_lists"] == len(set(cut))
     assert info["n_patterns"] == len(w.patterns)
+
+
+def test_match_checks_its_tensors_before_the_library():
+    import torch
+    with host_table([b"ab"], 256) as t:
+        z = torch.zeros(16, dtype=torch.uint8)
+        s = torch.tensor([0, 16], dtype=torch.int64)
+        with pytest.raises(ValueError):
+            pfac.match(t, z, s)  # host text: the device path needs device memory
+        with pytest.raises(ValueError):
+            pfac.match_into(t, z, s.to(torch.int32), torch.zeros(4, dtype=torch.int64))
