@@ -29,6 +29,12 @@
  * on which its device work is ordered.  The table is owned by the library
  * from pfac_build until pfac_table_free.  Calls on one table may run
  * concurrently on different streams as long as each uses its own workspace.
+ * A table lives on the device that was current when it was built: every
+ * call that launches work on it (matching, verification, autotuning,
+ * serving) must be made with that device current and, when a stream is
+ * given, a stream of that device; otherwise it returns PFAC_EINVAL before
+ * any device work.  (While a stream captures a CUDA graph its device cannot
+ * be queried, so then only the current device is checked.)
  *
  * Errors.  Every int-returning call returns a pfac_status; 0 is success.  A
  * failing call leaves its outputs unspecified (except PFAC_ENOSPC, below),
@@ -130,6 +136,19 @@ typedef struct {
     uint64_t position_base; /* added to every reported position (a shard's
                               or chunk's global offset); position_base +
                               n_bytes must stay below 2^40 */
+    void *ev_emit_begin;   /* optional cudaEvent_t recorded right before the
+                              scan kernel's second (emit) launch, which
+                              re-scans the slices whose matches did not fit
+                              their record space, for profiling */
+    void *ev_emit_end;     /* optional cudaEvent_t recorded right after it */
+    uint32_t scan_kernel;  /* which scan kernel runs the first stages (compressed
+                              layout): 0 = library choice (or the autotuner's),
+                              1 = queued kernel (input staged in shared memory
+                              by bulk copies), 2 = register-staged kernel
+                              (input read into registers; alphabets of 129 to
+                              256 symbols; excludes prefix_bytes = 2 and
+                              warps_per_cta) */
+    uint32_t reserved_scan;
 } pfac_match_opts;
 
 typedef struct {
@@ -197,7 +216,7 @@ typedef struct {
     uint32_t smem_bytes;     /* dynamic shared memory per CTA of the scan kernel */
     uint32_t prefix_bytes;   /* 1 = off, 2 = on */
     uint32_t warps_per_cta;  /* warps per CTA of the scan kernel (0: uncompressed) */
-    uint32_t reserved;
+    uint32_t scan_kernel;    /* 1 = queued, 2 = register-staged (0: uncompressed) */
 } pfac_plan_info;
 int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts, pfac_plan_info *out);
 
@@ -323,7 +342,10 @@ void pfac_match_host_release(void);
  *     device work;
  *   - the first call on a device looks up that device's copy of the array
  *     (cudaGetSymbolAddress, with the device current); make that first call
- *     before any stream capture;
+ *     before any stream capture.  The address is kept per device and per
+ *     CUDA context: after the device's context is replaced (for example by
+ *     cudaDeviceReset) the next call looks it up again, so that call too
+ *     belongs before any capture;
  *   - all calls on a device share the one array, and it keeps the previous
  *     call's contents (each call clears what must start at zero), so calls
  *     whose device work overlaps in time race and give wrong results: issue
@@ -358,6 +380,7 @@ typedef struct {
     uint32_t gram_filter; /* 1 = off, 2 = on */
     uint32_t prefix_bytes; /* 1 = off, 2 = on */
     uint32_t warps_per_cta;
+    uint32_t scan_kernel;  /* 1 = queued, 2 = register-staged */
 } pfac_tune_result;
 
 int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,

@@ -49,7 +49,9 @@ class MatchOpts(ctypes.Structure):
                 ("ev_scan_begin", ctypes.c_void_p), ("ev_scan_end", ctypes.c_void_p),
                 ("child_masks", ctypes.c_uint32), ("gram_filter", ctypes.c_uint32),
                 ("prefix_bytes", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
-                ("starts_end", ctypes.c_uint64), ("position_base", ctypes.c_uint64)]
+                ("starts_end", ctypes.c_uint64), ("position_base", ctypes.c_uint64),
+                ("ev_emit_begin", ctypes.c_void_p), ("ev_emit_end", ctypes.c_void_p),
+                ("scan_kernel", ctypes.c_uint32), ("reserved_scan", ctypes.c_uint32)]
 
 
 class TableInfo(ctypes.Structure):
@@ -70,7 +72,8 @@ class TuneResult(ctypes.Structure):
                 ("n_tried", ctypes.c_uint32),
                 ("scan_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
                 ("from_cache", ctypes.c_int), ("gram_filter", ctypes.c_uint32),
-                ("prefix_bytes", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32)]
+                ("prefix_bytes", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
+                ("scan_kernel", ctypes.c_uint32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -78,7 +81,7 @@ class PlanInfo(ctypes.Structure):
                 ("bitmap_copies", ctypes.c_uint32), ("child_masks", ctypes.c_uint32),
                 ("gram_filter", ctypes.c_uint32), ("gram_bits", ctypes.c_uint32),
                 ("smem_bytes", ctypes.c_uint32), ("prefix_bytes", ctypes.c_uint32),
-                ("warps_per_cta", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("warps_per_cta", ctypes.c_uint32), ("scan_kernel", ctypes.c_uint32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -171,17 +174,23 @@ def _stream(stream) -> int:
     return int(stream)
 
 
+KERNEL_QUEUED, KERNEL_REGISTER = 1, 2
+
+
 def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,
           gram_filter=0, prefix_bytes=0, starts_end=0, position_base=0, warps_per_cta=0,
-          scan_events=None):
+          scan_kernel=0, scan_events=None, emit_events=None):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
     o.bitmap_copies, o.child_masks, o.gram_filter = bitmap_copies, child_masks, gram_filter
     o.prefix_bytes, o.starts_end, o.position_base = prefix_bytes, starts_end, position_base
-    o.warps_per_cta = warps_per_cta
+    o.warps_per_cta, o.scan_kernel = warps_per_cta, scan_kernel
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event
+    if emit_events is not None:  # around the scan kernel's emit launch
+        o.ev_emit_begin = emit_events[0].cuda_event
+        o.ev_emit_end = emit_events[1].cuda_event
     return o
 
 
@@ -267,7 +276,7 @@ def plan(table: Table, **opt) -> dict:
     o = _opts(**opt)
     r = PlanInfo()
     _check(LIB.pfac_match_plan(table.handle, ctypes.byref(o), ctypes.byref(r)))
-    return {f: getattr(r, f) for f, _ in PlanInfo._fields_ if f != "reserved"}
+    return {f: getattr(r, f) for f, _ in PlanInfo._fields_}
 
 
 def match_host(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,
@@ -311,27 +320,55 @@ def verify(table: Table, text: torch.Tensor, seg: torch.Tensor, cand: torch.Tens
     return out[:int(cnt.item())]
 
 
+def _check_device_args(who: str, text: torch.Tensor, args) -> None:
+    """Every tensor handed to the library as a raw pointer must have the dtype
+    and layout the C ABI reads it with, on the text's CUDA device; otherwise
+    the kernels would read or write past a smaller buffer."""
+    for x, name, dt, optional in args:
+        if x is None and optional:
+            continue
+        if x is None or x.dtype != dt or not x.is_contiguous():
+            raise ValueError(f"{who}: {name} must be a contiguous {dt} tensor")
+    if text.device.type != "cuda":
+        raise ValueError(f"{who} takes the text on a CUDA device")
+    for x, name, _, _ in args:
+        if x is not None and x.device != text.device:
+            raise ValueError(f"{who}: {name} must be on {text.device}, like the text")
+
+
 def match_async(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,
                 count: torch.Tensor, status: torch.Tensor, workspace: torch.Tensor,
                 stream=None, **opt):
     """pfac_match_async: everything stays on the device (graph-capturable)."""
+    _check_device_args("match_async", text, (
+        (text, "text", torch.uint8, False), (seg, "segment offsets", torch.int64, False),
+        (out, "output", torch.int64, True), (count, "count", torch.int64, False),
+        (status, "status", torch.int32, True), (workspace, "workspace", torch.uint8, False)))
     o = _opts(**opt)
     n_seg = max(seg.numel() - 1, 0)
-    _check(LIB.pfac_match_async(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg,
-                                _ptr(out), out.numel() if out is not None else 0, _ptr(count),
-                                _ptr(status), _ptr(workspace), workspace.numel(),
-                                ctypes.byref(o), ctypes.c_void_p(_stream(stream))))
+    with torch.cuda.device(text.device):
+        _check(LIB.pfac_match_async(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg,
+                                    _ptr(out), out.numel() if out is not None else 0,
+                                    _ptr(count), _ptr(status), _ptr(workspace),
+                                    workspace.numel(), ctypes.byref(o),
+                                    ctypes.c_void_p(_stream(stream))))
 
 
 def match_noalloc(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,
                   count: torch.Tensor, status: torch.Tensor, stream=None, **opt):
     """pfac_match_noalloc: like match_async, but the library uses its built-in
     scratch array instead of a workspace, so nothing is allocated."""
+    _check_device_args("match_noalloc", text, (
+        (text, "text", torch.uint8, False), (seg, "segment offsets", torch.int64, False),
+        (out, "output", torch.int64, True), (count, "count", torch.int64, False),
+        (status, "status", torch.int32, True)))
     o = _opts(**opt)
     n_seg = max(seg.numel() - 1, 0)
-    _check(LIB.pfac_match_noalloc(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg,
-                                  _ptr(out), out.numel() if out is not None else 0, _ptr(count),
-                                  _ptr(status), ctypes.byref(o), ctypes.c_void_p(_stream(stream))))
+    with torch.cuda.device(text.device):
+        _check(LIB.pfac_match_noalloc(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg,
+                                      _ptr(out), out.numel() if out is not None else 0,
+                                      _ptr(count), _ptr(status), ctypes.byref(o),
+                                      ctypes.c_void_p(_stream(stream))))
 
 
 def match_into(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,
@@ -349,9 +386,10 @@ def match_into(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.T
     o = _opts(**opt)
     n = ctypes.c_uint64()
     n_seg = max(seg.numel() - 1, 0)
-    rc = LIB.pfac_match(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg, _ptr(out),
-                        out.numel() if out is not None else 0, ctypes.byref(n), ctypes.byref(o),
-                        ctypes.c_void_p(_stream(stream)))
+    with torch.cuda.device(text.device):
+        rc = LIB.pfac_match(table.handle, _ptr(text), text.numel(), _ptr(seg), n_seg, _ptr(out),
+                            out.numel() if out is not None else 0, ctypes.byref(n),
+                            ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     if rc == -5:
         err = PfacError(rc, f"{n.value} matches exceed capacity {out.numel()}")
         err.count = n.value

@@ -138,6 +138,10 @@ extern "C" int pfac_match_host(const pfac_table *t, const uint8_t *h_input, uint
     if (!t || !n_out || (n_bytes && !h_input) || !h_seg)
         return set_error(PFAC_EINVAL, "pfac_match_host: NULL argument");
     if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_match_host: table was built host-only");
+    {
+        const int drc = check_table_device(t, cuda_stream, "pfac_match_host");
+        if (drc) return drc;
+    }
     if (out_capacity && !h_out_keys) return set_error(PFAC_EINVAL, "pfac_match_host: NULL output");
     if (opts && (opts->starts_end || opts->position_base))
         return set_error(PFAC_EINVAL, "pfac_match_host: starts_end and position_base are set "

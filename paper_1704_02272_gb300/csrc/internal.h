@@ -23,11 +23,18 @@ struct pfac_table {
     uint32_t tuned_gram = 0;
     uint32_t tuned_bytes = 0;
     uint32_t tuned_nw = 0;
+    uint32_t tuned_kernel = 0;
 };
 
 namespace pfac {
 
 int set_error(int status, const char *fmt, ...);
 void clear_error();
+
+// PFAC_OK when the current device and, for a non-NULL stream, the stream's
+// device are the device the table was uploaded to; otherwise PFAC_EINVAL
+// (with a message naming `who`), so that no kernel is launched on one GPU
+// with another GPU's pointers.
+int check_table_device(const pfac_table *t, void *cuda_stream, const char *who);
 
 }  // namespace pfac

@@ -519,11 +519,19 @@ __device__ __forceinline__ bool mask_keep(const MatchParams &P, uint32_t x, uint
 // for each matched survivor, ranked among its slice's matched survivors (the
 // slice's entries are contiguous in the queue and resolve in one batch).
 // The last entry of each slice publishes the slice's record count; slices
-// with more matches than their record space go to the emit pass.
+// with more matches than their record space (P.unit_cap) go to the emit pass.
+//
+// A slice may also span batches (a kernel that resolves a slice with more
+// survivors than its queue holds in queue-sized chunks): the entries of
+// slice `carry_unit` then rank after the `carry` records of its earlier
+// batches, and when the batch's last entry is not its slice's last, that
+// slice and its records so far are returned in carry_unit / carry for the
+// next batch (carry_unit = UNIT_OVF when no slice continues).
 template <int W, int VAR>
-__device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, uint32_t n,
-                                              const uint32_t *Fs, const uint32_t *Cs,
-                                              const uint32_t *Es, uint32_t lane) {
+__device__ __forceinline__ void flush_records_c(const MatchParams &P, QEntry *q, uint32_t n,
+                                                const uint32_t *Fs, const uint32_t *Cs,
+                                                const uint32_t *Es, uint32_t lane,
+                                                uint32_t &carry_unit, uint32_t &carry) {
     if (n == 0) return;
     resolve_batch<W, VAR>(P, q, n, Fs, Cs, Es, lane);
     uint32_t fin[QU], pos[QU], unit[QU];
@@ -541,18 +549,20 @@ __device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, u
     }
     __syncwarp();
     // exclusive count of matched entries before each entry of the batch
-    uint32_t pre[QU], carry = 0;
+    uint32_t pre[QU], carry_in = 0;
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int u = 0; u < QU; u++) {
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, fin[u] != 0);
-        pre[u] = carry + __popc(b & lt);
-        carry += __popc(b);
+        pre[u] = carry_in + __popc(b & lt);
+        carry_in += __popc(b);
     }
 #pragma unroll
     for (int u = 0; u < QU; u++)
         if (unit[u] != 0xFFFFFFFFu) q[lane + 32u * u].x = pre[u];
     __syncwarp();
+    const uint32_t cap = P.unit_cap;
+    uint32_t cu = UNIT_OVF, cc = 0;
 #pragma unroll
     for (int u = 0; u < QU; u++) {
         if (unit[u] == 0xFFFFFFFFu) continue;
@@ -560,24 +570,37 @@ __device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, u
         const uint32_t p = pos[u] & 0x3FFu, slot = (pos[u] >> 10) & 0xFFu;
         const bool last = (pos[u] & LAST_FLAG) != 0;
         const uint32_t base = q[e - slot].x;
-        const uint32_t rank = pre[u] - base;
+        const uint32_t rank = pre[u] - base + (unit[u] == carry_unit ? carry : 0u);
         if (fin[u]) {
-            if (rank < (uint32_t)SCAP)
-                P.recs[(size_t)unit[u] * SCAP + rank] = ((uint64_t)p << 32) | fin[u];
+            if (rank < cap)
+                P.recs[(size_t)unit[u] * cap + rank] = ((uint64_t)p << 32) | fin[u];
             atomicAdd((unsigned long long *)(P.tile_k + unit[u]),
                       (unsigned long long)fin_len(P.T.pool, fin[u]));
         }
+        const uint32_t m = rank + (fin[u] ? 1u : 0u);
         if (last) {
-            const uint32_t m = rank + (fin[u] ? 1u : 0u);
-            if (m > (uint32_t)SCAP) {
+            if (m > cap) {
                 P.tile_m[unit[u]] = UNIT_OVF;
                 P.ovf_list[atomicAdd(&P.hdr->ovf_count, 1u)] = unit[u];
             } else {
                 P.tile_m[unit[u]] = m;
             }
+        } else if (e == n - 1) {
+            cu = unit[u];
+            cc = m;
         }
     }
+    carry_unit = __shfl_sync(0xFFFFFFFFu, cu, (n - 1) & 31u);
+    carry = __shfl_sync(0xFFFFFFFFu, cc, (n - 1) & 31u);
     __syncwarp();
+}
+
+template <int W, int VAR>
+__device__ __forceinline__ void flush_records(const MatchParams &P, QEntry *q, uint32_t n,
+                                              const uint32_t *Fs, const uint32_t *Cs,
+                                              const uint32_t *Es, uint32_t lane) {
+    uint32_t cu = UNIT_OVF, cc = 0;
+    flush_records_c<W, VAR>(P, q, n, Fs, Cs, Es, lane, cu, cc);
 }
 
 // Appends the candidates of the lanes set in `lanes` to the queue after the

@@ -1,0 +1,434 @@
+// Register-staged scan kernel for 8-bit symbols (alphabets of 129 to 256
+// symbols): the walk of Section 2.3 over the compressed records of Section
+// 3.1, with the input read from HBM straight into registers.
+//
+// * Work unit: the 512-byte slice of the queued kernel (same records, key
+//   counts and ordering kernels).  A warp takes two consecutive slices per
+//   step (pair g = slices 2g and 2g + 1, pairs dealt round-robin over the
+//   grid's warps).  Lane l holds bytes 16l .. 16l + 15 of each slice in four
+//   registers: one coalesced 16-byte load per lane and slice, issued one step
+//   ahead, the pairs further ahead prefetched into L2 by one bulk prefetch.
+//   The four bytes after a lane's sixteen come from lane l + 1 by a shuffle;
+//   for lane 31 of the first slice from lane 0 of the second, for lane 31 of
+//   the second from a 4-byte load of the next pair's head.
+// * First stage: each of the lane's 16 positions tests its k-symbol prefix
+//   index (or, with the gram filter, its hashed g-symbol string) against a
+//   bitmap in shared memory held in 2^REP copies interleaved word by word:
+//   lane l reads copy l mod 2^REP, so a warp's 32 random lookups meet fewer
+//   bank conflicts.  Per position: one funnel shift forms the index (none at
+//   every fourth position), one and-or gives the word address (plus a
+//   multiply and a shift for the gram hash), one rotate and one funnel shift
+//   move the tested bit into the lane's survivor mask.
+// * Second stage, for each candidate (a few per slice), from the registers:
+//   the exact prefix bit after the gram filter, the rank of the prefix index
+//   (Eq. 1 on the collapsed prefix level) and the child mask of its entry
+//   tested with the next symbol; what passes, and positions whose window
+//   leaves their segment (walks from the root), join the warp's queue.
+// * The queue is resolved in batches through L2 as in the queued kernel (the
+//   same resolver and record flush).  A slice with more queue entries than
+//   the queue holds is resolved in queue-sized chunks, its record ranks
+//   carried from chunk to chunk, so this kernel never needs the counting
+//   fallback of the queued kernel; slices with more matched positions than
+//   their record space still go to the emit pass.
+#pragma once
+#include "kernels_q.cuh"
+
+namespace pfac {
+
+constexpr int RNW = 16;    // warps per CTA
+constexpr int RPF = 8;     // steps ahead of the L2 prefetch
+
+struct RWarpArea {
+    QEntry q[QCAP];
+    uint32_t tail[QCAP];   // the resolver's long-walk list (must follow q)
+};
+
+__device__ __forceinline__ uint4 ld_stream16(const uint8_t *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_stream4(const uint8_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Bytes j .. j + 3 of the lane's 20 staged bytes (16 own, 4 halo) for a
+// run-time j < 16: a select chain instead of an indexed register access.
+__device__ __forceinline__ uint32_t r_window(const uint32_t (&w)[5], uint32_t j) {
+    const uint32_t i = j >> 2;
+    uint32_t lo = w[0], hi = w[1];
+    if (i == 1) { lo = w[1]; hi = w[2]; }
+    if (i == 2) { lo = w[2]; hi = w[3]; }
+    if (i == 3) { lo = w[3]; hi = w[4]; }
+    return __funnelshift_r(lo, hi, 8 * (j & 3));
+}
+
+// First stage of one slice for the lane's 16 positions: bit j of the result
+// is set when position j's window passes the filter.  amask selects the
+// word-index bits of the address; gm and gsh are the gram hash's multiplier
+// and shift.
+template <int REP, int GRAM>
+__device__ __forceinline__ uint32_t r_first_stage(const uint32_t (&w)[5], const uint8_t *Tb,
+                                                  uint32_t c4, uint32_t amask, uint32_t gm,
+                                                  uint32_t gsh) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        const uint32_t t =
+            (j & 3) ? __funnelshift_r(w[j >> 2], w[(j >> 2) + 1], 8 * (j & 3)) : w[j >> 2];
+        uint32_t a;
+        if (GRAM) {
+            // word = top bits of t * gm (table.h), placed at bit REP + 2
+            a = (((t * gm) >> gsh) & amask) | c4;
+        } else {
+            // word = t >> 5 (the index's bits above the bit number), placed
+            // at bit REP + 2; the bits above the index fall outside amask
+            a = ((REP >= 3 ? (t << (REP - 3)) : (t >> (3 - REP))) & amask) | c4;
+        }
+        const uint32_t word = *reinterpret_cast<const uint32_t *>(Tb + a);
+        // bit t & 31 of the word to bit 0, then into the top of acc
+        acc = __funnelshift_r(acc, __funnelshift_r(word, word, t), 1);
+    }
+    return acc >> 16;
+}
+
+// Second stage of one candidate whose window (bytes j .. j + 3) is t:
+// prefix index x = the first k symbols.  With the gram filter the exact bit
+// of x in F_k must be set.  With child masks, and when the next symbol lies
+// inside the walk's limit, the entry's mask must hold that symbol's bit (an
+// entry that reports output has an all-ones mask); a symbol outside the
+// alphabet ends every other walk.
+template <int GRAM>
+__device__ __forceinline__ bool r_keep(const MatchParams &P, uint32_t t, bool has_next,
+                                       const uint32_t *Fs, const uint32_t *Cs, const uint32_t *Ms,
+                                       uint32_t &x) {
+    const uint32_t kb = 8u * P.k;
+    x = kb >= 32 ? t : (t & ((1u << kb) - 1u));
+    if (GRAM) {
+        const uint32_t fw = Fs[(x >> 5) << P.rep_log2];
+        if (!((fw >> (x & 31)) & 1u)) return false;
+    }
+    if (!P.tbl_m_words || !has_next) return true;
+    const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, x);
+    const uint32_t mr = Ms[r];
+    const uint32_t c = (t >> kb) & 0xFFu;
+    return c < P.T.sigma ? ((mr >> child_hash(c, P.T.sigma)) & 1u) != 0 : mr == 0xFFFFFFFFu;
+}
+
+// Positions of one lane's 16 whose k-symbol window lies inside their segment
+// and the staged bytes (fv), and positions inside their segment at all (ex),
+// for slices where a segment ends or the input stops; as in the queued
+// kernel's filter.
+__device__ __forceinline__ void r_window_masks(const MatchParams &P, uint32_t p0, uint32_t kf,
+                                               uint32_t valid, uint32_t staged, uint32_t rem,
+                                               uint32_t lima, uint32_t limb, bool general,
+                                               uint64_t ustart, uint32_t &fv, uint32_t &ex) {
+    fv = 0;
+    ex = 0;
+    if (p0 >= valid) return;
+    if (!general) {
+        auto below = [&](uint32_t x) -> uint32_t {  // positions p0 + j < x
+            const uint32_t n = x > p0 ? (x - p0 < 16u ? x - p0 : 16u) : 0u;
+            return n >= 32 ? 0xFFFFFFFFu : (1u << n) - 1u;
+        };
+        const uint32_t in_a = below(lima), vm = below(valid);
+        const uint32_t la = lima < staged ? lima : staged, lb = limb < staged ? limb : staged;
+        const uint32_t fa = la >= kf ? below(la - kf + 1) : 0u;  // p + kf <= la
+        const uint32_t fb = lb >= kf ? below(lb - kf + 1) : 0u;
+        ex = (in_a | below(limb)) & vm;
+        fv = ((fa & in_a) | (fb & ~in_a)) & vm;
+        return;
+    }
+#pragma unroll 1
+    for (uint32_t j = 0; j < 16; j++) {
+        const uint32_t p = p0 + j;
+        if (p >= valid) break;
+        const uint32_t lj = lim_of(P, p, lima, limb, true, ustart, rem);
+        if (lj > p) ex |= 1u << j;
+        const uint32_t lw = lj < staged ? lj : staged;
+        if (p + kf <= lw) fv |= 1u << j;
+    }
+}
+
+// Segment ends of one slice for its lanes (multi-segment inputs): lima = the
+// first offset above the lane's first position, limb = the one after;
+// general = some lane's positions meet more than that (or the window of 32
+// offsets ends inside the slice), the exact limit then found by search.
+__device__ __forceinline__ void r_seg_limits(const MatchParams &P, uint32_t u, uint64_t ustart,
+                                             uint32_t rem, uint32_t lane, uint32_t &lima,
+                                             uint32_t &limb, bool &general) {
+    const uint32_t sf = __ldg(P.unit_seg + u);
+    const uint32_t si = sf + lane;
+    const uint64_t o = si <= P.n_seg ? __ldg(P.seg + si) : ~0ull;
+    uint32_t wv = LIM_MAX;
+    if (o != ~0ull) {
+        const uint64_t r = o > ustart ? o - ustart : 0;
+        wv = r < rem ? (uint32_t)r : rem;
+    }
+    const uint32_t w0 = __shfl_sync(0xFFFFFFFFu, wv, 0);
+    const uint32_t w1 = __shfl_sync(0xFFFFFFFFu, wv, 1);
+    general = false;
+    if (w0 >= (uint32_t)(SLICE + 16)) {
+        // no segment end inside the slice or its halo: one limit for every lane
+        lima = w0 < rem ? w0 : rem;
+        limb = w1 < rem ? w1 : rem;
+        return;
+    }
+    const uint32_t p0 = lane * QBPT;
+    uint32_t j = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t v = __shfl_sync(0xFFFFFFFFu, wv, j + s - 1);
+        if (v <= p0) j += s;
+    }
+    const uint32_t vj = __shfl_sync(0xFFFFFFFFu, wv, j);
+    const uint32_t vj1 = __shfl_sync(0xFFFFFFFFu, wv, j < 31 ? j + 1 : 31);
+    const uint32_t last = __shfl_sync(0xFFFFFFFFu, wv, 31);
+    if (vj > p0) {
+        lima = vj < rem ? vj : rem;
+        limb = (j < 31 && vj1 < rem) ? vj1 : rem;
+    } else {
+        lima = rem;
+        limb = rem;
+    }
+    const bool need = (last < (uint32_t)SLICE && last < rem) || (lima < p0 + QBPT && limb < p0 + QBPT);
+    general = __any_sync(0xFFFFFFFFu, need);
+}
+
+struct RQueue {
+    uint32_t qn;          // entries queued (warp-uniform)
+    uint32_t carry_unit;  // slice continued into the next batch (UNIT_OVF: none)
+    uint32_t carry;       // its records in earlier batches
+};
+
+// Appends the lane's queue entries (the bits of keep | root, in position
+// order; the lanes in lane order) for slice `unit`; resolves the queue first
+// when they do not fit, and resolves in queue-sized chunks a slice that alone
+// has more entries than the queue holds.
+template <int W, int VAR>
+__device__ __forceinline__ void r_append(const MatchParams &P, RWarpArea &A, RQueue &Q,
+                                         uint32_t keep, uint32_t root, const uint32_t (&w)[5],
+                                         uint32_t unit, uint32_t lima, uint32_t limb,
+                                         bool general, uint64_t ustart, uint32_t rem,
+                                         const uint32_t *Fs, const uint32_t *Cs,
+                                         const uint32_t *Es, uint32_t lane) {
+    const uint32_t m = keep | root;
+    const uint32_t c = __popc(m);
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += nb;
+    }
+    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    if (tot == 0) return;
+    const uint32_t excl = inc - c;
+    if (Q.qn + tot > (uint32_t)QCAP && Q.qn) {
+        flush_records_c<W, VAR>(P, A.q, Q.qn, Fs, Cs, Es, lane, Q.carry_unit, Q.carry);
+        Q.qn = 0;
+    }
+    const uint32_t p0 = lane * QBPT;
+    const uint32_t kb = 8u * P.k, kmask = kb >= 32 ? 0xFFFFFFFFu : (1u << kb) - 1u;
+    for (uint32_t done = 0;;) {
+        const uint32_t room = QCAP - Q.qn;
+        const uint32_t take = tot - done < room ? tot - done : room;
+        uint32_t mm = m, e = excl;
+        while (mm) {
+            const uint32_t j = __ffs(mm) - 1;
+            mm &= mm - 1;
+            if (e >= done && e < done + take) {
+                const uint32_t p = p0 + j, slot = e - done;
+                QEntry en;
+                en.unit = unit;
+                en.pos = p | (slot << 10) | (e + 1 == tot ? LAST_FLAG : 0u);
+                en.x = ((root >> j) & 1u) ? ROOT_X : (r_window(w, j) & kmask);
+                en.lim = lim_of(P, p, lima, limb, general, ustart, rem);
+                A.q[Q.qn + slot] = en;
+            }
+            e++;
+        }
+        __syncwarp();
+        Q.qn += take;
+        done += take;
+        if (done == tot) break;
+        // the queue is full and the slice goes on: resolve, carrying its ranks
+        flush_records_c<W, VAR>(P, A.q, Q.qn, Fs, Cs, Es, lane, Q.carry_unit, Q.carry);
+        Q.qn = 0;
+    }
+}
+
+// One slice: window masks, first stage, second stage, queue.
+template <int W, int REP, int GRAM, int VAR>
+__device__ __forceinline__ void r_slice(const MatchParams &P, RWarpArea &A, RQueue &Q,
+                                        const uint32_t (&w)[5], bool halo_ok, uint32_t u,
+                                        const uint8_t *Tb,
+                                        uint32_t c4, uint32_t amask, uint32_t gm, uint32_t gsh,
+                                        const uint32_t *Fs, const uint32_t *Cs,
+                                        const uint32_t *Es, const uint32_t *Ms, uint32_t lane) {
+    const uint64_t ustart = (uint64_t)u << SLICE_SHIFT;
+    const uint64_t remain = P.n - ustart;
+    const uint32_t rem = remain < LIM_MAX ? (uint32_t)remain : LIM_MAX;
+    uint32_t valid = rem < (uint32_t)SLICE ? rem : (uint32_t)SLICE;
+    {
+        const uint64_t sl = P.starts_end > ustart ? P.starts_end - ustart : 0;
+        if (sl < valid) valid = (uint32_t)sl;
+    }
+    // bytes held in registers: whole 16-byte chunks, then (halo_ok) the
+    // 4-byte head of the next slice
+    const uint32_t staged = rem < (uint32_t)SLICE ? rem & ~15u
+                                                  : (uint32_t)SLICE + (halo_ok ? 4u : 0u);
+    uint32_t lima = rem, limb = rem;
+    bool general = false;
+    if (P.n_seg > 1) r_seg_limits(P, u, ustart, rem, lane, lima, limb, general);
+    const uint32_t kf = P.kf;
+    const uint32_t p0 = lane * QBPT;
+    uint32_t surv = r_first_stage<REP, GRAM>(w, Tb, c4, amask, gm, gsh);
+    uint32_t fv = 0xFFFFu, ex = 0xFFFFu;
+    const uint32_t lim0 = lima < staged ? lima : staged;
+    if (general || p0 + QBPT - 1 + kf > lim0 || p0 + QBPT > valid)
+        r_window_masks(P, p0, kf, valid, staged, rem, lima, limb, general, ustart, fv, ex);
+    surv &= fv;
+    const uint32_t root = ex & ~fv;
+    // second stage over the lane's candidates
+    uint32_t keep = 0;
+    const uint32_t k = P.k;
+    uint32_t mm = surv;
+    while (mm) {
+        const uint32_t j = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const uint32_t p = p0 + j;
+        const uint32_t t = r_window(w, j);
+        // the next symbol is held in registers and inside the walk's limit
+        const bool has_next =
+            p + k < staged && p + k < lim_of(P, p, lima, limb, general, ustart, rem);
+        uint32_t x;
+        if (r_keep<GRAM>(P, t, has_next, Fs, Cs, Ms, x)) keep |= 1u << j;
+    }
+    if (__any_sync(0xFFFFFFFFu, (keep | root) != 0))
+        r_append<W, VAR>(P, A, Q, keep, root, w, u, lima, limb, general, ustart, rem, Fs, Cs, Es,
+                         lane);
+}
+
+// The scan pass of the compressed layout with 8-bit symbols.  The int
+// argument is unused (the launch signature is shared with the other scan
+// kernels).
+template <int W, int REP, int GRAM, int VAR>
+__global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, const int) {
+    constexpr uint32_t RTHREADS = RNW * 32;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n_units = P.n_tiles;
+    const uint32_t n_pairs = (n_units + 1) >> 1;
+    const uint32_t gw = blockIdx.x * RNW + warp, gstride = gridDim.x * RNW;
+    if (blockIdx.x * RNW >= n_pairs) return;  // the whole CTA has no pair
+
+    uint32_t *Fs = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *Cs = Fs + P.tbl_words;
+    uint32_t *Es = Cs + P.tbl_c_words;
+    uint32_t *Ms = Es + P.tbl_e_words;
+    uint32_t *Gs = Ms + P.tbl_m_words;
+    RWarpArea *areas = reinterpret_cast<RWarpArea *>(
+        smem + ((((size_t)P.tbl_words + P.tbl_c_words + P.tbl_e_words + P.tbl_m_words +
+                  P.tbl_g_words) * 4 + 127) & ~(size_t)127));
+    {
+        const uint32_t rep = P.rep_log2;
+        for (uint32_t i = threadIdx.x; i < P.tbl_words; i += RTHREADS) Fs[i] = __ldg(P.F + (i >> rep));
+        for (uint32_t i = threadIdx.x; i < P.tbl_c_words; i += RTHREADS) Cs[i] = __ldg(P.C + i);
+        if (VAR == VAR_FE)
+            for (uint32_t i = threadIdx.x; i < P.tbl_e_words; i += RTHREADS) Es[i] = __ldg(P.E + i);
+        for (uint32_t i = threadIdx.x; i < P.tbl_m_words; i += RTHREADS) Ms[i] = __ldg(P.M + i);
+        // gram filter: word w of each copy is the OR of 2^g_fold table words
+        const uint32_t gr = P.g_rep, gf = P.g_fold;
+        for (uint32_t i = threadIdx.x; i < P.tbl_g_words; i += RTHREADS) {
+            const uint32_t *src = P.T.G + ((size_t)(i >> gr) << gf);
+            uint32_t v = 0;
+            for (uint32_t f = 0; f < (1u << gf); f++) v |= __ldg(src + f);
+            Gs[i] = v;
+        }
+    }
+    __syncthreads();
+    RWarpArea &A = areas[warp];
+
+    // first-stage constants: the table, the lane's copy, the address mask
+    const uint8_t *Tb = reinterpret_cast<const uint8_t *>(GRAM ? Gs : Fs);
+    const uint32_t c4 = (lane & ((1u << REP) - 1u)) << 2;
+    uint32_t amask, gm = 0, gsh = 0;
+    if (GRAM) {
+        const uint32_t hbw = P.g_hb - 5;
+        gm = gram_mul(8u * P.kf);
+        gsh = 30u - hbw - REP;  // (t * gm) >> gsh puts the word at bit REP + 2
+        amask = ((1u << hbw) - 1u) << (REP + 2);
+    } else {
+        amask = ((1u << (8u * P.k - 5u)) - 1u) << (REP + 2);
+    }
+
+    const uint64_t N = P.n;
+    auto load_pair = [&](uint32_t i, uint4 &a, uint4 &b, uint32_t &h) {
+        a = make_uint4(0, 0, 0, 0);
+        b = a;
+        h = 0;
+        const uint32_t g = gw + i * gstride;
+        if (g >= n_pairs) return;
+        const uint64_t s0 = (uint64_t)g << (SLICE_SHIFT + 1);
+        const uint64_t o0 = s0 + lane * 16u, o1 = o0 + SLICE;
+        if (o0 + 16 <= N) a = ld_stream16(P.in + o0);
+        if (o1 + 16 <= N) b = ld_stream16(P.in + o1);
+        if (lane == 31 && s0 + 2 * SLICE + 4 <= N) h = ld_stream4(P.in + s0 + 2 * SLICE);
+    };
+    auto prefetch = [&](uint32_t i) {
+        const uint32_t g = gw + i * gstride;
+        if (lane == 0 && g < n_pairs) {
+            const uint64_t s0 = (uint64_t)g << (SLICE_SHIFT + 1);
+            if (s0 < N) {
+                const uint64_t left = N - s0;
+                const uint32_t bytes = (left < 2 * SLICE ? (uint32_t)left : 2u * SLICE) & ~15u;
+                if (bytes) prefetch_l2(P.in + s0, bytes);
+            }
+        }
+    };
+    if (lane == 0)
+        for (uint32_t i = 0; i < RPF; i++) prefetch(i);
+
+    RQueue Q{0u, UNIT_OVF, 0u};
+    uint4 ca, cb, na, nb;
+    uint32_t ch, nh;
+    load_pair(0, ca, cb, ch);
+    for (uint32_t i = 0; gw + i * gstride < n_pairs; i++) {
+        load_pair(i + 1, na, nb, nh);
+        prefetch(i + RPF);
+        const uint32_t g = gw + i * gstride;
+        // halo words: the next lane's first word; lane 31 takes the second
+        // slice's lane 0 (first slice) or the next pair's head (second slice)
+        const uint32_t a_next = __shfl_down_sync(0xFFFFFFFFu, ca.x, 1);
+        const uint32_t b_next = __shfl_down_sync(0xFFFFFFFFu, cb.x, 1);
+        const uint32_t b_first = __shfl_sync(0xFFFFFFFFu, cb.x, 0);
+        {
+            // the head of slice 2g + 1 is held when its lane 0 chunk was loaded
+            const uint32_t wa[5] = {ca.x, ca.y, ca.z, ca.w, lane == 31 ? b_first : a_next};
+            const uint64_t s1 = ((uint64_t)2 * g + 1) << SLICE_SHIFT;
+            r_slice<W, REP, GRAM, VAR>(P, A, Q, wa, s1 + 16 <= N, 2 * g, Tb, c4, amask, gm, gsh,
+                                       Fs, Cs, Es, Ms, lane);
+        }
+        if (2 * g + 1 < n_units) {
+            const uint32_t wb[5] = {cb.x, cb.y, cb.z, cb.w, lane == 31 ? ch : b_next};
+            const uint64_t s2 = ((uint64_t)2 * g + 2) << SLICE_SHIFT;
+            r_slice<W, REP, GRAM, VAR>(P, A, Q, wb, s2 + 4 <= N, 2 * g + 1, Tb, c4, amask, gm, gsh,
+                                       Fs, Cs, Es, Ms, lane);
+        }
+        ca = na;
+        cb = nb;
+        ch = nh;
+    }
+    flush_records_c<W, VAR>(P, A.q, Q.qn, Fs, Cs, Es, lane, Q.carry_unit, Q.carry);
+}
+
+}  // namespace pfac

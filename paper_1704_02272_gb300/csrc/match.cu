@@ -9,7 +9,7 @@
 #include <mutex>
 
 #include "internal.h"
-#include "kernels_q.cuh"
+#include "kernels_r.cuh"
 
 namespace pfac {
 
@@ -22,6 +22,15 @@ void *scan_kernel_bps6(int, int, int);
 void *scan_kernel_bps7(int, int, int);
 void *scan_kernel_bps8(int, int, int);
 void *scan_kernel_dense();
+void *scan_kernel_r8_g0_f(int rep);
+void *scan_kernel_r8_g0_fe(int rep);
+void *scan_kernel_r8_g1_f(int rep);
+void *scan_kernel_r8_g1_fe(int rep);
+
+static void *scan_kernel_r(int rep, bool gram, int var) {
+    if (gram) return var == VAR_FE ? scan_kernel_r8_g1_fe(rep) : scan_kernel_r8_g1_f(rep);
+    return var == VAR_FE ? scan_kernel_r8_g0_fe(rep) : scan_kernel_r8_g0_f(rep);
+}
 
 constexpr int CHUNK = 1024;      // tiles per chunk of the key-count scan
 constexpr int RT = 1024;         // threads of the scan/offset kernels
@@ -239,7 +248,14 @@ struct Plan {
     void *kernel_emit;  // emit pass
     size_t smem;
     bool queued;
+    int kind;           // SCAN_QUEUED or SCAN_REGISTER (compressed layout)
+    // emit pass of a register-staged plan: the queued kernel with tables of
+    // its own (one bitmap copy, entries through L2)
+    size_t smem_emit;
+    uint32_t e_tbl_words, e_tbl_m_words;
 };
+
+enum { SCAN_QUEUED = 1, SCAN_REGISTER = 2 };
 
 struct WsLayout {
     uint64_t hdr, tile_m, tile_k, key_off, chunk, ovf, recs, bounds, total;
@@ -318,6 +334,135 @@ static double first_stage_cost(double dens, int rep, bool hashed) {
            90.0 * (1.0 - exp(-cand)) + 12.0 * cand;
 }
 
+// Expected iterations of the register-staged kernel's second-stage loop:
+// the largest candidate count over a warp's 32 lanes when each lane's count
+// is Poisson with mean lam.
+static double r_rounds(double lam) {
+    double e = 0.0, cdf = 0.0, pm = exp(-lam);
+    for (int m = 0; m < 200; m++) {
+        cdf += pm;
+        const double gt = 1.0 - pow(cdf < 1.0 ? cdf : 1.0, 32.0);  // P(max > m)
+        e += gt;
+        if (gt < 1e-7) break;
+        pm *= lam / (m + 1);
+    }
+    return e;
+}
+
+// Estimated warp instructions per slice of the register-staged kernel: the
+// first stage (5 per position, 7 with the gram hash), bank-conflict replays
+// and about 27 per round of the second-stage loop.
+static double r_cost(double dens, int rep, bool hashed) {
+    return 16.0 * (hashed ? 7.0 : 5.0) + 16.0 * (load_wavefronts(rep) - 1.0) +
+           27.0 * r_rounds(16.0 * dens);
+}
+
+static size_t r_smem(uint64_t words) {
+    return (((size_t)words * 4 + 127) & ~(size_t)127) + RNW * sizeof(RWarpArea);
+}
+
+constexpr int R_MAX_REP = 4;  // copies of the first-stage bitmap: 1 .. 16
+constexpr bool R_BY_DEFAULT = false;  // the register-staged kernel runs on request
+
+// Plan of the register-staged kernel (8-bit symbols): the first stage (the
+// prefix bitmap, or the gram filter folded to fit) and its copies, entries
+// and child masks in shared memory as they fit, chosen by r_cost; the emit
+// pass runs the queued kernel with one bitmap copy.
+static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks, uint32_t gram,
+                       int want, Plan *pl) {
+    const DevTable &T = t->dev;
+    const uint64_t ent = 1ull << (k * T.bps);
+    const uint32_t fw = (uint32_t)(ent >= 32 ? ent / 32 : 1);
+    const uint32_t cw = (fw + (1u << T.c_shift[k]) - 1) >> T.c_shift[k];
+    const uint32_t ew = T.n_e[k];
+    const bool have_m = T.M[k] != nullptr;
+    const uint32_t mw = T.m_words[k];
+    const double dens_f = (double)ew / (double)ent;
+    double best = 1e30;
+    int b_var = 0, b_rep = -1;
+    uint32_t b_fold = 0;
+    bool b_gram = false, b_m = false;
+    for (int vv = VAR_FE; vv >= VAR_F; vv--) {
+        if (var != 0 && var != vv) continue;
+        for (int mm = 1; mm >= 0; mm--) {
+            const bool mon = mm == 1;
+            if (mon && !(have_m && masks != 1)) continue;
+            if (!mon && masks == 2) continue;
+            const uint64_t base = cw + (vv == VAR_FE ? ew : 0u) + (mon ? mw : 0u);
+            // a preference for what keeps the walks short: entries in shared
+            // memory, and above all the child masks, which drop most candidates
+            const double bias = (vv == VAR_FE ? 1.0 : 1.05) * (mon ? 1.0 : 1.3);
+            for (int r = 0; r <= R_MAX_REP; r++) {
+                if (want >= 0 && r != want) continue;
+                if (gram != 2 && r_smem(base + ((uint64_t)fw << r)) <= SMEM_LIMIT) {
+                    const double c = r_cost(dens_f, r, false) * bias;
+                    if (c < best) {
+                        best = c;
+                        b_var = vv;
+                        b_rep = r;
+                        b_gram = false;
+                        b_m = mon;
+                    }
+                }
+                if (T.g_len && gram != 1) {
+                    const uint32_t hb = T.g_bits;
+                    const uint64_t gw0 = (1ull << hb) / 32;
+                    for (uint32_t f = 0; hb - f >= GRAM_MIN_BITS; f++) {
+                        if (r_smem(base + fw + ((gw0 >> f) << r)) > SMEM_LIMIT) continue;
+                        const double dens = 1.0 - exp(-(double)T.g_set / (double)(1ull << (hb - f)));
+                        const double c = r_cost(dens, r, true) * bias;
+                        if ((gram == 2 || dens < 0.5) && c < best) {
+                            best = c;
+                            b_var = vv;
+                            b_rep = r;
+                            b_gram = true;
+                            b_fold = f;
+                            b_m = mon;
+                        }
+                        break;  // the least folding that fits
+                    }
+                }
+            }
+        }
+    }
+    if (b_rep < 0)
+        return set_error(PFAC_EINVAL, "pfac_match: no register-staged plan fits in shared memory "
+                         "with depth %u%s", k, want >= 0 ? " and these copies" : "");
+    pl->var = b_var;
+    pl->k = k;
+    pl->tbl_c_words = cw;
+    pl->tbl_e_words = b_var == VAR_FE ? ew : 0u;
+    pl->tbl_m_words = b_m ? mw : 0u;
+    pl->tbl_b_words = 0;
+    if (b_gram) {
+        pl->rep_log2 = 0;
+        pl->tbl_words = fw;
+        pl->g_rep = (uint32_t)b_rep;
+        pl->g_fold = b_fold;
+        pl->tbl_g_words = (uint32_t)((((1ull << T.g_bits) / 32) >> b_fold) << b_rep);
+    } else {
+        pl->rep_log2 = (uint32_t)b_rep;
+        pl->tbl_words = fw << b_rep;
+    }
+    pl->nw = RNW;
+    pl->kind = SCAN_REGISTER;
+    pl->kernel = scan_kernel_r(b_rep, b_gram, b_var);
+    pl->smem = r_smem((uint64_t)pl->tbl_words + pl->tbl_c_words + pl->tbl_e_words +
+                      pl->tbl_m_words + pl->tbl_g_words);
+    // the emit pass: the queued kernel, one bitmap copy, entries through L2,
+    // child masks when they fit beside its warps' rings
+    pl->e_tbl_words = fw;
+    pl->e_tbl_m_words = (have_m && queued_smem((uint64_t)fw + cw + mw, QW) <= SMEM_LIMIT) ? mw : 0u;
+    pl->smem_emit = queued_smem((uint64_t)fw + cw + pl->e_tbl_m_words, QW);
+    pl->kernel_emit = scan_kernel_for(T.bps, VAR_F, 1, QW);
+    pl->unit_shift = SLICE_SHIFT;
+    pl->unit_cap = SCAP;
+    pl->queued = true;
+    if (!pl->kernel || !pl->kernel_emit)
+        return set_error(PFAC_EINVAL, "pfac_match: no register-staged kernel for this table");
+    return PFAC_OK;
+}
+
 static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl) {
     const DevTable &T = t->dev;
     memset(pl, 0, sizeof(*pl));
@@ -389,6 +534,22 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                          copies);
     if (var != 0 && var != VAR_F && var != VAR_FE)
         return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
+
+    // ---- the register-staged kernel (8-bit symbols): on request, or by
+    // default when the caller asks for nothing only the queued kernel has
+    const uint32_t want_kind = opts && opts->scan_kernel ? opts->scan_kernel
+                                                         : (use_tuned ? t->tuned_kernel : 0u);
+    if (want_kind > 2) return set_error(PFAC_EINVAL, "pfac_match: scan_kernel %u", want_kind);
+    const bool r_usable = T.bps == 8 && pbytes != 2 && !(opts && opts->warps_per_cta);
+    if (want_kind == SCAN_REGISTER && !r_usable)
+        return set_error(PFAC_EINVAL, "pfac_match: the register-staged kernel needs 8-bit symbols "
+                         "(alphabets of 129 to 256) and no prefix bytes or CTA width");
+    if (want_kind == SCAN_REGISTER || (want_kind == 0 && r_usable && R_BY_DEFAULT)) {
+        const int rc = make_plan_r(t, k, var, masks, gram, want, pl);
+        if (rc == PFAC_OK || want_kind == SCAN_REGISTER) return rc;
+        clear_error();
+        memset(pl, 0, sizeof(*pl));
+    }
 
     // ---- prefix bitmap as the first stage: largest replication that fits
     auto best_rep = [&](uint64_t extra) -> int {
@@ -529,6 +690,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     if (queued_smem(tw, nwant) > SMEM_LIMIT)
         return set_error(PFAC_EINVAL, "pfac_match: %u warps do not fit next to the tables", nwant);
     pl->nw = nwant;
+    pl->kind = SCAN_QUEUED;
     pl->kernel = scan_kernel_for(T.bps, var, 0, (int)nwant);
     pl->kernel_emit = scan_kernel_for(T.bps, var, 1, (int)nwant);
     pl->smem = queued_smem(tw, nwant);
@@ -561,6 +723,34 @@ static int prepare_kernel(void *fn, size_t smem) {
         done_dev[n_done] = dev;
         done_sz[n_done] = smem;
         n_done++;
+    }
+    return PFAC_OK;
+}
+
+int check_table_device(const pfac_table *t, void *cuda_stream, const char *who) {
+    int cur = 0;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess)
+        return set_error(PFAC_ECUDA, "%s: cudaGetDevice: %s", who, cudaGetErrorString(e));
+    if (cur != t->device)
+        return set_error(PFAC_EINVAL, "%s: the current device is %d but the table lives on "
+                         "device %d; make device %d current", who, cur, t->device, t->device);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cuda_stream && cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusNone;
+    }
+    // the stream's device cannot be queried while the stream captures a graph
+    // (the query is not permitted then); the current-device check stands
+    if (cuda_stream && cap == cudaStreamCaptureStatusNone) {
+        int sd = 0;
+        e = cudaStreamGetDevice((cudaStream_t)cuda_stream, &sd);
+        if (e != cudaSuccess)
+            return set_error(PFAC_ECUDA, "%s: cudaStreamGetDevice: %s", who,
+                             cudaGetErrorString(e));
+        if (sd != t->device)
+            return set_error(PFAC_EINVAL, "%s: the stream belongs to device %d but the table "
+                             "lives on device %d", who, sd, t->device);
     }
     return PFAC_OK;
 }
@@ -608,6 +798,7 @@ extern "C" int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts,
     out->gram_bits = g ? t->dev.g_bits - pl.g_fold : 0u;
     out->prefix_bytes = pl.tbl_b_words ? 2u : 1u;
     out->warps_per_cta = pl.nw;
+    out->scan_kernel = (uint32_t)pl.kind;
     return PFAC_OK;
 }
 
@@ -619,6 +810,10 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     if (!t || !d_count || !d_seg_offsets || !d_workspace)
         return set_error(PFAC_EINVAL, "pfac_match: NULL argument");
     if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_match: table was built host-only");
+    {
+        const int drc = check_table_device(t, cuda_stream, "pfac_match");
+        if (drc) return drc;
+    }
     if (n_bytes && !d_input) return set_error(PFAC_EINVAL, "pfac_match: NULL input");
     if (((uintptr_t)d_input & 15) != 0)
         return set_error(PFAC_EINVAL, "pfac_match: input must be 16-byte aligned");
@@ -644,8 +839,10 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     if (workspace_bytes < L.total)
         return set_error(PFAC_EINVAL, "pfac_match: workspace of %llu bytes, %llu needed",
                          (unsigned long long)workspace_bytes, (unsigned long long)L.total);
+    const bool reg = pl.kind == SCAN_REGISTER;
+    const size_t smem_emit = reg ? pl.smem_emit : pl.smem;
     rc = prepare_kernel(pl.kernel, pl.smem);
-    if (!rc && pl.kernel_emit != pl.kernel) rc = prepare_kernel(pl.kernel_emit, pl.smem);
+    if (!rc && pl.kernel_emit != pl.kernel) rc = prepare_kernel(pl.kernel_emit, smem_emit);
     if (rc) return rc;
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -698,7 +895,9 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.rep_log2 = pl.rep_log2;
     P.dense_rows = pl.dense_rows;
     const uint32_t nthreads = pl.queued ? pl.nw * 32 : NTHREADS;
-    const uint32_t units_per_cta = pl.queued ? pl.nw : 1;
+    // units a CTA takes in one round: the register-staged kernel's warps
+    // take two slices each
+    const uint32_t units_per_cta = pl.queued ? (reg ? 2 * pl.nw : pl.nw) : 1;
 
     // header, and for the queued kernel the per-unit record and key counts
     // (the scan pass writes them only for units with kept survivors)
@@ -730,11 +929,34 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
         k_offsets<<<P.n_chunks, RT, 0, st>>>(P);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && opts && opts->ev_emit_begin)
+        e = cudaEventRecord((cudaEvent_t)opts->ev_emit_begin, st);
     if (e == cudaSuccess && P.n_tiles) {
         int emit = 1;
-        void *args[] = {&P, &emit};
-        e = cudaLaunchKernel(pl.kernel_emit, dim3(grid), dim3(nthreads), args, pl.smem, st);
+        if (reg) {
+            // the queued kernel re-scans the overflowing slices with its own
+            // tables: one prefix-bitmap copy, entries through L2
+            MatchParams P2 = P;
+            P2.tbl_words = pl.e_tbl_words;
+            P2.rep_log2 = 0;
+            P2.tbl_e_words = 0;
+            P2.tbl_m_words = pl.e_tbl_m_words;
+            P2.tbl_g_words = 0;
+            P2.g_rep = P2.g_fold = P2.g_hb = 0;
+            P2.tbl_b_words = 0;
+            P2.kf = pl.k;
+            const uint64_t want_e = ((uint64_t)P.n_tiles + QW - 1) / QW;
+            const uint32_t grid_e =
+                (uint64_t)nsm * cps < want_e ? (uint32_t)nsm * cps : (uint32_t)want_e;
+            void *args[] = {&P2, &emit};
+            e = cudaLaunchKernel(pl.kernel_emit, dim3(grid_e), dim3(QW * 32), args, smem_emit, st);
+        } else {
+            void *args[] = {&P, &emit};
+            e = cudaLaunchKernel(pl.kernel_emit, dim3(grid), dim3(nthreads), args, pl.smem, st);
+        }
     }
+    if (e == cudaSuccess && opts && opts->ev_emit_end)
+        e = cudaEventRecord((cudaEvent_t)opts->ev_emit_end, st);
     if (e == cudaSuccess) {
         const uint64_t units = P.n_tiles ? P.n_tiles : 1;
         uint64_t blocks = (units + 255) / 256;
@@ -754,6 +976,9 @@ extern "C" int pfac_match(const pfac_table *t, const uint8_t *d_input, uint64_t 
                           void *cuda_stream) {
     clear_error();
     if (!t || !n_out) return set_error(PFAC_EINVAL, "pfac_match: NULL argument");
+    if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_match: table was built host-only");
+    int drc = check_table_device(t, cuda_stream, "pfac_match");
+    if (drc) return drc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     uint64_t ws_bytes = 0;
     int rc0 = pfac_workspace_bytes(t, n_bytes, n_segments, opts, &ws_bytes);

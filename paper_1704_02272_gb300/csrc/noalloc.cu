@@ -24,11 +24,44 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
+// Per device: the CUDA context the address was looked up in, and the
+// address.  A device whose context was destroyed and created again (a
+// cudaDeviceReset) gets a new lookup when its current context differs.
+struct ScratchAddr {
+    void *ctx = nullptr;
+    void *ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
+
+// The driver's cuCtxGetCurrent, reached through the runtime so the library
+// needs no link against the driver library; nullptr when unavailable.
+typedef int (*CtxGetCurrentFn)(void **);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (CtxGetCurrentFn)f;
+    }();
+    return fn;
+}
+
+void *current_context() {
+    void *ctx = nullptr;
+    CtxGetCurrentFn f = ctx_get_current();
+    if (!f || f(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 // Device address of this device's copy of the array.  In host code the
 // array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress with the device current; it is looked up on the first
+// call on a device (and again after that device's context was replaced).
 int scratch_for_current_device(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -38,15 +71,20 @@ int scratch_for_current_device(void **out) {
     if (dev < 0 || dev >= kMaxDevices)
         return pfac::set_error(PFAC_EINVAL, "pfac_match_noalloc: device %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchAddr &c = g_scratch[dev];
+    void *ctx = current_context();
+    if (!c.ptr || !ctx || c.ctx != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
             return pfac::set_error(PFAC_ECUDA, "pfac_match_noalloc: cudaGetSymbolAddress: %s",
                                    cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
+        }
+        c.ptr = p;
+        c.ctx = current_context();  // the runtime's context exists now
     }
-    *out = g_scratch_ptr[dev];
+    *out = c.ptr;
     return PFAC_OK;
 }
 
@@ -59,8 +97,12 @@ extern "C" int pfac_match_noalloc(const pfac_table *t, const uint8_t *d_input, u
                                   void *cuda_stream) {
     pfac::clear_error();
     if (!t) return pfac::set_error(PFAC_EINVAL, "pfac_match_noalloc: NULL table");
+    if (!t->d_blob)
+        return pfac::set_error(PFAC_EINVAL, "pfac_match_noalloc: table was built host-only");
+    int rc = pfac::check_table_device(t, cuda_stream, "pfac_match_noalloc");
+    if (rc) return rc;
     uint64_t need = 0;
-    int rc = pfac_workspace_bytes(t, n_bytes, n_segments, opts, &need);
+    rc = pfac_workspace_bytes(t, n_bytes, n_segments, opts, &need);
     if (rc) return rc;
     if (need > (uint64_t)PFAC_NOALLOC_SCRATCH_BYTES)
         return pfac::set_error(PFAC_EINVAL,

@@ -285,6 +285,10 @@ extern "C" int pfac_server_create(const pfac_table *t, const pfac_server_opts *o
     clear_error();
     if (!t || !out) return set_error(PFAC_EINVAL, "pfac_server_create: NULL argument");
     if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_server_create: host-only table");
+    {
+        const int drc = check_table_device(t, nullptr, "pfac_server_create");
+        if (drc) return drc;
+    }
     pfac_server_opts opt{};
     if (o) opt = *o;
     const uint32_t n_slots = opt.n_slots ? opt.n_slots : 4;

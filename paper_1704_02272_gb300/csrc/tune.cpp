@@ -1,12 +1,14 @@
 // Autotuner of the scan configuration (pfac_autotune).  For a built table
 // and a device-resident sample it times the scan kernel for each candidate
-// (prefix depth resolved in shared memory x entries in shared memory or not x
-// child masks on or off x the first stage (prefix bitmap, gram filter or
-// prefix bytes) x copies of that bitmap over the banks), keeps the fastest as the
+// (the scan kernel: queued or register-staged x prefix depth resolved in
+// shared memory x entries in shared memory or not x child masks on or off x
+// the first stage (prefix bitmap, gram filter or prefix bytes) x copies of
+// that bitmap over the banks x CTA width), keeps the fastest as the
 // table's default, and can remember the choice in a small text cache keyed by
 // the table's shape and the GPU.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -36,27 +38,45 @@ std::string cache_key(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments
     return buf;
 }
 
+// A cache line: key, variant, depth, copies, masks, gram filter, prefix
+// bytes, warps per CTA, scan kernel, time.  Lines without the scan kernel
+// (written before the register-staged kernel existed) name the queued one.
 bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_t *k,
                   uint32_t *c, uint32_t *mk, uint32_t *gf, uint32_t *pb, uint32_t *nw,
-                  float *ms) {
+                  uint32_t *kind, float *ms) {
     FILE *f = fopen(path, "r");
     if (!f) return false;
     char line[512];
     bool found = false;
     while (fgets(line, sizeof line, f)) {
-        char kbuf[300];
-        uint32_t a, b, d, g, h, y, z;
-        float e;
-        if (sscanf(line, "%299s %u %u %u %u %u %u %u %f", kbuf, &a, &b, &d, &g, &h, &y, &z,
-                   &e) == 9 &&
-            key == kbuf) {
-            *pb = y;
-            *nw = z;
-            *v = a;
-            *k = b;
-            *c = d;
-            *mk = g;
-            *gf = h;
+        // whitespace-separated tokens: the key, then 8 or 9 fields
+        char *tok[12], *save = nullptr;
+        int nt = 0;
+        for (char *p = strtok_r(line, " \t\r\n", &save); p && nt < 12;
+             p = strtok_r(nullptr, " \t\r\n", &save))
+            tok[nt++] = p;
+        if ((nt != 9 && nt != 10) || key != tok[0]) continue;
+        uint32_t u[8];
+        bool ok = true;
+        for (int i = 0; i < nt - 2; i++) {
+            char *end = nullptr;
+            const unsigned long x = strtoul(tok[1 + i], &end, 10);
+            if (!end || *end || x > 0xFFFFFFFFul) ok = false;
+            u[i] = (uint32_t)x;
+        }
+        char *end = nullptr;
+        const float e = strtof(tok[nt - 1], &end);
+        if (!ok || !end || *end) continue;
+        {
+            const uint32_t q = nt == 10 ? u[7] : 1u;
+            *v = u[0];
+            *k = u[1];
+            *c = u[2];
+            *mk = u[3];
+            *gf = u[4];
+            *pb = u[5];
+            *nw = u[6];
+            *kind = q;
             *ms = e;
             found = true;  // the last line for a key wins
         }
@@ -78,14 +98,17 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     memset(&res, 0, sizeof res);
     const std::string key = cache_key(t, n_bytes, n_segments);
     if (cache_path) {
-        uint32_t v, k, c, mk, gf, pb, nw;
+        uint32_t v, k, c, mk, gf, pb, nw, kind;
         float ms;
-        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &nw, &ms) && k >= t->kmin &&
-            k <= t->kmax && (gf != 2 || t->dev.g_len) && (pb != 2 || t->dev.B[k])) {
+        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &nw, &kind, &ms) &&
+            k >= t->kmin && k <= t->kmax && (gf != 2 || t->dev.g_len) &&
+            (pb != 2 || t->dev.B[k])) {
             t->tuned_bytes = pb;
             t->tuned_nw = nw;
+            t->tuned_kernel = kind;
             res.prefix_bytes = pb;
             res.warps_per_cta = nw;
+            res.scan_kernel = kind;
             t->tuned_variant = v;
             t->tuned_k = k;
             t->tuned_copies = c;
@@ -101,8 +124,9 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
             // a cached choice that no longer makes a plan (an edited or
             // foreign cache line) is dropped and the table tuned afresh
             pfac_plan_info pi;
-            const bool sane = (nw == 16 || nw == 24) && v <= 2 && mk <= 2 && gf <= 2 &&
-                              pb <= 2 && c <= 32 && (c & (c - 1)) == 0;
+            const bool sane = (kind == 1 ? (nw == 16 || nw == 24) : (kind == 2 && nw == 0)) &&
+                              v <= 2 && mk <= 2 && gf <= 2 && pb <= 2 && c <= 32 &&
+                              (c & (c - 1)) == 0;
             if (sane && pfac_match_plan(t, nullptr, &pi) == PFAC_OK) {
                 if (out) *out = res;
                 return PFAC_OK;
@@ -116,13 +140,19 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     t->tuned_variant = t->tuned_k = t->tuned_copies = t->tuned_masks = t->tuned_gram = 0;
     t->tuned_bytes = 0;
     t->tuned_nw = 0;
+    t->tuned_kernel = 0;
+    if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_autotune: table was built host-only");
+    {
+        const int drc = check_table_device(t, cuda_stream, "pfac_autotune");
+        if (drc) return drc;
+    }
 
     struct Cand {
-        uint32_t var, k, copies, masks, gram, bytes, nw;
+        uint32_t var, k, copies, masks, gram, bytes, nw, kernel;
         float ms;
     };
     std::vector<Cand> cands;
-    cands.push_back({0, 0, 0, 0, 0, 0, 0, 0.f});  // library default
+    cands.push_back({0, 0, 0, 0, 0, 0, 0, 0, 0.f});  // library default
     const uint32_t gmax = t->dev.g_len ? 2u : 1u;
     for (uint32_t nw : {16u, 24u})
         for (uint32_t k = t->kmin; k <= t->kmax; k++)
@@ -130,9 +160,17 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
                 for (uint32_t masks = 1; masks <= 2; masks++) {
                     for (uint32_t gram = 1; gram <= gmax; gram++)
                         for (uint32_t copies = 32; copies >= 1; copies >>= 1)
-                            cands.push_back({var, k, copies, masks, gram, 1, nw, 0.f});
-                    if (t->dev.B[k]) cands.push_back({var, k, 1, masks, 1, 2, nw, 0.f});
+                            cands.push_back({var, k, copies, masks, gram, 1, nw, 1, 0.f});
+                    if (t->dev.B[k]) cands.push_back({var, k, 1, masks, 1, 2, nw, 1, 0.f});
                 }
+    // the register-staged kernel (8-bit symbols): its CTA width is fixed
+    if (t->dev.bps == 8)
+        for (uint32_t k = t->kmin; k <= t->kmax; k++)
+            for (uint32_t var = 1; var <= 2; var++)
+                for (uint32_t masks = 1; masks <= 2; masks++)
+                    for (uint32_t gram = 1; gram <= gmax; gram++)
+                        for (uint32_t copies = 16; copies >= 1; copies >>= 1)
+                            cands.push_back({var, k, copies, masks, gram, 1, 0, 2, 0.f});
 
     uint64_t ws_max = 0;
     std::vector<Cand> ok;
@@ -146,6 +184,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.gram_filter = c.gram;
         o.prefix_bytes = c.bytes;
         o.warps_per_cta = c.nw;
+        o.scan_kernel = c.kernel;
         uint64_t b = 0;
         if (pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b) != PFAC_OK) continue;
         ws_max = std::max(ws_max, b);
@@ -155,13 +194,17 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     void *ws = nullptr, *small = nullptr;
     cudaError_t e = cudaMalloc(&ws, ws_max ? ws_max : 256);
     if (e == cudaSuccess) e = cudaMalloc(&small, 256);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventCreate(&e2);
+    if (e == cudaSuccess) e = cudaEventCreate(&e3);
     if (e != cudaSuccess) {
         cudaFree(ws);
         cudaFree(small);
         if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e2) cudaEventDestroy(e2);
         cudaGetLastError();
         return set_error(PFAC_ENOMEM, "pfac_autotune: %s", cudaGetErrorString(e));
     }
@@ -178,6 +221,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.gram_filter = c.gram;
         o.prefix_bytes = c.bytes;
         o.warps_per_cta = c.nw;
+        o.scan_kernel = c.kernel;
         uint64_t b = 0;
         pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b);
         // warm-up, then the median of three timed scans
@@ -187,15 +231,21 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
             clear_error();
             continue;
         }
+        // both launches of the scan kernel: the scan pass and the emit pass
         o.ev_scan_begin = e0;
         o.ev_scan_end = e1;
+        o.ev_emit_begin = e2;
+        o.ev_emit_end = e3;
         float t3[3];
         bool good = true;
         for (int r = 0; r < 3 && good; r++) {
             rc = pfac_match_async(t, d_sample, n_bytes, d_seg_offsets, n_segments, nullptr, 0,
                                   d_cnt, d_st, ws, b, &o, st);
-            if (rc == PFAC_OK && cudaEventSynchronize(e1) == cudaSuccess)
-                cudaEventElapsedTime(&t3[r], e0, e1);
+            float ms_scan = 0.f, ms_emit = 0.f;
+            if (rc == PFAC_OK && cudaEventSynchronize(e3) == cudaSuccess &&
+                cudaEventElapsedTime(&ms_scan, e0, e1) == cudaSuccess &&
+                cudaEventElapsedTime(&ms_emit, e2, e3) == cudaSuccess)
+                t3[r] = ms_scan + ms_emit;
             else
                 good = false;
         }
@@ -212,6 +262,8 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    cudaEventDestroy(e3);
     cudaFree(ws);
     cudaFree(small);
     if (e != cudaSuccess) return set_error(PFAC_ECUDA, "pfac_autotune: %s", cudaGetErrorString(e));
@@ -231,6 +283,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         t->tuned_gram = best.gram;
         t->tuned_bytes = best.bytes;
         t->tuned_nw = best.nw;
+        t->tuned_kernel = best.kernel;
     }
     res.variant = best.var;
     res.prefix_depth = best.k;
@@ -239,12 +292,14 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     res.gram_filter = best.gram;
     res.prefix_bytes = best.bytes;
     res.warps_per_cta = best.nw;
+    res.scan_kernel = best.kernel;
     res.scan_ms = best.ms;
     if (cache_path && best.var) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s %u %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k,
-                    best.copies, best.masks, best.gram, best.bytes, best.nw, best.ms);
+            fprintf(f, "%s %u %u %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k,
+                    best.copies, best.masks, best.gram, best.bytes, best.nw, best.kernel,
+                    best.ms);
             fclose(f);
         }
     }

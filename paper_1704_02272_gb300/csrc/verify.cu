@@ -137,6 +137,8 @@ extern "C" int pfac_verify(const pfac_table *t, const uint8_t *d_input, uint64_t
     if (!t || !d_count || !d_seg_offsets || (n_keys && (!d_keys || !d_out)))
         return set_error(PFAC_EINVAL, "pfac_verify: NULL argument");
     if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_verify: table was built host-only");
+    const int drc = check_table_device(t, cuda_stream, "pfac_verify");
+    if (drc) return drc;
     if (!t->dev.trunc || !t->dev.pat)
         return set_error(PFAC_EINVAL, "pfac_verify: the table was not built with truncate_depth");
     if (n_keys && d_keys == d_out)

@@ -110,15 +110,23 @@ def test_empty_pattern_set_builds():
 
 
 def test_host_only_table_cannot_match():
-    import torch
+    # straight through the C ABI: a host-only table is rejected before any
+    # pointer is used or any CUDA call is made
+    import ctypes
+    lib = pfac.binding.LIB
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced
     with host_table([b"ab"], 256) as t:
-        with pytest.raises(pfac.PfacError) as ei:
-            z = torch.zeros(16, dtype=torch.uint8)
-            s = torch.tensor([0, 16], dtype=torch.int64)
-            pfac.match_async(t, z, s, torch.zeros(4, dtype=torch.int64),
-                             torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int32),
-                             torch.zeros(1 << 16, dtype=torch.uint8), stream=0)
-        assert ei.value.status == -1
+        o = pfac.binding.MatchOpts()
+        rc = lib.pfac_match_async(t.handle, fake, 16, fake, 1, fake, 4, fake, fake, fake,
+                                  1 << 16, ctypes.byref(o), None)
+        assert rc == -1
+        rc = lib.pfac_match_noalloc(t.handle, fake, 16, fake, 1, fake, 4, fake, fake,
+                                    ctypes.byref(o), None)
+        assert rc == -1
+        n = ctypes.c_uint64()
+        rc = lib.pfac_match(t.handle, fake, 16, fake, 1, fake, 4, ctypes.byref(n),
+                            ctypes.byref(o), None)
+        assert rc == -1
 
 
 def gram_strings_brute(patterns, g, bps):
@@ -183,3 +191,35 @@ def test_match_checks_its_tensors_before_the_library():
             pfac.match(t, z, s)  # host text: the device path needs device memory
         with pytest.raises(ValueError):
             pfac.match_into(t, z, s.to(torch.int32), torch.zeros(4, dtype=torch.int64))
+
+
+@pytest.mark.parametrize("fn", ["match_async", "match_noalloc"])
+def test_async_entry_points_check_their_tensors(fn):
+    # a wrongly typed or strided tensor would make the kernels read or write
+    # past a smaller buffer: the binding refuses it before the library
+    import torch
+    with host_table([b"ab"], 256) as t:
+        z = torch.zeros(16, dtype=torch.uint8)
+        s = torch.tensor([0, 16], dtype=torch.int64)
+        out = torch.zeros(4, dtype=torch.int64)
+        cnt = torch.zeros(1, dtype=torch.int64)
+        st = torch.zeros(1, dtype=torch.int32)
+        ws = [torch.zeros(1 << 16, dtype=torch.uint8)] if fn == "match_async" else []
+        call = getattr(pfac, fn)
+        bad = [
+            (z, s.to(torch.int32), out, cnt, st),          # 4-byte offsets
+            (z, s, out.to(torch.int32), cnt, st),          # 4-byte keys
+            (z, s, out, cnt.to(torch.int32), st),          # 4-byte count
+            (z, s, out, cnt, st.to(torch.int64)),          # 8-byte status
+            (z, s, torch.zeros(8, dtype=torch.int64)[::2], cnt, st),  # strided output
+            (z.to(torch.int16), s, out, cnt, st),          # wide text
+        ]
+        for args in bad:
+            with pytest.raises(ValueError, match="contiguous"):
+                call(t, *args, *ws)
+        if fn == "match_async":
+            with pytest.raises(ValueError, match="contiguous"):
+                call(t, z, s, out, cnt, st, ws[0].to(torch.int32))
+        # well-formed host tensors: refused because the path needs device memory
+        with pytest.raises(ValueError, match="CUDA device"):
+            call(t, z, s, out, cnt, st, *ws)
