@@ -255,14 +255,14 @@ def user_options(args):
     for key, val in (("variant", args.variant), ("prefix_depth", args.prefix_depth),
                      ("bitmap_copies", args.copies), ("child_masks", args.masks),
                      ("gram_filter", args.gram), ("prefix_bytes", args.bytes),
-                     ("warps_per_cta", args.warps)):
+                     ("warps_per_cta", args.warps), ("scan_kernel", args.kernel)):
         if val:
             user_opt[key] = val
     return user_opt
 
 
 def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_steps=True,
-              gpu_index=0, barrier=None):
+              gpu_index=0, barrier=None, call_opt=None):
     """Times one workload: K steps of one pfac_match_async over the whole
     input (the captured graph of the call, replayed), the scan kernel's two
     launches (scan pass, emit pass) by events on their stream, and the
@@ -270,6 +270,9 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
     objects the caller needs for the end-to-end leg."""
     N = w.n_bytes
     S = len(w.seg_offsets) - 1
+    # the bytes this call's walks start at (a shard's own share; the rest of
+    # its text is the read halo)
+    n_starts = call_opt["starts_end"] if call_opt and call_opt.get("starts_end") else N
     text = torch.from_numpy(w.text).to(dev)
     seg = torch.from_numpy(w.seg_offsets.astype(np.int64)).to(dev)
     t0 = time.perf_counter()
@@ -290,9 +293,10 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
         cut = int(np.searchsorted(offs, nb, side="left"))  # offsets below nb
         s_offs = torch.from_numpy(np.concatenate([offs[:cut], [nb]])).to(dev)
         tune = pfac.autotune(table, text[:nb], s_offs)
+    call_opt = call_opt or {}
     # the untimed reference call runs the plan the steps run
     with torch.cuda.stream(stream):
-        keys = pfac.match(table, text, seg, stream=stream, **user_opt)
+        keys = pfac.match(table, text, seg, stream=stream, **user_opt, **call_opt)
         stream.synchronize()
     n_match = keys.numel()
     cap = n_match + 1024
@@ -314,6 +318,7 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
 
     def step(i=None, tbl=table):
         opt = dict(user_opt) if tbl is table else {}
+        opt.update(call_opt)
         if i is not None:
             opt["scan_events"] = (sc_b[i], sc_e[i])
             opt["emit_events"] = (em_b[i], em_e[i])
@@ -368,7 +373,7 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
     assert int(cnt.item()) == n_match
 
     # uncompressed table on the same GPU, same input
-    dk = pfac.match(dense, text, seg, stream=stream)
+    dk = pfac.match(dense, text, seg, stream=stream, **call_opt)
     stream.synchronize()
     exact = bool(torch.equal(dk, keys))
     del dk
@@ -382,7 +387,7 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
         step(tbl=dense)
     d1.record(stream)
     stream.synchronize()
-    dense_gbps = 8.0 * N * K / (d0.elapsed_time(d1) / 1e3) / 1e9
+    dense_gbps = 8.0 * n_starts * K / (d0.elapsed_time(d1) / 1e3) / 1e9
 
     hbm_peak, peak_kind = peaks()
     # algorithmic bytes of the scan kernel's launches in one step: every input
@@ -392,7 +397,7 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
     # between them read the input and write those bytes
     pos = keys >> 24
     matched_positions = int(torch.unique_consecutive(pos).numel()) if n_match else 0
-    alg_bytes = N + 8 * matched_positions
+    alg_bytes = n_starts + 8 * matched_positions
     scan_avg_ms = sum(scan_ms) / K
     emit_avg_ms = sum(emit_ms) / K
     kern_ms = scan_avg_ms + emit_avg_ms
@@ -406,7 +411,7 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
                 "alg_bytes_per_launch": alg_bytes,
                 "scan_pass_ms": round(scan_avg_ms, 4), "emit_pass_ms": round(emit_avg_ms, 4)}
     cell = {
-        "value": round(8.0 * N * K / (total_ms / 1e3) / 1e9, 3), "unit": "Gbps",
+        "value": round(8.0 * n_starts * K / (total_ms / 1e3) / 1e9, 3), "unit": "Gbps",
         "ms_per_step": round(total_ms / K, 4),
         "p50_ms": round(statistics.median(step_ms), 4),
         "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
@@ -426,6 +431,20 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
     return cell, ctx
 
 
+def shard_workload(full, world, rank):
+    """One job split by start position: every rank builds the same workload,
+    keeps its share plus a read halo of max_len - 1 bytes, and reports global
+    positions (starts_end / position_base).  Returns the rank's workload, its
+    match options and its shard."""
+    from paper_1704_02272_gb300 import shard as shard_mod
+    sh = shard_mod.plan(full.n_bytes, full.seg_offsets, world, full.max_len)[rank]
+    if sh.stop <= sh.start:
+        raise SystemExit(f"rank {rank} has no share of a {full.n_bytes}-byte input")
+    w = workloads.Workload(f"{full.name}-shard{rank}", full.sigma, full.patterns,
+                           np.ascontiguousarray(full.text[sh.start:sh.read_end]), sh.seg)
+    return w, {"starts_end": sh.stop - sh.start, "position_base": sh.start}, sh
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_setup(args.gpus)
@@ -433,7 +452,16 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     import paper_1704_02272_gb300 as pfac
 
-    w = load_workload(args.workload, rank)
+    from paper_1704_02272_gb300 import shard as shard_mod
+    strong = world > 1 and args.scaling == "strong"
+    call_opt, sh = None, None
+    if strong:
+        full = load_workload(args.workload, 0)
+        w, call_opt, sh = shard_workload(full, world, rank)
+        N_job, N_rank = full.n_bytes, sh.stop - sh.start
+    else:
+        w = load_workload(args.workload, rank)
+        N_job, N_rank = w.n_bytes * world, w.n_bytes
     N = w.n_bytes
     S = len(w.seg_offsets) - 1
     stream = torch.cuda.Stream(device=dev)
@@ -442,14 +470,30 @@ def run_ours(args):
 
     barrier = torch.distributed.barrier if world > 1 else None
     cell, ctx = time_cell(pfac, torch, w, dev, stream, args, user_opt, args.workload,
-                          gpu_index=local, barrier=barrier)
+                          gpu_index=local, barrier=barrier, call_opt=call_opt)
     clk = cell.pop("clocks")
     total_ms = ctx["total_ms"]
     if world > 1:
         tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(tt.item())
-    value = 8.0 * N * world * K / (total_ms / 1e3) / 1e9
+    value = 8.0 * N_job * K / (total_ms / 1e3) / 1e9
+    shard_line = None
+    if strong:
+        # after the timed region: the merge (one gather of counts and lists,
+        # concatenated in rank order), checked on rank 0 against one
+        # unsharded call over the whole input
+        merged = shard_mod.gather(ctx["keys"])
+        shard_line = {"ranks": world, "share_bytes": N_rank, "halo_bytes": N - N_rank,
+                      "merged_matches": int(merged.numel())}
+        if rank == 0:
+            ft = torch.from_numpy(full.text).to(dev)
+            fs = torch.from_numpy(full.seg_offsets.astype(np.int64)).to(dev)
+            whole = pfac.match(ctx["table"], ft, fs, **user_opt)
+            torch.cuda.synchronize()
+            shard_line["bit_exact_vs_unsharded"] = bool(torch.equal(whole, merged))
+            del ft, fs, whole
+        del merged
     table, keys, n_match, cap = ctx["table"], ctx["keys"], ctx["n_match"], ctx["cap"]
     text, seg = ctx["text"], ctx["seg"]
 
@@ -486,8 +530,13 @@ def run_ours(args):
     n_chunks = (N + chunk - 1) // chunk
 
     def e2e_step():
-        return pfac.match_host(table, host_in, host_seg, host_out, chunk_bytes=chunk,
-                               stream=stream, **user_opt)
+        n = pfac.match_host(table, host_in, host_seg, host_out, chunk_bytes=chunk,
+                            stream=stream, **user_opt)
+        if sh is not None:
+            # the shard's own starts, at global positions (its halo's starts
+            # belong to the next rank)
+            return int(shard_mod.own(host_out[:n].numpy().view(np.uint64), sh).size)
+        return n
 
     for _ in range(max(1, W)):
         e2e_step()
@@ -504,7 +553,7 @@ def run_ours(args):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(tt.item())
     halo = (n_chunks - 1) * max(w.max_len - 1, 0)
-    e2e = {"value": round(8.0 * N * world / e2e_s / 1e9, 3), "unit": "Gbps",
+    e2e = {"value": round(8.0 * N_job / e2e_s / 1e9, 3), "unit": "Gbps",
            "h2d_bytes_per_step": int(N + halo + 8 * (S + 1 + 2 * n_chunks)),
            "d2h_bytes_per_step": int(8 * e2e_n + 16 * n_chunks),
            "call": "pfac_match_host", "chunk_bytes": chunk}
@@ -516,7 +565,7 @@ def run_ours(args):
     # the cell the 50%-of-HBM target is judged on: alphabet 256, 1,000
     # patterns, 512 MiB (timed the same way, on rank 0's GPU only)
     extra = {}
-    if not args.no_sweep_cell and args.workload != "sweep-256-1000" and rank == 0:
+    if not args.no_sweep_cell and args.workload != "sweep-256-1000" and world == 1:
         wc = load_workload("sweep-256-1000", 0)
         c2, cx2 = time_cell(pfac, torch, wc, dev, stream, args, user_opt, "sweep-256-1000")
         c2["config"] = {"workload": "sweep cell: alphabet 256, 1,000 patterns U[4,64], 512 MiB "
@@ -532,9 +581,13 @@ def run_ours(args):
     line = {
         "metric": METRIC,
         "value": round(value, 3), "unit": "Gbps", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": round(total_ms / K, 4), "higher_is_better": True,
+        "scaling": "strong" if strong else "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": dict(base_config(w, args), prefix_depth=cell["scan_plan"]["prefix_depth"],
+        "config": dict(base_config(w if not strong else full, args),
+                       parallelism=(f"{world} start-range shards of one input" if strong else
+                                    f"{world} independent inputs" if world > 1 else "1 GPU"),
+                       prefix_depth=cell["scan_plan"]["prefix_depth"],
                        variant=args.variant or "default", bitmap_copies=args.copies or "auto",
                        autotuned=cell.pop("autotuned"), scan_plan=cell.pop("scan_plan"),
                        cuda_graph=cell.pop("cuda_graph")),
@@ -542,6 +595,7 @@ def run_ours(args):
         "matches": cell["matches"], "matched_position_frac": cell["matched_position_frac"],
         "table_bytes": cell["table_bytes"], "dense": cell["dense"],
         "prefix_matching": prefix_line,
+        "shards": shard_line,
         "build_s": cell["build_s"],
         "roofline": roofline,
         "e2e": e2e,
@@ -551,7 +605,7 @@ def run_ours(args):
     }
     line.update(extra)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        line["cpu_baseline"] = cpu_baseline(w if not strong else full)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -650,6 +704,10 @@ def main():
                     help="dram bytes per scan launch from an ncu capture of the current kernel sources")
     ap.add_argument("--ref-sample-mib", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
+                    help="with several GPUs: strong = one input split by start position "
+                         "(shards with a read halo, merged after the timed region); weak = "
+                         "an input of the full size per GPU")
     ap.add_argument("--no-sweep-cell", action="store_true",
                     help="skip the alphabet-256 x 1,000-pattern cell timed after the main "
                          "workload")
@@ -660,6 +718,9 @@ def main():
     ap.add_argument("--gram", type=int, default=0, help="gram filter first stage: 1 off, 2 on")
     ap.add_argument("--bytes", type=int, default=0, help="prefix bytes first stage: 1 off, 2 on")
     ap.add_argument("--warps", type=int, default=0, help="scan-kernel warps per CTA: 16 or 24")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="scan kernel: 1 queued (input staged in shared memory), 2 register-staged "
+                         "(alphabets of 129-256 symbols)")
     ap.add_argument("--truncate", type=int, default=0,
                     help="prefix matching (Section 2.4): tables hold the patterns cut to this "
                          "many symbols; the timed step yields candidates, verified after")

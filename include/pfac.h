@@ -149,6 +149,24 @@ typedef struct {
                               256 symbols; excludes prefix_bytes = 2 and
                               warps_per_cta) */
     uint32_t reserved_scan;
+    /* Testing aids for the failure path of the queued kernel's bounded waits
+     * (they change no result of a call that does not set them): */
+    uint32_t test_wait_limit_us; /* 0 = the default bound of every wait on a
+                              bulk copy (4 s); else this many microseconds */
+    uint32_t test_withhold_slice; /* 0 = off; s > 0: the copy of the 512-byte
+                              slice s - 1 is never issued, so the wait for it
+                              gives up after the bound, the kernel records
+                              PFAC_ETIMEOUT (pfac_match returns it) and the
+                              device stays usable */
+    uint32_t records_per_slice; /* match records kept per 512-byte slice by the
+                              scan pass (compressed layout): 0 = library
+                              choice (512 when the pattern set makes more
+                              than 8 matched positions per slice likely on
+                              uniform text, else 32, or the autotuner's), 32,
+                              or 512 (every position: no slice is ever scanned
+                              a second time; 8 bytes of workspace per input
+                              byte) */
+    uint32_t reserved_rec;
 } pfac_match_opts;
 
 typedef struct {
@@ -217,6 +235,8 @@ typedef struct {
     uint32_t prefix_bytes;   /* 1 = off, 2 = on */
     uint32_t warps_per_cta;  /* warps per CTA of the scan kernel (0: uncompressed) */
     uint32_t scan_kernel;    /* 1 = queued, 2 = register-staged (0: uncompressed) */
+    uint32_t records_per_slice; /* 32 or 512 (compressed layout) */
+    uint32_t reserved;
 } pfac_plan_info;
 int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts, pfac_plan_info *out);
 
@@ -381,6 +401,7 @@ typedef struct {
     uint32_t prefix_bytes; /* 1 = off, 2 = on */
     uint32_t warps_per_cta;
     uint32_t scan_kernel;  /* 1 = queued, 2 = register-staged */
+    uint32_t records_per_slice;
 } pfac_tune_result;
 
 int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,

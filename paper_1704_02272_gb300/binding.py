@@ -51,7 +51,9 @@ class MatchOpts(ctypes.Structure):
                 ("prefix_bytes", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
                 ("starts_end", ctypes.c_uint64), ("position_base", ctypes.c_uint64),
                 ("ev_emit_begin", ctypes.c_void_p), ("ev_emit_end", ctypes.c_void_p),
-                ("scan_kernel", ctypes.c_uint32), ("reserved_scan", ctypes.c_uint32)]
+                ("scan_kernel", ctypes.c_uint32), ("reserved_scan", ctypes.c_uint32),
+                ("test_wait_limit_us", ctypes.c_uint32), ("test_withhold_slice", ctypes.c_uint32),
+                ("records_per_slice", ctypes.c_uint32), ("reserved_rec", ctypes.c_uint32)]
 
 
 class TableInfo(ctypes.Structure):
@@ -73,7 +75,7 @@ class TuneResult(ctypes.Structure):
                 ("scan_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
                 ("from_cache", ctypes.c_int), ("gram_filter", ctypes.c_uint32),
                 ("prefix_bytes", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
-                ("scan_kernel", ctypes.c_uint32)]
+                ("scan_kernel", ctypes.c_uint32), ("records_per_slice", ctypes.c_uint32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -81,7 +83,8 @@ class PlanInfo(ctypes.Structure):
                 ("bitmap_copies", ctypes.c_uint32), ("child_masks", ctypes.c_uint32),
                 ("gram_filter", ctypes.c_uint32), ("gram_bits", ctypes.c_uint32),
                 ("smem_bytes", ctypes.c_uint32), ("prefix_bytes", ctypes.c_uint32),
-                ("warps_per_cta", ctypes.c_uint32), ("scan_kernel", ctypes.c_uint32)]
+                ("warps_per_cta", ctypes.c_uint32), ("scan_kernel", ctypes.c_uint32),
+                ("records_per_slice", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -179,12 +182,15 @@ KERNEL_QUEUED, KERNEL_REGISTER = 1, 2
 
 def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,
           gram_filter=0, prefix_bytes=0, starts_end=0, position_base=0, warps_per_cta=0,
-          scan_kernel=0, scan_events=None, emit_events=None):
+          scan_kernel=0, scan_events=None, emit_events=None, test_wait_limit_us=0,
+          test_withhold_slice=0, records_per_slice=0):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
     o.bitmap_copies, o.child_masks, o.gram_filter = bitmap_copies, child_masks, gram_filter
     o.prefix_bytes, o.starts_end, o.position_base = prefix_bytes, starts_end, position_base
     o.warps_per_cta, o.scan_kernel = warps_per_cta, scan_kernel
+    o.test_wait_limit_us, o.test_withhold_slice = test_wait_limit_us, test_withhold_slice
+    o.records_per_slice = records_per_slice
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event
@@ -276,7 +282,7 @@ def plan(table: Table, **opt) -> dict:
     o = _opts(**opt)
     r = PlanInfo()
     _check(LIB.pfac_match_plan(table.handle, ctypes.byref(o), ctypes.byref(r)))
-    return {f: getattr(r, f) for f, _ in PlanInfo._fields_}
+    return {f: getattr(r, f) for f, _ in PlanInfo._fields_ if f != "reserved"}
 
 
 def match_host(table: Table, text: torch.Tensor, seg: torch.Tensor, out: torch.Tensor,

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <string>
 #include <vector>
@@ -120,6 +121,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         std::vector<Pat> pats(n_patterns);
         uint32_t min_len = n_patterns ? 0xFFFFFFFFu : 0, max_len = 0;
         uint64_t total = 0;
+        double match_density = 0.0;
         for (uint32_t i = 0; i < n_patterns; i++) {
             uint32_t L = lengths[i];
             if (L == 0) return set_error(PFAC_EINVAL, "pfac_build: pattern %u is empty", i);
@@ -137,6 +139,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
             min_len = std::min(min_len, L);
             max_len = std::max(max_len, L);
             total += L;
+            // expected matches per position of uniform text over the alphabet
+            match_density += std::pow((double)sigma, -(double)L);
         }
         if (total >= 0x7FFFFFF0ull)
             return set_error(PFAC_EINVAL, "pfac_build: %llu pattern bytes exceed 2^31",
@@ -633,6 +637,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         t->kmax = dense ? 0 : kmax;
         t->kmin = dense ? 0 : kmin;
 
+        t->match_density = match_density;
         pfac_table_info_t &I = t->info;
         I.alphabet_size = sigma;
         I.n_patterns = n_patterns;

@@ -100,7 +100,14 @@ struct MatchParams {
     uint64_t pos_base;    // added to every reported position
     uint32_t tbl_b_words; // prefix bytes in shared memory as the first stage (0 = not used)
     uint32_t dense_rows;  // dense layout: states whose rows live in shared memory
+    // testing aids of the queued kernel: the bound of its waits, and a slice
+    // whose copy is never issued (UNIT_NONE: none), so that the wait for it
+    // runs out
+    uint64_t wait_limit_ns;
+    uint32_t withhold_unit;
 };
+
+constexpr uint32_t UNIT_NONE = 0xFFFFFFFFu;
 
 // ------------------------------------------------------------ PTX helpers --
 
@@ -145,14 +152,15 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Waits for the phase of `parity` to complete; gives up after WAIT_LIMIT_NS.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// Waits for the phase of `parity` to complete; gives up after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns = WAIT_LIMIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; it++) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63) == 63) {
-            if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+            if (global_ns() - t0 > limit_ns) return false;
             __nanosleep(128);
         }
     }

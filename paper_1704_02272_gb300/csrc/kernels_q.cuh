@@ -803,8 +803,10 @@ __device__ __forceinline__ int append_slice(const MatchParams &P, QEntry *q, uin
 }
 
 // Resolves every survivor of one slice in quarters of 8 lanes (at most 128
-// candidates each).  emit == 0: returns the slice's key count.  emit == 1:
-// writes the slice's keys at key_off[unit] and returns the count.
+// candidates each).  emit == 0: returns the slice's key count, and with
+// record space for every position of the slice (P.unit_cap >= SLICE) also
+// writes its records in position order, their number to *n_recs.  emit ==
+// 1: writes the slice's keys at key_off[unit] and returns the count.
 template <int W, int BPS, int VAR>
 __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *q, uint32_t cand,
                                                   uint32_t rootm, const uint32_t (&bs)[BPS + 1],
@@ -813,8 +815,11 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
                                                   bool general_lims, uint64_t ustart,
                                                   uint32_t rem, const uint32_t *Fs,
                                                   const uint32_t *Cs, const uint32_t *Es,
-                                                  const uint32_t *Ms, uint32_t lane, bool emit) {
+                                                  const uint32_t *Ms, uint32_t lane, bool emit,
+                                                  uint32_t *n_recs = nullptr) {
     uint64_t keys = 0;
+    uint32_t nrec = 0;
+    const bool records = !emit && P.unit_cap >= (uint32_t)SLICE;
     const uint64_t obase = emit ? P.key_off[unitid] : 0;
     for (int qt = 0; qt < 4; qt++) {
         AppendState ast{0u, 0u, false};
@@ -833,6 +838,14 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
         __syncwarp();
 #pragma unroll
         for (int u = 0; u < QU; u++) {
+            if (records) {
+                // one record per matched position, ranked in position order
+                const uint32_t b = __ballot_sync(0xFFFFFFFFu, fin[u] != 0);
+                if (fin[u])
+                    P.recs[(size_t)unitid * P.unit_cap + nrec + __popc(b & ((1u << lane) - 1u))] =
+                        ((uint64_t)(pos[u] & 0x3FFu) << 32) | fin[u];
+                nrec += __popc(b);
+            }
             const uint32_t L = fin[u] ? fin_len(P.T.pool, fin[u]) : 0u;
             uint32_t inc = L;
 #pragma unroll
@@ -852,6 +865,7 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
         }
         __syncwarp();
     }
+    if (n_recs) *n_recs = nrec;
     return keys;
 }
 
@@ -918,6 +932,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const MatchParams P, const
         const uint64_t avail = P.n - start;
         const uint32_t bytes = (avail < (uint64_t)QSTAGE ? (uint32_t)avail : (uint32_t)QSTAGE) & ~15u;
         uint64_t *bar = &A.bar[i % QRING];
+        if (u == P.withhold_unit) return;  // testing: this stage never completes
         mbar_arrive_expect_tx(bar, bytes);
         if (bytes) bulk_g2s(A.ring[i % QRING], P.in + start, bytes, bar);
     };
@@ -999,7 +1014,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const MatchParams P, const
         }
 
         const uint32_t s = i % QRING;
-        if (!mbar_wait_bounded(&A.bar[s], (i / QRING) & 1)) {
+        if (!mbar_wait_bounded(&A.bar[s], (i / QRING) & 1, P.wait_limit_ns)) {
             if (lane == 0) atomicOr(&P.hdr->status, ST_TIMEOUT);
             failed = true;
             i_fail = i;
@@ -1041,16 +1056,23 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const MatchParams P, const
                 if (ar == AP_DONE) qn += ast.kept;
             }
             if (ar == AP_OVER) {
-                // more survivors than the (now empty) queue holds: count now,
-                // emit later
+                // more survivors than the (now empty) queue holds: resolved
+                // now in quarters; with record space for every position the
+                // records are written now, otherwise the keys are counted now
+                // and written by the emit pass
+                uint32_t nrec = 0;
                 const uint64_t keys = resolve_slice<W, BPS, VAR>(P, A.q, cand, rootm, bs, sb,
                                                                  staged, u, lima, limb,
                                                                  general_lims, ustart, rem, Fs,
-                                                                 Cs, Es, Ms, lane, false);
+                                                                 Cs, Es, Ms, lane, false, &nrec);
                 if (lane == 0) {
-                    P.tile_m[u] = UNIT_OVF;
                     P.tile_k[u] = keys;
-                    P.ovf_list[atomicAdd(&P.hdr->ovf_count, 1u)] = u;
+                    if (P.unit_cap >= (uint32_t)SLICE) {
+                        P.tile_m[u] = nrec;
+                    } else {
+                        P.tile_m[u] = UNIT_OVF;
+                        P.ovf_list[atomicAdd(&P.hdr->ovf_count, 1u)] = u;
+                    }
                 }
             }
         }
@@ -1065,7 +1087,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const MatchParams P, const
         // the stages of units i_fail .. i_fail + QRING - 1
         for (uint32_t i = i_fail; i < i_fail + QRING; i++) {
             if (gw + i * gstride >= n_units) break;
-            mbar_wait_bounded(&A.bar[i % QRING], (i / QRING) & 1);
+            mbar_wait_bounded(&A.bar[i % QRING], (i / QRING) & 1, P.wait_limit_ns);
         }
     }
 }

@@ -72,33 +72,44 @@ __device__ __forceinline__ uint32_t r_window(const uint32_t (&w)[5], uint32_t j)
     return __funnelshift_r(lo, hi, 8 * (j & 3));
 }
 
-// First stage of one slice for the lane's 16 positions: bit j of the result
-// is set when position j's window passes the filter.  amask selects the
-// word-index bits of the address; gm and gsh are the gram hash's multiplier
-// and shift.
+// Word address of position window t in the first-stage table: for the
+// prefix bitmap the index's bits above the bit number (t >> 5) placed at bit
+// REP + 2; for the gram filter the top bits of the hash t * gm (table.h),
+// taken by a high multiply by gmh = 2^(word bits + REP + 2) so that the
+// shift runs on the multiply pipe.  amask keeps the word bits, c4 selects
+// the lane's copy.
 template <int REP, int GRAM>
-__device__ __forceinline__ uint32_t r_first_stage(const uint32_t (&w)[5], const uint8_t *Tb,
-                                                  uint32_t c4, uint32_t amask, uint32_t gm,
-                                                  uint32_t gsh) {
-    uint32_t acc = 0;
+__device__ __forceinline__ uint32_t r_addr(uint32_t t, uint32_t c4, uint32_t amask, uint32_t gm,
+                                           uint32_t gmh) {
+    if (GRAM) return (__umulhi(t * gm, gmh) & amask) | c4;
+    return ((REP >= 3 ? (t << (REP - 3)) : (t >> (3 - REP))) & amask) | c4;
+}
+
+// First stage of the two slices of a step for the lane's 16 positions in
+// each (their 32 lookups independent, so they overlap): bit j of sa / sb is
+// set when position j's window passes the filter.
+template <int REP, int GRAM>
+__device__ __forceinline__ void r_first_stage2(const uint32_t (&wa)[5], const uint32_t (&wb)[5],
+                                               const uint8_t *Tb, uint32_t c4, uint32_t amask,
+                                               uint32_t gm, uint32_t gmh, uint32_t &sa,
+                                               uint32_t &sb) {
+    uint32_t acc_a = 0, acc_b = 0;
 #pragma unroll
     for (int j = 0; j < 16; j++) {
-        const uint32_t t =
-            (j & 3) ? __funnelshift_r(w[j >> 2], w[(j >> 2) + 1], 8 * (j & 3)) : w[j >> 2];
-        uint32_t a;
-        if (GRAM) {
-            // word = top bits of t * gm (table.h), placed at bit REP + 2
-            a = (((t * gm) >> gsh) & amask) | c4;
-        } else {
-            // word = t >> 5 (the index's bits above the bit number), placed
-            // at bit REP + 2; the bits above the index fall outside amask
-            a = ((REP >= 3 ? (t << (REP - 3)) : (t >> (3 - REP))) & amask) | c4;
-        }
-        const uint32_t word = *reinterpret_cast<const uint32_t *>(Tb + a);
-        // bit t & 31 of the word to bit 0, then into the top of acc
-        acc = __funnelshift_r(acc, __funnelshift_r(word, word, t), 1);
+        const uint32_t ta =
+            (j & 3) ? __funnelshift_r(wa[j >> 2], wa[(j >> 2) + 1], 8 * (j & 3)) : wa[j >> 2];
+        const uint32_t tb =
+            (j & 3) ? __funnelshift_r(wb[j >> 2], wb[(j >> 2) + 1], 8 * (j & 3)) : wb[j >> 2];
+        const uint32_t xa = *reinterpret_cast<const uint32_t *>(
+            Tb + r_addr<REP, GRAM>(ta, c4, amask, gm, gmh));
+        const uint32_t xb = *reinterpret_cast<const uint32_t *>(
+            Tb + r_addr<REP, GRAM>(tb, c4, amask, gm, gmh));
+        // bit t & 31 of each word to bit 0, then into the top of acc
+        acc_a = __funnelshift_r(acc_a, __funnelshift_r(xa, xa, ta), 1);
+        acc_b = __funnelshift_r(acc_b, __funnelshift_r(xb, xb, tb), 1);
     }
-    return acc >> 16;
+    sa = acc_a >> 16;
+    sb = acc_b >> 16;
 }
 
 // Second stage of one candidate whose window (bytes j .. j + 3) is t:
@@ -266,13 +277,11 @@ __device__ __forceinline__ void r_append(const MatchParams &P, RWarpArea &A, RQu
     }
 }
 
-// One slice: window masks, first stage, second stage, queue.
-template <int W, int REP, int GRAM, int VAR>
+// One slice after its first stage (surv): window masks, second stage, queue.
+template <int W, int GRAM, int VAR>
 __device__ __forceinline__ void r_slice(const MatchParams &P, RWarpArea &A, RQueue &Q,
-                                        const uint32_t (&w)[5], bool halo_ok, uint32_t u,
-                                        const uint8_t *Tb,
-                                        uint32_t c4, uint32_t amask, uint32_t gm, uint32_t gsh,
-                                        const uint32_t *Fs, const uint32_t *Cs,
+                                        const uint32_t (&w)[5], uint32_t surv, bool halo_ok,
+                                        uint32_t u, const uint32_t *Fs, const uint32_t *Cs,
                                         const uint32_t *Es, const uint32_t *Ms, uint32_t lane) {
     const uint64_t ustart = (uint64_t)u << SLICE_SHIFT;
     const uint64_t remain = P.n - ustart;
@@ -291,7 +300,6 @@ __device__ __forceinline__ void r_slice(const MatchParams &P, RWarpArea &A, RQue
     if (P.n_seg > 1) r_seg_limits(P, u, ustart, rem, lane, lima, limb, general);
     const uint32_t kf = P.kf;
     const uint32_t p0 = lane * QBPT;
-    uint32_t surv = r_first_stage<REP, GRAM>(w, Tb, c4, amask, gm, gsh);
     uint32_t fv = 0xFFFFu, ex = 0xFFFFu;
     const uint32_t lim0 = lima < staged ? lima : staged;
     if (general || p0 + QBPT - 1 + kf > lim0 || p0 + QBPT > valid)
@@ -361,11 +369,11 @@ __global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, cons
     // first-stage constants: the table, the lane's copy, the address mask
     const uint8_t *Tb = reinterpret_cast<const uint8_t *>(GRAM ? Gs : Fs);
     const uint32_t c4 = (lane & ((1u << REP) - 1u)) << 2;
-    uint32_t amask, gm = 0, gsh = 0;
+    uint32_t amask, gm = 0, gmh = 0;
     if (GRAM) {
         const uint32_t hbw = P.g_hb - 5;
         gm = gram_mul(8u * P.kf);
-        gsh = 30u - hbw - REP;  // (t * gm) >> gsh puts the word at bit REP + 2
+        gmh = 1u << (hbw + REP + 2);  // high word of y * gmh: the word at bit REP + 2
         amask = ((1u << hbw) - 1u) << (REP + 2);
     } else {
         amask = ((1u << (8u * P.k - 5u)) - 1u) << (REP + 2);
@@ -411,19 +419,17 @@ __global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, cons
         const uint32_t a_next = __shfl_down_sync(0xFFFFFFFFu, ca.x, 1);
         const uint32_t b_next = __shfl_down_sync(0xFFFFFFFFu, cb.x, 1);
         const uint32_t b_first = __shfl_sync(0xFFFFFFFFu, cb.x, 0);
-        {
-            // the head of slice 2g + 1 is held when its lane 0 chunk was loaded
-            const uint32_t wa[5] = {ca.x, ca.y, ca.z, ca.w, lane == 31 ? b_first : a_next};
-            const uint64_t s1 = ((uint64_t)2 * g + 1) << SLICE_SHIFT;
-            r_slice<W, REP, GRAM, VAR>(P, A, Q, wa, s1 + 16 <= N, 2 * g, Tb, c4, amask, gm, gsh,
-                                       Fs, Cs, Es, Ms, lane);
-        }
-        if (2 * g + 1 < n_units) {
-            const uint32_t wb[5] = {cb.x, cb.y, cb.z, cb.w, lane == 31 ? ch : b_next};
-            const uint64_t s2 = ((uint64_t)2 * g + 2) << SLICE_SHIFT;
-            r_slice<W, REP, GRAM, VAR>(P, A, Q, wb, s2 + 4 <= N, 2 * g + 1, Tb, c4, amask, gm, gsh,
-                                       Fs, Cs, Es, Ms, lane);
-        }
+        const uint32_t wa[5] = {ca.x, ca.y, ca.z, ca.w, lane == 31 ? b_first : a_next};
+        const uint32_t wb[5] = {cb.x, cb.y, cb.z, cb.w, lane == 31 ? ch : b_next};
+        uint32_t sa, sb;
+        r_first_stage2<REP, GRAM>(wa, wb, Tb, c4, amask, gm, gmh, sa, sb);
+        // the head of slice 2g + 1 is held when its lane 0 chunk was loaded,
+        // that of the next pair when lane 31 loaded it
+        const uint64_t s1 = ((uint64_t)2 * g + 1) << SLICE_SHIFT;
+        r_slice<W, GRAM, VAR>(P, A, Q, wa, sa, s1 + 16 <= N, 2 * g, Fs, Cs, Es, Ms, lane);
+        if (2 * g + 1 < n_units)
+            r_slice<W, GRAM, VAR>(P, A, Q, wb, sb, s1 + SLICE + 4 <= N, 2 * g + 1, Fs, Cs, Es, Ms,
+                                  lane);
         ca = na;
         cb = nb;
         ch = nh;

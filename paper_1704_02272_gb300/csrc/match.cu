@@ -197,8 +197,9 @@ __global__ void __launch_bounds__(RT) k_offsets(const MatchParams P) {
     }
 }
 
-// Writes the keys of every tile whose records were kept (one thread per tile);
-// the last CTA publishes the call's status.
+// Writes the keys of every tile whose records were kept; the last CTA
+// publishes the call's status.
+constexpr uint32_t EXPAND_THREAD_MAX = 32;  // records a single thread expands
 __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
     __shared__ bool last;
     // one thread per unit: most units hold a few records or none, so the
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
     const uint32_t *pool = P.T.pool;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P.n_tiles; t += nthr) {
         const uint32_t m = P.tile_m[t];
-        if (m == 0 || m > P.unit_cap) continue;
+        if (m == 0 || m > P.unit_cap || m > EXPAND_THREAD_MAX) continue;
         uint64_t o = P.key_off[t];
         const uint64_t *rr = P.recs + t * P.unit_cap;
         const uint64_t tile_start = t << P.unit_shift;
@@ -218,6 +219,51 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
             const uint64_t pk = (P.pos_base + tile_start + (r >> 32)) << PFAC_ID_BITS;
             for (uint32_t e = 0; e < L; e++, o++)
                 if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
+        }
+    }
+    // units with more records (record space for every position): a whole
+    // warp per unit, 32 records at a time, each lane's keys placed by a warp
+    // scan of the records' key counts
+    if (P.unit_cap > EXPAND_THREAD_MAX) {
+        const uint32_t lane = threadIdx.x & 31;
+        const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const uint64_t nwarps = nthr >> 5;
+        for (uint64_t t0 = gwarp * 32; t0 < P.n_tiles; t0 += nwarps * 32) {
+            const uint64_t tl = t0 + lane;
+            const uint32_t ml = tl < P.n_tiles ? P.tile_m[tl] : 0u;
+            uint32_t dense = __ballot_sync(0xFFFFFFFFu, ml > EXPAND_THREAD_MAX && ml <= P.unit_cap);
+            while (dense) {
+                const uint32_t j = __ffs(dense) - 1;
+                dense &= dense - 1;
+                const uint64_t t = t0 + j;
+                const uint32_t m = __shfl_sync(0xFFFFFFFFu, ml, j);
+                uint64_t o = P.key_off[t];
+                const uint64_t *rr = P.recs + t * P.unit_cap;
+                const uint64_t tile_start = t << P.unit_shift;
+                for (uint32_t i0 = 0; i0 < m; i0 += 32) {
+                    const uint32_t i = i0 + lane;
+                    uint64_t r = 0;
+                    uint32_t L = 0;
+                    if (i < m) {
+                        r = rr[i];
+                        L = fin_len(pool, (uint32_t)r);
+                    }
+                    uint32_t inc = L;
+#pragma unroll
+                    for (int s = 1; s < 32; s <<= 1) {
+                        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, inc, s);
+                        if (lane >= (uint32_t)s) inc += nb;
+                    }
+                    if (L) {
+                        const uint32_t *ids = fin_ids(pool, (uint32_t)r);
+                        const uint64_t pk = (P.pos_base + tile_start + (r >> 32)) << PFAC_ID_BITS;
+                        uint64_t oo = o + inc - L;
+                        for (uint32_t e = 0; e < L; e++, oo++)
+                            if (oo < P.cap) P.out[oo] = pk | __ldg(ids + e);
+                    }
+                    o += __shfl_sync(0xFFFFFFFFu, inc, 31);
+                }
+            }
         }
     }
     __syncthreads();
@@ -334,27 +380,14 @@ static double first_stage_cost(double dens, int rep, bool hashed) {
            90.0 * (1.0 - exp(-cand)) + 12.0 * cand;
 }
 
-// Expected iterations of the register-staged kernel's second-stage loop:
-// the largest candidate count over a warp's 32 lanes when each lane's count
-// is Poisson with mean lam.
-static double r_rounds(double lam) {
-    double e = 0.0, cdf = 0.0, pm = exp(-lam);
-    for (int m = 0; m < 200; m++) {
-        cdf += pm;
-        const double gt = 1.0 - pow(cdf < 1.0 ? cdf : 1.0, 32.0);  // P(max > m)
-        e += gt;
-        if (gt < 1e-7) break;
-        pm *= lam / (m + 1);
-    }
-    return e;
-}
-
-// Estimated warp instructions per slice of the register-staged kernel: the
-// first stage (5 per position, 7 with the gram hash), bank-conflict replays
-// and about 27 per round of the second-stage loop.
+// Estimated SM cycles per slice of the register-staged kernel beyond a fixed
+// part: the first stage's shared-memory wavefronts (16 lookups a lane) and
+// about 10 cycles per candidate for the second stage (a fit to the alphabet-
+// 256 cell with 1,000 patterns: 112 cycles a slice with the gram filter at
+// 0.1% candidates and 3.7 wavefronts a lookup, 157 with the prefix bitmap in
+// 16 copies at 1.5% and 2 wavefronts), plus a little for the gram hash.
 static double r_cost(double dens, int rep, bool hashed) {
-    return 16.0 * (hashed ? 7.0 : 5.0) + 16.0 * (load_wavefronts(rep) - 1.0) +
-           27.0 * r_rounds(16.0 * dens);
+    return 16.0 * load_wavefronts(rep) + 10.0 * 512.0 * dens + (hashed ? 4.0 : 0.0);
 }
 
 static size_t r_smem(uint64_t words) {
@@ -362,7 +395,7 @@ static size_t r_smem(uint64_t words) {
 }
 
 constexpr int R_MAX_REP = 4;  // copies of the first-stage bitmap: 1 .. 16
-constexpr bool R_BY_DEFAULT = false;  // the register-staged kernel runs on request
+constexpr bool R_BY_DEFAULT = true;  // the register-staged kernel where it applies
 
 // Plan of the register-staged kernel (8-bit symbols): the first stage (the
 // prefix bitmap, or the gram filter folded to fit) and its copies, entries
@@ -535,6 +568,16 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     if (var != 0 && var != VAR_F && var != VAR_FE)
         return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
 
+    // ---- records kept per slice: 32, or 512 (one per position, so that no
+    // slice is scanned twice) where many matches are likely
+    const uint32_t recs = opts && opts->records_per_slice
+                              ? opts->records_per_slice
+                              : (use_tuned && t->tuned_records
+                                     ? t->tuned_records
+                                     : (t->match_density * SLICE > 8.0 ? (uint32_t)SLICE : SCAP));
+    if (recs != (uint32_t)SCAP && recs != (uint32_t)SLICE)
+        return set_error(PFAC_EINVAL, "pfac_match: records_per_slice %u (32 or 512)", recs);
+
     // ---- the register-staged kernel (8-bit symbols): on request, or by
     // default when the caller asks for nothing only the queued kernel has
     const uint32_t want_kind = opts && opts->scan_kernel ? opts->scan_kernel
@@ -546,6 +589,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                          "(alphabets of 129 to 256) and no prefix bytes or CTA width");
     if (want_kind == SCAN_REGISTER || (want_kind == 0 && r_usable && R_BY_DEFAULT)) {
         const int rc = make_plan_r(t, k, var, masks, gram, want, pl);
+        pl->unit_cap = recs;
         if (rc == PFAC_OK || want_kind == SCAN_REGISTER) return rc;
         clear_error();
         memset(pl, 0, sizeof(*pl));
@@ -695,7 +739,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     pl->kernel_emit = scan_kernel_for(T.bps, var, 1, (int)nwant);
     pl->smem = queued_smem(tw, nwant);
     pl->unit_shift = SLICE_SHIFT;
-    pl->unit_cap = SCAP;
+    pl->unit_cap = recs;
     pl->queued = true;
     if (!pl->kernel || !pl->kernel_emit)
         return set_error(PFAC_EINVAL, "pfac_match: no kernel for this table");
@@ -799,6 +843,7 @@ extern "C" int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts,
     out->prefix_bytes = pl.tbl_b_words ? 2u : 1u;
     out->warps_per_cta = pl.nw;
     out->scan_kernel = (uint32_t)pl.kind;
+    out->records_per_slice = pl.unit_cap;
     return PFAC_OK;
 }
 
@@ -894,6 +939,9 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.tbl_e_words = pl.tbl_e_words;
     P.rep_log2 = pl.rep_log2;
     P.dense_rows = pl.dense_rows;
+    P.wait_limit_ns = opts && opts->test_wait_limit_us ? (uint64_t)opts->test_wait_limit_us * 1000
+                                                       : WAIT_LIMIT_NS;
+    P.withhold_unit = opts && opts->test_withhold_slice ? opts->test_withhold_slice - 1 : UNIT_NONE;
     const uint32_t nthreads = pl.queued ? pl.nw * 32 : NTHREADS;
     // units a CTA takes in one round: the register-staged kernel's warps
     // take two slices each

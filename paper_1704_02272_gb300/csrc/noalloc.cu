@@ -13,6 +13,7 @@
 // PFAC_NOALLOC_SCRATCH_BYTES that every GPU which loads this library holds
 // until the process exits.
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -104,6 +105,21 @@ extern "C" int pfac_match_noalloc(const pfac_table *t, const uint8_t *d_input, u
     uint64_t need = 0;
     rc = pfac_workspace_bytes(t, n_bytes, n_segments, opts, &need);
     if (rc) return rc;
+    // a library choice of record space for every position (8 bytes of scratch
+    // per input byte) gives way to the smaller record space when only that fits
+    pfac_match_opts o32;
+    if (need > (uint64_t)PFAC_NOALLOC_SCRATCH_BYTES && !(opts && opts->records_per_slice)) {
+        if (opts) o32 = *opts;
+        else memset(&o32, 0, sizeof o32);
+        o32.records_per_slice = 32;
+        uint64_t need32 = 0;
+        if (pfac_workspace_bytes(t, n_bytes, n_segments, &o32, &need32) == PFAC_OK &&
+            need32 <= (uint64_t)PFAC_NOALLOC_SCRATCH_BYTES) {
+            opts = &o32;
+            need = need32;
+        }
+        pfac::clear_error();
+    }
     if (need > (uint64_t)PFAC_NOALLOC_SCRATCH_BYTES)
         return pfac::set_error(PFAC_EINVAL,
                                "pfac_match_noalloc: an input of %llu bytes in %u segments needs "

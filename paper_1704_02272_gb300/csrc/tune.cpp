@@ -39,11 +39,12 @@ std::string cache_key(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments
 }
 
 // A cache line: key, variant, depth, copies, masks, gram filter, prefix
-// bytes, warps per CTA, scan kernel, time.  Lines without the scan kernel
-// (written before the register-staged kernel existed) name the queued one.
+// bytes, warps per CTA, scan kernel, records per slice, time.  Lines without
+// the scan kernel (written before the register-staged kernel existed) name
+// the queued one; lines without the records leave them to the library.
 bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_t *k,
                   uint32_t *c, uint32_t *mk, uint32_t *gf, uint32_t *pb, uint32_t *nw,
-                  uint32_t *kind, float *ms) {
+                  uint32_t *kind, uint32_t *recs, float *ms) {
     FILE *f = fopen(path, "r");
     if (!f) return false;
     char line[512];
@@ -55,8 +56,8 @@ bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_
         for (char *p = strtok_r(line, " \t\r\n", &save); p && nt < 12;
              p = strtok_r(nullptr, " \t\r\n", &save))
             tok[nt++] = p;
-        if ((nt != 9 && nt != 10) || key != tok[0]) continue;
-        uint32_t u[8];
+        if (nt < 9 || nt > 11 || key != tok[0]) continue;
+        uint32_t u[9];
         bool ok = true;
         for (int i = 0; i < nt - 2; i++) {
             char *end = nullptr;
@@ -68,7 +69,8 @@ bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_
         const float e = strtof(tok[nt - 1], &end);
         if (!ok || !end || *end) continue;
         {
-            const uint32_t q = nt == 10 ? u[7] : 1u;
+            const uint32_t q = nt >= 10 ? u[7] : 1u;
+            *recs = nt == 11 ? u[8] : 0u;
             *v = u[0];
             *k = u[1];
             *c = u[2];
@@ -98,14 +100,16 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     memset(&res, 0, sizeof res);
     const std::string key = cache_key(t, n_bytes, n_segments);
     if (cache_path) {
-        uint32_t v, k, c, mk, gf, pb, nw, kind;
+        uint32_t v, k, c, mk, gf, pb, nw, kind, rp;
         float ms;
-        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &nw, &kind, &ms) &&
+        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &nw, &kind, &rp, &ms) &&
             k >= t->kmin && k <= t->kmax && (gf != 2 || t->dev.g_len) &&
             (pb != 2 || t->dev.B[k])) {
             t->tuned_bytes = pb;
             t->tuned_nw = nw;
             t->tuned_kernel = kind;
+            t->tuned_records = rp;
+            res.records_per_slice = rp;
             res.prefix_bytes = pb;
             res.warps_per_cta = nw;
             res.scan_kernel = kind;
@@ -125,6 +129,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
             // foreign cache line) is dropped and the table tuned afresh
             pfac_plan_info pi;
             const bool sane = (kind == 1 ? (nw == 16 || nw == 24) : (kind == 2 && nw == 0)) &&
+                              (rp == 0 || rp == 32 || rp == 512) &&
                               v <= 2 && mk <= 2 && gf <= 2 && pb <= 2 && c <= 32 &&
                               (c & (c - 1)) == 0;
             if (sane && pfac_match_plan(t, nullptr, &pi) == PFAC_OK) {
@@ -141,6 +146,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     t->tuned_bytes = 0;
     t->tuned_nw = 0;
     t->tuned_kernel = 0;
+    t->tuned_records = 0;
     if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_autotune: table was built host-only");
     {
         const int drc = check_table_device(t, cuda_stream, "pfac_autotune");
@@ -150,6 +156,21 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     struct Cand {
         uint32_t var, k, copies, masks, gram, bytes, nw, kernel;
         float ms;
+        uint32_t recs = 0;  // records per slice (0: the library's choice)
+    };
+    auto opts_of = [](const Cand &c) {
+        pfac_match_opts o;
+        memset(&o, 0, sizeof o);
+        o.variant = c.var;
+        o.prefix_depth = c.k;
+        o.bitmap_copies = c.copies;
+        o.child_masks = c.masks;
+        o.gram_filter = c.gram;
+        o.prefix_bytes = c.bytes;
+        o.warps_per_cta = c.nw;
+        o.scan_kernel = c.kernel;
+        o.records_per_slice = c.recs;
+        return o;
     };
     std::vector<Cand> cands;
     cands.push_back({0, 0, 0, 0, 0, 0, 0, 0, 0.f});  // library default
@@ -175,19 +196,14 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     uint64_t ws_max = 0;
     std::vector<Cand> ok;
     for (const Cand &c : cands) {
-        pfac_match_opts o;
-        memset(&o, 0, sizeof o);
-        o.variant = c.var;
-        o.prefix_depth = c.k;
-        o.bitmap_copies = c.copies;
-        o.child_masks = c.masks;
-        o.gram_filter = c.gram;
-        o.prefix_bytes = c.bytes;
-        o.warps_per_cta = c.nw;
-        o.scan_kernel = c.kernel;
+        pfac_match_opts o = opts_of(c);
         uint64_t b = 0;
         if (pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b) != PFAC_OK) continue;
         ws_max = std::max(ws_max, b);
+        // room for the same plan with a record per position (tried last)
+        o.records_per_slice = 512;
+        if (pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b) == PFAC_OK)
+            ws_max = std::max(ws_max, b);
         ok.push_back(c);
     }
     clear_error();
@@ -210,52 +226,57 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     }
     uint64_t *d_cnt = (uint64_t *)small;
     int32_t *d_st = (int32_t *)((uint8_t *)small + 128);
-    std::vector<Cand> timed;
-    for (Cand c : ok) {
-        pfac_match_opts o;
-        memset(&o, 0, sizeof o);
-        o.variant = c.var;
-        o.prefix_depth = c.k;
-        o.bitmap_copies = c.copies;
-        o.child_masks = c.masks;
-        o.gram_filter = c.gram;
-        o.prefix_bytes = c.bytes;
-        o.warps_per_cta = c.nw;
-        o.scan_kernel = c.kernel;
+    // the scan kernel's time for one candidate (both launches: the scan pass
+    // and the emit pass), median of three after a warm-up; false when it
+    // does not run
+    auto time_cand = [&](Cand &c) -> bool {
+        pfac_match_opts o = opts_of(c);
         uint64_t b = 0;
         pfac_workspace_bytes(t, n_bytes, n_segments, &o, &b);
-        // warm-up, then the median of three timed scans
         int rc = pfac_match_async(t, d_sample, n_bytes, d_seg_offsets, n_segments, nullptr, 0,
                                   d_cnt, d_st, ws, b, &o, st);
         if (rc != PFAC_OK) {
             clear_error();
-            continue;
+            return false;
         }
-        // both launches of the scan kernel: the scan pass and the emit pass
         o.ev_scan_begin = e0;
         o.ev_scan_end = e1;
         o.ev_emit_begin = e2;
         o.ev_emit_end = e3;
         float t3[3];
-        bool good = true;
-        for (int r = 0; r < 3 && good; r++) {
+        for (int r = 0; r < 3; r++) {
             rc = pfac_match_async(t, d_sample, n_bytes, d_seg_offsets, n_segments, nullptr, 0,
                                   d_cnt, d_st, ws, b, &o, st);
             float ms_scan = 0.f, ms_emit = 0.f;
             if (rc == PFAC_OK && cudaEventSynchronize(e3) == cudaSuccess &&
                 cudaEventElapsedTime(&ms_scan, e0, e1) == cudaSuccess &&
-                cudaEventElapsedTime(&ms_emit, e2, e3) == cudaSuccess)
+                cudaEventElapsedTime(&ms_emit, e2, e3) == cudaSuccess) {
                 t3[r] = ms_scan + ms_emit;
-            else
-                good = false;
-        }
-        if (!good) {
-            clear_error();
-            continue;
+            } else {
+                clear_error();
+                return false;
+            }
         }
         std::sort(t3, t3 + 3);
         c.ms = t3[1];
-        timed.push_back(c);
+        return true;
+    };
+    std::vector<Cand> timed;
+    for (Cand c : ok)
+        if (time_cand(c)) timed.push_back(c);
+    // the best plan with the other record space per slice
+    if (!timed.empty()) {
+        Cand best0 = timed[0];
+        for (const Cand &c : timed)
+            if (c.var && c.ms < best0.ms) best0 = c;
+        pfac_plan_info pi;
+        pfac_match_opts o = opts_of(best0);
+        if (best0.var && pfac_match_plan(t, &o, &pi) == PFAC_OK) {
+            Cand alt = best0;
+            alt.recs = pi.records_per_slice == 512 ? 32u : 512u;
+            if (time_cand(alt)) timed.push_back(alt);
+        }
+        clear_error();
     }
     int32_t h_st = 0;
     e = cudaMemcpyAsync(&h_st, d_st, 4, cudaMemcpyDeviceToHost, st);
@@ -284,6 +305,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         t->tuned_bytes = best.bytes;
         t->tuned_nw = best.nw;
         t->tuned_kernel = best.kernel;
+        t->tuned_records = best.recs;
     }
     res.variant = best.var;
     res.prefix_depth = best.k;
@@ -293,13 +315,14 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     res.prefix_bytes = best.bytes;
     res.warps_per_cta = best.nw;
     res.scan_kernel = best.kernel;
+    res.records_per_slice = best.recs;
     res.scan_ms = best.ms;
     if (cache_path && best.var) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s %u %u %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k,
+            fprintf(f, "%s %u %u %u %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k,
                     best.copies, best.masks, best.gram, best.bytes, best.nw, best.kernel,
-                    best.ms);
+                    best.recs, best.ms);
             fclose(f);
         }
     }

@@ -38,3 +38,28 @@ def test_committed_table_is_well_formed():
         assert isinstance(entries, list) and entries, workload
         for traffic, digest, plan in entries:
             assert traffic > 0 and len(digest) == 16 and plan
+
+
+def test_strong_scaling_shards_cover_the_job_once():
+    # the multi-GPU bench mode: every start position of the job belongs to
+    # exactly one rank; each rank's text is its share plus the read halo, and
+    # the oracle over the shards (positions moved by position_base, starts
+    # below starts_end) concatenates to the oracle over the whole input
+    import numpy as np
+    import oracle
+    import workloads
+    full = workloads.config3(n_bytes=3 << 20, n_patterns=3000)
+    ref_pos, ref_ids = oracle.match_ac(full.patterns, full.text, full.seg_offsets)
+    ref = oracle.pack_keys(ref_pos, ref_ids)
+    for world in (2, 3, 8):
+        parts, covered = [], 0
+        for rank in range(world):
+            w, opt, sh = bench.shard_workload(full, world, rank)
+            assert opt["position_base"] == sh.start == covered
+            assert w.n_bytes - opt["starts_end"] <= full.max_len - 1
+            assert w.text.ctypes.data % 16 == 0 or sh.start % 16 == 0
+            covered += opt["starts_end"]
+            pos, ids = oracle.match_ac(w.patterns, w.text, w.seg_offsets, hi=opt["starts_end"])
+            parts.append(oracle.pack_keys(pos + np.uint64(sh.start), ids))
+        assert covered == full.n_bytes
+        assert np.array_equal(np.concatenate(parts), ref), world

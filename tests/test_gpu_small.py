@@ -345,3 +345,45 @@ def test_wide_cta(case):
             assert_same(got, ref, f"24 warps depth {k} {extra}")
             ran += 1
     assert ran >= 1
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"s{c[0]}-sig{c[1]}" for c in CASES])
+def test_records_per_slice_both_ways(case):
+    # 32 records per slice (slices with more matched positions are re-scanned
+    # by the emit pass) and 512 (one record per position: one pass) give the
+    # oracle's keys on both scan kernels where they apply
+    seed, sigma, n, lo, hi, N, S, plants, ts = case
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, N, n_segments=S, n_plants=plants,
+                            text_sigma=ts)
+    ref = oracle_keys(w)
+    text, seg = to_device(w)
+    with pfac.Table(w.patterns, w.sigma) as t:
+        kernels = (1, 2) if bits_per_symbol(sigma) == 8 else (1,)
+        for kern in kernels:
+            for recs in (32, 512):
+                p = pfac.plan(t, scan_kernel=kern, records_per_slice=recs)
+                assert p["records_per_slice"] == recs and p["scan_kernel"] == kern
+                keys = pfac.match(t, text, seg, scan_kernel=kern, records_per_slice=recs)
+                torch.cuda.synchronize()
+                assert_same(keys_np(keys), ref, f"kernel {kern} records {recs}")
+
+
+def test_dense_matches_one_pass():
+    # every position matches several patterns: with 512 records per slice the
+    # scan pass keeps them all (no emit pass) and the warp-wide expansion
+    # writes the keys; with 32 the emit pass does
+    import itertools
+    pats = [bytes(p) for L in range(1, 6) for p in itertools.product(range(3), repeat=L)]
+    rs = np.random.RandomState(3)
+    text = rs.randint(0, 3, size=300_001).astype(np.uint8)
+    for sigma in (3, 4):
+        w = workloads.Workload("dense", sigma, pats, text, workloads.single_segment(text.size))
+        ref = oracle_keys(w)
+        assert ref.size > 4 * text.size
+        tt, sg = to_device(w)
+        with pfac.Table(pats, sigma) as t:
+            assert pfac.plan(t)["records_per_slice"] == 512  # the library's choice here
+            for recs in (32, 512):
+                keys = pfac.match(t, tt, sg, records_per_slice=recs)
+                torch.cuda.synchronize()
+                assert_same(keys_np(keys), ref, f"dense sigma {sigma} records {recs}")

@@ -93,3 +93,47 @@ def test_workspace_grows_with_the_input_and_stops_at_2_40():
             with pytest.raises(pfac.PfacError) as e:
                 pfac.workspace_bytes(t, n, 1)
             assert e.value.status == EINVAL
+
+
+@pytest.mark.parametrize("n", (100, 1000, 10000))
+def test_register_staged_plans(n):
+    # the register-staged kernel (8-bit symbols): every option combination
+    # either fits shared memory and honours the options, or fails cleanly;
+    # its CTA width is fixed and it takes neither prefix bytes nor a width
+    with host_table(256, n) as t:
+        ks = held_depths(t)
+        n_ok = 0
+        for k, var, masks, gram, copies in itertools.product(
+                ks, (0, 1, 2), (0, 1, 2), (0, 1, 2), (0, 1, 2, 4, 8, 16, 32)):
+            opt = dict(prefix_depth=k, variant=var, child_masks=masks, gram_filter=gram,
+                       bitmap_copies=copies, scan_kernel=2)
+            try:
+                p = pfac.plan(t, **opt)
+            except pfac.PfacError as e:
+                assert e.status == EINVAL, opt
+                continue
+            n_ok += 1
+            assert p["scan_kernel"] == 2 and p["warps_per_cta"] == 16, (opt, p)
+            assert p["smem_bytes"] <= SMEM_LIMIT and p["prefix_bytes"] == 1, (opt, p)
+            assert p["prefix_depth"] == k
+            for key, val in (("variant", var), ("child_masks", masks), ("gram_filter", gram),
+                             ("bitmap_copies", copies)):
+                if val:
+                    assert p[key] == val, (opt, p)
+            assert p["bitmap_copies"] <= 16
+        assert n_ok > 0
+        for opt in (dict(scan_kernel=2, prefix_bytes=2), dict(scan_kernel=2, warps_per_cta=16),
+                    dict(scan_kernel=3)):
+            with pytest.raises(pfac.PfacError) as e:
+                pfac.plan(t, **opt)
+            assert e.value.status == EINVAL, opt
+        assert pfac.plan(t, scan_kernel=1)["scan_kernel"] == 1
+
+
+def test_register_staged_kernel_needs_8_bit_symbols():
+    for sigma in (4, 20, 64):
+        with host_table(sigma, 1000) as t:
+            assert pfac.plan(t)["scan_kernel"] == 1
+            with pytest.raises(pfac.PfacError) as e:
+                pfac.plan(t, scan_kernel=2)
+            assert e.value.status == EINVAL
