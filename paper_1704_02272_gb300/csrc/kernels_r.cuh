@@ -87,29 +87,32 @@ __device__ __forceinline__ uint32_t r_addr(uint32_t t, uint32_t c4, uint32_t ama
 
 // First stage of the two slices of a step for the lane's 16 positions in
 // each (their 32 lookups independent, so they overlap): bit j of sa / sb is
-// set when position j's window passes the filter.
+// set when position j's window passes the filter.  The first-stage table
+// sits at the start of the dynamic shared memory, so a lookup needs no base
+// register.  Each slice's bits gather in two chains of eight.
 template <int REP, int GRAM>
 __device__ __forceinline__ void r_first_stage2(const uint32_t (&wa)[5], const uint32_t (&wb)[5],
-                                               const uint8_t *Tb, uint32_t c4, uint32_t amask,
-                                               uint32_t gm, uint32_t gmh, uint32_t &sa,
-                                               uint32_t &sb) {
-    uint32_t acc_a = 0, acc_b = 0;
+                                               uint32_t c4, uint32_t amask, uint32_t gm,
+                                               uint32_t gmh, uint32_t &sa, uint32_t &sb) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint32_t acc_a[2] = {0, 0}, acc_b[2] = {0, 0};
 #pragma unroll
     for (int j = 0; j < 16; j++) {
         const uint32_t ta =
             (j & 3) ? __funnelshift_r(wa[j >> 2], wa[(j >> 2) + 1], 8 * (j & 3)) : wa[j >> 2];
         const uint32_t tb =
             (j & 3) ? __funnelshift_r(wb[j >> 2], wb[(j >> 2) + 1], 8 * (j & 3)) : wb[j >> 2];
-        const uint32_t xa = *reinterpret_cast<const uint32_t *>(
-            Tb + r_addr<REP, GRAM>(ta, c4, amask, gm, gmh));
-        const uint32_t xb = *reinterpret_cast<const uint32_t *>(
-            Tb + r_addr<REP, GRAM>(tb, c4, amask, gm, gmh));
+        const uint32_t xa =
+            *reinterpret_cast<const uint32_t *>(smem + r_addr<REP, GRAM>(ta, c4, amask, gm, gmh));
+        const uint32_t xb =
+            *reinterpret_cast<const uint32_t *>(smem + r_addr<REP, GRAM>(tb, c4, amask, gm, gmh));
         // bit t & 31 of each word to bit 0, then into the top of acc
-        acc_a = __funnelshift_r(acc_a, __funnelshift_r(xa, xa, ta), 1);
-        acc_b = __funnelshift_r(acc_b, __funnelshift_r(xb, xb, tb), 1);
+        acc_a[j >> 3] = __funnelshift_r(acc_a[j >> 3], __funnelshift_r(xa, xa, ta), 1);
+        acc_b[j >> 3] = __funnelshift_r(acc_b[j >> 3], __funnelshift_r(xb, xb, tb), 1);
     }
-    sa = acc_a >> 16;
-    sb = acc_b >> 16;
+    // positions 0..7 end at bits 24..31 of the first chain, 8..15 of the second
+    sa = (acc_a[0] >> 24) | ((acc_a[1] >> 16) & 0xFF00u);
+    sb = (acc_b[0] >> 24) | ((acc_b[1] >> 16) & 0xFF00u);
 }
 
 // Second stage of one candidate whose window (bytes j .. j + 3) is t:
@@ -249,6 +252,9 @@ __device__ __forceinline__ void r_append(const MatchParams &P, RWarpArea &A, RQu
     }
     const uint32_t p0 = lane * QBPT;
     const uint32_t kb = 8u * P.k, kmask = kb >= 32 ? 0xFFFFFFFFu : (1u << kb) - 1u;
+    // walks stop at the input end (a clean slice's limits do not say where)
+    const uint64_t remain = P.n - ustart;
+    const uint32_t rem_x = remain < LIM_MAX ? (uint32_t)remain : LIM_MAX;
     for (uint32_t done = 0;;) {
         const uint32_t room = QCAP - Q.qn;
         const uint32_t take = tot - done < room ? tot - done : room;
@@ -262,7 +268,8 @@ __device__ __forceinline__ void r_append(const MatchParams &P, RWarpArea &A, RQu
                 en.unit = unit;
                 en.pos = p | (slot << 10) | (e + 1 == tot ? LAST_FLAG : 0u);
                 en.x = ((root >> j) & 1u) ? ROOT_X : (r_window(w, j) & kmask);
-                en.lim = lim_of(P, p, lima, limb, general, ustart, rem);
+                const uint32_t lj = lim_of(P, p, lima, limb, general, ustart, rem);
+                en.lim = lj < rem_x ? lj : rem_x;
                 A.q[Q.qn + slot] = en;
             }
             e++;
@@ -281,29 +288,34 @@ __device__ __forceinline__ void r_append(const MatchParams &P, RWarpArea &A, RQu
 template <int W, int GRAM, int VAR>
 __device__ __forceinline__ void r_slice(const MatchParams &P, RWarpArea &A, RQueue &Q,
                                         const uint32_t (&w)[5], uint32_t surv, bool halo_ok,
-                                        uint32_t u, const uint32_t *Fs, const uint32_t *Cs,
-                                        const uint32_t *Es, const uint32_t *Ms, uint32_t lane) {
+                                        uint32_t u, bool clean, const uint32_t *Fs,
+                                        const uint32_t *Cs, const uint32_t *Es,
+                                        const uint32_t *Ms, uint32_t lane) {
     const uint64_t ustart = (uint64_t)u << SLICE_SHIFT;
-    const uint64_t remain = P.n - ustart;
-    const uint32_t rem = remain < LIM_MAX ? (uint32_t)remain : LIM_MAX;
-    uint32_t valid = rem < (uint32_t)SLICE ? rem : (uint32_t)SLICE;
-    {
+    const uint32_t p0 = lane * QBPT;
+    // a clean slice (one segment; the slice, its 4-byte halo and every
+    // start inside the input and below starts_end) needs no limits: every
+    // position starts a walk and every window is held in registers; the
+    // exact input end is applied when survivors are queued
+    uint32_t rem = LIM_MAX, valid = SLICE, staged = SLICE + 4, lima = LIM_MAX, limb = LIM_MAX;
+    bool general = false;
+    uint32_t fv = 0xFFFFu, ex = 0xFFFFu;
+    if (!clean) {
+        const uint64_t remain = P.n - ustart;
+        rem = remain < LIM_MAX ? (uint32_t)remain : LIM_MAX;
+        valid = rem < (uint32_t)SLICE ? rem : (uint32_t)SLICE;
         const uint64_t sl = P.starts_end > ustart ? P.starts_end - ustart : 0;
         if (sl < valid) valid = (uint32_t)sl;
+        // bytes held in registers: whole 16-byte chunks, then (halo_ok) the
+        // 4-byte head of the next slice
+        staged = rem < (uint32_t)SLICE ? rem & ~15u : (uint32_t)SLICE + (halo_ok ? 4u : 0u);
+        lima = limb = rem;
+        if (P.n_seg > 1) r_seg_limits(P, u, ustart, rem, lane, lima, limb, general);
+        const uint32_t kf = P.kf;
+        const uint32_t lim0 = lima < staged ? lima : staged;
+        if (general || p0 + QBPT - 1 + kf > lim0 || p0 + QBPT > valid)
+            r_window_masks(P, p0, kf, valid, staged, rem, lima, limb, general, ustart, fv, ex);
     }
-    // bytes held in registers: whole 16-byte chunks, then (halo_ok) the
-    // 4-byte head of the next slice
-    const uint32_t staged = rem < (uint32_t)SLICE ? rem & ~15u
-                                                  : (uint32_t)SLICE + (halo_ok ? 4u : 0u);
-    uint32_t lima = rem, limb = rem;
-    bool general = false;
-    if (P.n_seg > 1) r_seg_limits(P, u, ustart, rem, lane, lima, limb, general);
-    const uint32_t kf = P.kf;
-    const uint32_t p0 = lane * QBPT;
-    uint32_t fv = 0xFFFFu, ex = 0xFFFFu;
-    const uint32_t lim0 = lima < staged ? lima : staged;
-    if (general || p0 + QBPT - 1 + kf > lim0 || p0 + QBPT > valid)
-        r_window_masks(P, p0, kf, valid, staged, rem, lima, limb, general, ustart, fv, ex);
     surv &= fv;
     const uint32_t root = ex & ~fv;
     // second stage over the lane's candidates
@@ -339,11 +351,13 @@ __global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, cons
     const uint32_t gw = blockIdx.x * RNW + warp, gstride = gridDim.x * RNW;
     if (blockIdx.x * RNW >= n_pairs) return;  // the whole CTA has no pair
 
-    uint32_t *Fs = reinterpret_cast<uint32_t *>(smem);
+    // the first-stage table at offset 0: the gram filter, or the prefix
+    // bitmap copies when there is none
+    uint32_t *Gs = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *Fs = Gs + P.tbl_g_words;
     uint32_t *Cs = Fs + P.tbl_words;
     uint32_t *Es = Cs + P.tbl_c_words;
     uint32_t *Ms = Es + P.tbl_e_words;
-    uint32_t *Gs = Ms + P.tbl_m_words;
     RWarpArea *areas = reinterpret_cast<RWarpArea *>(
         smem + ((((size_t)P.tbl_words + P.tbl_c_words + P.tbl_e_words + P.tbl_m_words +
                   P.tbl_g_words) * 4 + 127) & ~(size_t)127));
@@ -366,8 +380,7 @@ __global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, cons
     __syncthreads();
     RWarpArea &A = areas[warp];
 
-    // first-stage constants: the table, the lane's copy, the address mask
-    const uint8_t *Tb = reinterpret_cast<const uint8_t *>(GRAM ? Gs : Fs);
+    // first-stage constants: the lane's copy, the address mask, the hash
     const uint32_t c4 = (lane & ((1u << REP) - 1u)) << 2;
     uint32_t amask, gm = 0, gmh = 0;
     if (GRAM) {
@@ -380,7 +393,26 @@ __global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, cons
     }
 
     const uint64_t N = P.n;
+    // clean pairs (every load in bounds, the next pair's head too, every
+    // start below starts_end, one segment) take loads without checks and
+    // slices without limits: pairs g < g_clean
+    uint32_t g_clean = 0;
+    if (P.n_seg <= 1 && N >= 4) {
+        const uint64_t a = (N - 4) >> (SLICE_SHIFT + 1), b = P.starts_end >> (SLICE_SHIFT + 1);
+        const uint64_t c = a < b ? a : b;
+        g_clean = c < n_pairs ? (uint32_t)c : n_pairs;
+    }
+    const uint32_t it_clean = gw < g_clean ? (g_clean - gw + gstride - 1) / gstride : 0u;
+    const uint64_t step_b = (uint64_t)gstride << (SLICE_SHIFT + 1);
+    const uint8_t *lane_ptr = P.in + ((uint64_t)gw << (SLICE_SHIFT + 1)) + lane * 16u;
     auto load_pair = [&](uint32_t i, uint4 &a, uint4 &b, uint32_t &h) {
+        const uint8_t *q = lane_ptr + i * step_b;
+        if (i < it_clean) {
+            a = ld_stream16(q);
+            b = ld_stream16(q + SLICE);
+            h = lane == 31 ? ld_stream4(q + SLICE + 16) : 0u;
+            return;
+        }
         a = make_uint4(0, 0, 0, 0);
         b = a;
         h = 0;
@@ -392,19 +424,10 @@ __global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, cons
         if (o1 + 16 <= N) b = ld_stream16(P.in + o1);
         if (lane == 31 && s0 + 2 * SLICE + 4 <= N) h = ld_stream4(P.in + s0 + 2 * SLICE);
     };
-    auto prefetch = [&](uint32_t i) {
-        const uint32_t g = gw + i * gstride;
-        if (lane == 0 && g < n_pairs) {
-            const uint64_t s0 = (uint64_t)g << (SLICE_SHIFT + 1);
-            if (s0 < N) {
-                const uint64_t left = N - s0;
-                const uint32_t bytes = (left < 2 * SLICE ? (uint32_t)left : 2u * SLICE) & ~15u;
-                if (bytes) prefetch_l2(P.in + s0, bytes);
-            }
-        }
-    };
+    // the L2 prefetch runs RPF steps ahead over the clean pairs
+    const uint8_t *pair_ptr = P.in + ((uint64_t)gw << (SLICE_SHIFT + 1));
     if (lane == 0)
-        for (uint32_t i = 0; i < RPF; i++) prefetch(i);
+        for (uint32_t i = 0; i < RPF && i < it_clean; i++) prefetch_l2(pair_ptr + i * step_b, 2 * SLICE);
 
     RQueue Q{0u, UNIT_OVF, 0u};
     uint4 ca, cb, na, nb;
@@ -412,8 +435,9 @@ __global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, cons
     load_pair(0, ca, cb, ch);
     for (uint32_t i = 0; gw + i * gstride < n_pairs; i++) {
         load_pair(i + 1, na, nb, nh);
-        prefetch(i + RPF);
+        if (lane == 0 && i + RPF < it_clean) prefetch_l2(pair_ptr + (i + RPF) * step_b, 2 * SLICE);
         const uint32_t g = gw + i * gstride;
+        const bool clean = i < it_clean;
         // halo words: the next lane's first word; lane 31 takes the second
         // slice's lane 0 (first slice) or the next pair's head (second slice)
         const uint32_t a_next = __shfl_down_sync(0xFFFFFFFFu, ca.x, 1);
@@ -422,14 +446,15 @@ __global__ void __launch_bounds__(RNW * 32, 1) k_scanr(const MatchParams P, cons
         const uint32_t wa[5] = {ca.x, ca.y, ca.z, ca.w, lane == 31 ? b_first : a_next};
         const uint32_t wb[5] = {cb.x, cb.y, cb.z, cb.w, lane == 31 ? ch : b_next};
         uint32_t sa, sb;
-        r_first_stage2<REP, GRAM>(wa, wb, Tb, c4, amask, gm, gmh, sa, sb);
+        r_first_stage2<REP, GRAM>(wa, wb, c4, amask, gm, gmh, sa, sb);
         // the head of slice 2g + 1 is held when its lane 0 chunk was loaded,
         // that of the next pair when lane 31 loaded it
         const uint64_t s1 = ((uint64_t)2 * g + 1) << SLICE_SHIFT;
-        r_slice<W, GRAM, VAR>(P, A, Q, wa, sa, s1 + 16 <= N, 2 * g, Fs, Cs, Es, Ms, lane);
-        if (2 * g + 1 < n_units)
-            r_slice<W, GRAM, VAR>(P, A, Q, wb, sb, s1 + SLICE + 4 <= N, 2 * g + 1, Fs, Cs, Es, Ms,
-                                  lane);
+        r_slice<W, GRAM, VAR>(P, A, Q, wa, sa, clean || s1 + 16 <= N, 2 * g, clean, Fs, Cs, Es,
+                              Ms, lane);
+        if (clean || 2 * g + 1 < n_units)
+            r_slice<W, GRAM, VAR>(P, A, Q, wb, sb, clean || s1 + SLICE + 4 <= N, 2 * g + 1, clean,
+                                  Fs, Cs, Es, Ms, lane);
         ca = na;
         cb = nb;
         ch = nh;
