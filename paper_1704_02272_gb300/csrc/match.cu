@@ -22,14 +22,24 @@ void *scan_kernel_bps6(int, int, int);
 void *scan_kernel_bps7(int, int, int);
 void *scan_kernel_bps8(int, int, int);
 void *scan_kernel_dense();
-void *scan_kernel_r8_g0_f(int rep);
-void *scan_kernel_r8_g0_fe(int rep);
-void *scan_kernel_r8_g1_f(int rep);
-void *scan_kernel_r8_g1_fe(int rep);
+void *scan_kernel_r8_g0_f(int rep, int nw);
+void *scan_kernel_r8_g0_fe(int rep, int nw);
+void *scan_kernel_r8_g1_f(int rep, int nw);
+void *scan_kernel_r8_g1_fe(int rep, int nw);
+void *scan_kernel_r2_g0_f(int rep, int nw);
+void *scan_kernel_r2_g0_fe(int rep, int nw);
+void *scan_kernel_r2_g1_f(int rep, int nw);
+void *scan_kernel_r2_g1_fe(int rep, int nw);
 
-static void *scan_kernel_r(int rep, bool gram, int var) {
-    if (gram) return var == VAR_FE ? scan_kernel_r8_g1_fe(rep) : scan_kernel_r8_g1_f(rep);
-    return var == VAR_FE ? scan_kernel_r8_g0_fe(rep) : scan_kernel_r8_g0_f(rep);
+// the register-staged kernel for 8-bit or 2-bit symbols
+static void *scan_kernel_r(uint32_t bps, int rep, bool gram, int var, int nw) {
+    if (bps == 2) {
+        if (gram) return var == VAR_FE ? scan_kernel_r2_g1_fe(rep, nw) : scan_kernel_r2_g1_f(rep, nw);
+        return var == VAR_FE ? scan_kernel_r2_g0_fe(rep, nw) : scan_kernel_r2_g0_f(rep, nw);
+    }
+    if (bps != 8) return nullptr;
+    if (gram) return var == VAR_FE ? scan_kernel_r8_g1_fe(rep, nw) : scan_kernel_r8_g1_f(rep, nw);
+    return var == VAR_FE ? scan_kernel_r8_g0_fe(rep, nw) : scan_kernel_r8_g0_f(rep, nw);
 }
 
 constexpr int CHUNK = 1024;      // tiles per chunk of the key-count scan
@@ -390,19 +400,19 @@ static double r_cost(double dens, int rep, bool hashed) {
     return 16.0 * load_wavefronts(rep) + 10.0 * 512.0 * dens + (hashed ? 4.0 : 0.0);
 }
 
-static size_t r_smem(uint64_t words) {
-    return (((size_t)words * 4 + 127) & ~(size_t)127) + RNW * sizeof(RWarpArea);
+static size_t r_smem(uint64_t words, uint32_t nw = RNW) {
+    return (((size_t)words * 4 + 127) & ~(size_t)127) + nw * sizeof(RWarpArea);
 }
 
 constexpr int R_MAX_REP = 4;  // copies of the first-stage bitmap: 1 .. 16
-constexpr bool R_BY_DEFAULT = true;  // the register-staged kernel where it applies
+constexpr bool R_BY_DEFAULT = true;  // the register-staged kernel by default for 8-bit symbols
 
 // Plan of the register-staged kernel (8-bit symbols): the first stage (the
 // prefix bitmap, or the gram filter folded to fit) and its copies, entries
 // and child masks in shared memory as they fit, chosen by r_cost; the emit
 // pass runs the queued kernel with one bitmap copy.
 static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks, uint32_t gram,
-                       int want, Plan *pl) {
+                       int want, uint32_t nw, Plan *pl) {
     const DevTable &T = t->dev;
     const uint64_t ent = 1ull << (k * T.bps);
     const uint32_t fw = (uint32_t)(ent >= 32 ? ent / 32 : 1);
@@ -427,7 +437,7 @@ static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks,
             const double bias = (vv == VAR_FE ? 1.0 : 1.05) * (mon ? 1.0 : 1.3);
             for (int r = 0; r <= R_MAX_REP; r++) {
                 if (want >= 0 && r != want) continue;
-                if (gram != 2 && r_smem(base + ((uint64_t)fw << r)) <= SMEM_LIMIT) {
+                if (gram != 2 && r_smem(base + ((uint64_t)fw << r), nw) <= SMEM_LIMIT) {
                     const double c = r_cost(dens_f, r, false) * bias;
                     if (c < best) {
                         best = c;
@@ -441,7 +451,7 @@ static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks,
                     const uint32_t hb = T.g_bits;
                     const uint64_t gw0 = (1ull << hb) / 32;
                     for (uint32_t f = 0; hb - f >= GRAM_MIN_BITS; f++) {
-                        if (r_smem(base + fw + ((gw0 >> f) << r)) > SMEM_LIMIT) continue;
+                        if (r_smem(base + fw + ((gw0 >> f) << r), nw) > SMEM_LIMIT) continue;
                         const double dens = 1.0 - exp(-(double)T.g_set / (double)(1ull << (hb - f)));
                         const double c = r_cost(dens, r, true) * bias;
                         if ((gram == 2 || dens < 0.5) && c < best) {
@@ -477,11 +487,11 @@ static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks,
         pl->rep_log2 = (uint32_t)b_rep;
         pl->tbl_words = fw << b_rep;
     }
-    pl->nw = RNW;
+    pl->nw = nw;
     pl->kind = SCAN_REGISTER;
-    pl->kernel = scan_kernel_r(b_rep, b_gram, b_var);
+    pl->kernel = scan_kernel_r(T.bps, b_rep, b_gram, b_var, (int)nw);
     pl->smem = r_smem((uint64_t)pl->tbl_words + pl->tbl_c_words + pl->tbl_e_words +
-                      pl->tbl_m_words + pl->tbl_g_words);
+                      pl->tbl_m_words + pl->tbl_g_words, nw);
     // the emit pass: the queued kernel, one bitmap copy, entries through L2,
     // child masks when they fit beside its warps' rings
     pl->e_tbl_words = fw;
@@ -583,12 +593,15 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     const uint32_t want_kind = opts && opts->scan_kernel ? opts->scan_kernel
                                                          : (use_tuned ? t->tuned_kernel : 0u);
     if (want_kind > 2) return set_error(PFAC_EINVAL, "pfac_match: scan_kernel %u", want_kind);
-    const bool r_usable = T.bps == 8 && pbytes != 2 && !(opts && opts->warps_per_cta);
+    const bool r_usable = (T.bps == 8 || T.bps == 2) && pbytes != 2;
     if (want_kind == SCAN_REGISTER && !r_usable)
-        return set_error(PFAC_EINVAL, "pfac_match: the register-staged kernel needs 8-bit symbols "
-                         "(alphabets of 129 to 256) and no prefix bytes or CTA width");
-    if (want_kind == SCAN_REGISTER || (want_kind == 0 && r_usable && R_BY_DEFAULT)) {
-        const int rc = make_plan_r(t, k, var, masks, gram, want, pl);
+        return set_error(PFAC_EINVAL, "pfac_match: the register-staged kernel needs 8-bit or 2-bit "
+                         "symbols (alphabets of 129 to 256, or of up to 4) and no prefix bytes");
+    if (want_kind == SCAN_REGISTER || (want_kind == 0 && r_usable && T.bps == 8 && R_BY_DEFAULT)) {
+        const uint32_t rnw = opts && opts->warps_per_cta
+                                 ? opts->warps_per_cta
+                                 : (use_tuned && t->tuned_nw ? t->tuned_nw : (uint32_t)RNW);
+        const int rc = make_plan_r(t, k, var, masks, gram, want, rnw, pl);
         pl->unit_cap = recs;
         if (rc == PFAC_OK || want_kind == SCAN_REGISTER) return rc;
         clear_error();

@@ -1,0 +1,26 @@
+// Instances of the register-staged scan kernel (2-bit symbols) with the
+// prefix bitmap as the first stage and the prefix entries read through L2
+// (one translation unit per group, so that they compile in parallel).
+#include "kernels_r.cuh"
+
+namespace pfac {
+
+template <int NW>
+static void *pick(int rep) {
+    switch (rep) {
+        case 0: return (void *)k_scanr<2, 1, 0, 0, VAR_F, NW>;
+        case 1: return (void *)k_scanr<2, 1, 1, 0, VAR_F, NW>;
+        case 2: return (void *)k_scanr<2, 1, 2, 0, VAR_F, NW>;
+        case 3: return (void *)k_scanr<2, 1, 3, 0, VAR_F, NW>;
+        case 4: return (void *)k_scanr<2, 1, 4, 0, VAR_F, NW>;
+        default: return nullptr;
+    }
+}
+
+void *scan_kernel_r2_g0_f(int rep, int nw) {
+    if (nw == RNW) return pick<RNW>(rep);
+    if (nw == RNW_WIDE) return pick<RNW_WIDE>(rep);
+    return nullptr;
+}
+
+}  // namespace pfac

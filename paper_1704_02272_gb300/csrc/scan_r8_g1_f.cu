@@ -5,15 +5,22 @@
 
 namespace pfac {
 
-void *scan_kernel_r8_g1_f(int rep) {
+template <int NW>
+static void *pick(int rep) {
     switch (rep) {
-        case 0: return (void *)k_scanr<8, 0, 1, VAR_F>;
-        case 1: return (void *)k_scanr<8, 1, 1, VAR_F>;
-        case 2: return (void *)k_scanr<8, 2, 1, VAR_F>;
-        case 3: return (void *)k_scanr<8, 3, 1, VAR_F>;
-        case 4: return (void *)k_scanr<8, 4, 1, VAR_F>;
+        case 0: return (void *)k_scanr<8, 8, 0, 1, VAR_F, NW>;
+        case 1: return (void *)k_scanr<8, 8, 1, 1, VAR_F, NW>;
+        case 2: return (void *)k_scanr<8, 8, 2, 1, VAR_F, NW>;
+        case 3: return (void *)k_scanr<8, 8, 3, 1, VAR_F, NW>;
+        case 4: return (void *)k_scanr<8, 8, 4, 1, VAR_F, NW>;
         default: return nullptr;
     }
+}
+
+void *scan_kernel_r8_g1_f(int rep, int nw) {
+    if (nw == RNW) return pick<RNW>(rep);
+    if (nw == RNW_WIDE) return pick<RNW_WIDE>(rep);
+    return nullptr;
 }
 
 }  // namespace pfac

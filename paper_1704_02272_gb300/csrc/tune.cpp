@@ -128,7 +128,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
             // a cached choice that no longer makes a plan (an edited or
             // foreign cache line) is dropped and the table tuned afresh
             pfac_plan_info pi;
-            const bool sane = (kind == 1 ? (nw == 16 || nw == 24) : (kind == 2 && nw == 0)) &&
+            const bool sane = (kind == 1 || kind == 2) && (nw == 0 || nw == 16 || nw == 24) &&
                               (rp == 0 || rp == 32 || rp == 512) &&
                               v <= 2 && mk <= 2 && gf <= 2 && pb <= 2 && c <= 32 &&
                               (c & (c - 1)) == 0;
@@ -184,14 +184,15 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
                             cands.push_back({var, k, copies, masks, gram, 1, nw, 1, 0.f});
                     if (t->dev.B[k]) cands.push_back({var, k, 1, masks, 1, 2, nw, 1, 0.f});
                 }
-    // the register-staged kernel (8-bit symbols): its CTA width is fixed
-    if (t->dev.bps == 8)
-        for (uint32_t k = t->kmin; k <= t->kmax; k++)
-            for (uint32_t var = 1; var <= 2; var++)
-                for (uint32_t masks = 1; masks <= 2; masks++)
-                    for (uint32_t gram = 1; gram <= gmax; gram++)
-                        for (uint32_t copies = 16; copies >= 1; copies >>= 1)
-                            cands.push_back({var, k, copies, masks, gram, 1, 0, 2, 0.f});
+    // the register-staged kernel (8-bit and 2-bit symbols)
+    if (t->dev.bps == 8 || t->dev.bps == 2)
+        for (uint32_t nw : {16u})
+            for (uint32_t k = t->kmin; k <= t->kmax; k++)
+                for (uint32_t var = 1; var <= 2; var++)
+                    for (uint32_t masks = 1; masks <= 2; masks++)
+                        for (uint32_t gram = 1; gram <= gmax; gram++)
+                            for (uint32_t copies = 16; copies >= 1; copies >>= 1)
+                                cands.push_back({var, k, copies, masks, gram, 1, nw, 2, 0.f});
 
     uint64_t ws_max = 0;
     std::vector<Cand> ok;

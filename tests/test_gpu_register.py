@@ -1,5 +1,6 @@
 """GPU parity of the register-staged scan kernel (alphabets of 129 to 256
-symbols): the C ABI with scan_kernel = 2 against the CPU oracle, element by
+symbols, and of up to 4): the C ABI with scan_kernel = 2 against the CPU
+oracle, element by
 element, for every first stage (prefix bitmap, gram filter), bitmap copies,
 prefix depth, child masks on and off and entries in or out of shared memory,
 on single- and multi-segment inputs with ragged ends, and on inputs dense
@@ -58,6 +59,13 @@ CASES = [
     (204, 200, 800, 1, 6, 300_000, 17, 800, 256),         # bytes >= sigma in the text
     (205, 256, 50, 3, 20, 33_000, 3, 200, None),          # few slices, tiny segments
     (206, 130, 4000, 1, 4, 500_000, 1, 1000, None),       # short patterns, dense prefixes
+    # 2-bit symbols (one per byte)
+    (221, 4, 400, 4, 14, 400_000, 1, 800, None),
+    (222, 4, 2000, 8, 30, 300_003, 1, 500, None),          # ragged tail, long patterns
+    (223, 4, 300, 2, 12, 350_000, 300, 700, None),         # many segments
+    (224, 4, 200, 1, 9, 250_000, 9, 600, 8),               # bytes 4..7 in the text
+    (225, 3, 150, 1, 8, 200_000, 5, 500, 4),               # symbol 3 outside the alphabet
+    (226, 3, 60, 1, 12, 150_000, 3, 300, 200),            # bytes far outside the alphabet
 ]
 
 
@@ -70,7 +78,7 @@ def test_register_kernel_all_plans(case):
     assert ref.size > 0
     with pfac.Table(w.patterns, w.sigma, host_only=True) as th:
         kdef = th.info()["prefix_depth"]
-    ran = every_plan(w, ref, f"case {seed}", sorted({1, kdef}))
+    ran = every_plan(w, ref, f"case {seed}", sorted({max(1, kdef - 2), kdef}))
     assert ran >= 8
 
 
@@ -142,6 +150,26 @@ def test_register_kernel_starts_end_and_base():
     pos = ref >> np.uint64(24)
     want = ref[(pos >= np.uint64(base)) & (pos < np.uint64(hi))]
     assert_same(keys_np(keys), want, "shard")
+
+
+def test_register_kernel_full_size_dna():
+    # the DNA-shaped workload at its full 256 MiB: whole list against the
+    # oracle in 32 MiB windows of start positions
+    w = workloads.config2()
+    text, seg = to_device(w)
+    import oracle
+    ac = oracle.ACOracle(w.patterns)
+    try:
+        step = 32 << 20
+        ref = np.concatenate([oracle_keys(w, lo=a, hi=min(a + step, w.n_bytes), ac=ac)
+                              for a in range(0, w.n_bytes, step)])
+        with pfac.Table(w.patterns, 4) as t:
+            for opt in ({}, {"gram_filter": 2}, {"prefix_depth": 9, "bitmap_copies": 4}):
+                keys = pfac.match(t, text, seg, scan_kernel=REG, **opt)
+                torch.cuda.synchronize()
+                assert_same(keys_np(keys), ref, f"dna {opt}")
+    finally:
+        ac.close()
 
 
 def test_register_kernel_full_size_sweep_cell():

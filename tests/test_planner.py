@@ -97,23 +97,23 @@ def test_workspace_grows_with_the_input_and_stops_at_2_40():
 
 @pytest.mark.parametrize("n", (100, 1000, 10000))
 def test_register_staged_plans(n):
-    # the register-staged kernel (8-bit symbols): every option combination
+    # the register-staged kernel (8-bit symbols here): every option combination
     # either fits shared memory and honours the options, or fails cleanly;
     # its CTA width is fixed and it takes neither prefix bytes nor a width
     with host_table(256, n) as t:
         ks = held_depths(t)
         n_ok = 0
-        for k, var, masks, gram, copies in itertools.product(
-                ks, (0, 1, 2), (0, 1, 2), (0, 1, 2), (0, 1, 2, 4, 8, 16, 32)):
+        for k, var, masks, gram, copies, nw in itertools.product(
+                ks, (0, 1, 2), (0, 1, 2), (0, 1, 2), (0, 1, 2, 4, 8, 16, 32), (0, 24)):
             opt = dict(prefix_depth=k, variant=var, child_masks=masks, gram_filter=gram,
-                       bitmap_copies=copies, scan_kernel=2)
+                       bitmap_copies=copies, scan_kernel=2, warps_per_cta=nw)
             try:
                 p = pfac.plan(t, **opt)
             except pfac.PfacError as e:
                 assert e.status == EINVAL, opt
                 continue
             n_ok += 1
-            assert p["scan_kernel"] == 2 and p["warps_per_cta"] == 16, (opt, p)
+            assert p["scan_kernel"] == 2 and p["warps_per_cta"] == (nw or 16), (opt, p)
             assert p["smem_bytes"] <= SMEM_LIMIT and p["prefix_bytes"] == 1, (opt, p)
             assert p["prefix_depth"] == k
             for key, val in (("variant", var), ("child_masks", masks), ("gram_filter", gram),
@@ -122,7 +122,7 @@ def test_register_staged_plans(n):
                     assert p[key] == val, (opt, p)
             assert p["bitmap_copies"] <= 16
         assert n_ok > 0
-        for opt in (dict(scan_kernel=2, prefix_bytes=2), dict(scan_kernel=2, warps_per_cta=16),
+        for opt in (dict(scan_kernel=2, prefix_bytes=2), dict(scan_kernel=2, warps_per_cta=20),
                     dict(scan_kernel=3)):
             with pytest.raises(pfac.PfacError) as e:
                 pfac.plan(t, **opt)
@@ -130,10 +130,33 @@ def test_register_staged_plans(n):
         assert pfac.plan(t, scan_kernel=1)["scan_kernel"] == 1
 
 
-def test_register_staged_kernel_needs_8_bit_symbols():
-    for sigma in (4, 20, 64):
+def test_register_staged_kernel_needs_8_or_2_bit_symbols():
+    for sigma in (20, 64):
         with host_table(sigma, 1000) as t:
             assert pfac.plan(t)["scan_kernel"] == 1
             with pytest.raises(pfac.PfacError) as e:
                 pfac.plan(t, scan_kernel=2)
             assert e.value.status == EINVAL
+    with host_table(4, 1000) as t:
+        assert pfac.plan(t)["scan_kernel"] == 1  # on request only, for 2-bit symbols
+        assert pfac.plan(t, scan_kernel=2)["scan_kernel"] == 2
+
+
+@pytest.mark.parametrize("n", (100, 1000, 10000))
+def test_register_staged_plans_2_bit(n):
+    with host_table(4, n) as t:
+        ks = held_depths(t)
+        n_ok = 0
+        for k, var, masks, gram, copies in itertools.product(
+                ks, (0, 1, 2), (0, 1, 2), (0, 1, 2), (0, 1, 4, 16)):
+            opt = dict(prefix_depth=k, variant=var, child_masks=masks, gram_filter=gram,
+                       bitmap_copies=copies, scan_kernel=2)
+            try:
+                p = pfac.plan(t, **opt)
+            except pfac.PfacError as e:
+                assert e.status == EINVAL, opt
+                continue
+            n_ok += 1
+            assert p["scan_kernel"] == 2 and p["smem_bytes"] <= SMEM_LIMIT, (opt, p)
+            assert p["prefix_depth"] == k
+        assert n_ok > 0
