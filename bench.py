@@ -16,7 +16,9 @@ algorithmic bytes over the time of both of its launches, the scan pass and the
 emit pass), the CPU oracle timed on a bounded sample, clocks sampled during the
 timed region, and the number of kernels launched.  The line also carries
 ``sweep_256_1000``: the same measurements on the alphabet-256 cell with 1,000
-patterns and 512 MiB of input, timed after the main workload.
+patterns and 512 MiB of input, timed after the main workload, and
+``serving``: one level of the serving loop (50,000 resident patterns, Poisson
+arrivals of packet batches offered at 100 Gbps for 2 s) with request p50/p99.
 
 ``--impl reference`` times the CPU oracle (Aho-Corasick with failure links,
 all host cores) on bounded samples of the same workload instead.
@@ -388,6 +390,8 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
     d1.record(stream)
     stream.synchronize()
     dense_gbps = 8.0 * n_starts * K / (d0.elapsed_time(d1) / 1e3) / 1e9
+    merged = None if args.no_suffix_merge or args.truncate else time_merged(
+        pfac, torch, w, text, seg, keys, stream, args, call_opt, n_starts)
 
     hbm_peak, peak_kind = peaks()
     # algorithmic bytes of the scan kernel's launches in one step: every input
@@ -420,6 +424,7 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
                         "paper_model": info["paper_bytes"], "trie_nodes": info["trie_nodes"],
                         "records": info["records"], "merged_leaves": info["merged_leaves"]},
         "dense": {"value": round(dense_gbps, 3), "unit": "Gbps", "bit_exact_vs_compressed": exact},
+        "suffix_merge": merged,
         "build_s": {"compressed": round(build_s, 3), "dense": round(dense_build_s, 3)},
         "roofline": roofline,
         "scan_plan": plan, "autotuned": tune, "cuda_graph": bool(graph is not None),
@@ -429,6 +434,51 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
     ctx = {"table": table, "dense": dense, "text": text, "seg": seg, "keys": keys,
            "cap": cap, "total_ms": total_ms, "n_match": n_match}
     return cell, ctx
+
+
+def time_merged(pfac, torch, w, text, seg, keys, stream, args, call_opt, n_starts):
+    """The merged trie (reduction step 2, Section 3.2) on the same input: its
+    table sizes against the tree's, whether its keys equal the plain table's,
+    and its throughput over K eager calls with the library's default plan."""
+    N, S, K = w.n_bytes, len(w.seg_offsets) - 1, args.steps
+    t0 = time.perf_counter()
+    mt = pfac.Table(w.patterns, w.sigma, suffix_merge=True)
+    m_build = time.perf_counter() - t0
+    try:
+        mi = mt.info()
+        with torch.cuda.stream(stream):
+            mk = pfac.match(mt, text, seg, stream=stream, **call_opt)
+            stream.synchronize()
+        exact = bool(torch.equal(mk, keys))
+        out = torch.empty(keys.numel() + 1024, dtype=torch.int64, device=text.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=text.device)
+        st = torch.zeros(1, dtype=torch.int32, device=text.device)
+        ws = torch.empty(pfac.workspace_bytes(mt, N, S), dtype=torch.uint8, device=text.device)
+        del mk
+
+        def step():
+            pfac.match_async(mt, text, seg, out, cnt, st, ws, stream=stream, **call_opt)
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step()
+        e1.record(stream)
+        stream.synchronize()
+        assert int(st.item()) == 0, f"device status {int(st.item())}"
+        gbps = 8.0 * n_starts * K / (e0.elapsed_time(e1) / 1e3) / 1e9
+        per_node = (w.sigma + 7) // 8 + 4
+        return {"value": round(gbps, 3), "unit": "Gbps", "bit_exact_vs_compressed": exact,
+                "device_bytes": mi["device_bytes"], "records": mi["records"],
+                "merged_trie_nodes": mi["merged_trie_nodes"], "side_entries": mi["side_entries"],
+                "paper_model": mi["merged_trie_nodes"] * per_node,
+                "node_reduction": round(1.0 - mi["merged_trie_nodes"] / mi["trie_nodes"], 4),
+                "build_s": round(m_build, 3), "plan": "library default, eager calls"}
+    finally:
+        mt.close()
 
 
 def shard_workload(full, world, rank):
@@ -577,6 +627,11 @@ def run_ours(args):
         extra["sweep_256_1000"] = c2
         del cx2, wc
 
+    # one short serving level (100 Gbps offered, 2 s of arrivals) with the
+    # request latency the serving loop reports
+    if not args.no_serving and world == 1:
+        extra["serving"] = serving_levels(args, [100.0], 2.0, 30, 2000, verbose=False)[0]
+
     roofline = cell.pop("roofline")
     line = {
         "metric": METRIC,
@@ -612,12 +667,13 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_serving(args):
+def serving_levels(args, loads, seconds, n_min, n_max, verbose=True):
     """Serving loop: Poisson arrivals of packet batches (1-4096 packets of
     64-9000 bytes, 50,000 IDS-shaped patterns resident) at each offered load;
-    each level runs 10 s of arrivals or 10,000 batches, whichever is fewer.
-    Reports p50/p99 latency (completion minus scheduled arrival) and the
-    sustained throughput per load level, one JSON line per level."""
+    each level runs `seconds` of arrivals (at least n_min, at most n_max
+    batches).  Per level: p50/p99 latency (completion minus scheduled
+    arrival), its parts (how late the load generator submitted, the wait for
+    admission, the time on the GPU) and the sustained throughput."""
     import gc
     import threading
     import torch
@@ -632,7 +688,6 @@ def run_serving(args):
     table = pfac.Table(pats, 256)
     t0, s0 = batches[0]
     pfac.autotune(table, torch.from_numpy(t0).cuda(), torch.from_numpy(s0.view(np.int64)).cuda())
-    loads = [float(x) for x in args.loads.split(",")]
     biggest = max(t.size for t, _ in batches)
     out = []
     with pfac.Server(table, n_slots=args.serve_slots, device_bytes=args.serve_pool << 20,
@@ -647,9 +702,9 @@ def run_serving(args):
             gc.collect()
             gc.disable()
             rate = load * 1e9 / 8.0 / mean_bytes  # batches per second
-            n = int(min(max(args.serve_min, rate * args.serve_seconds), args.serve_max))
+            n = int(min(max(n_min, rate * seconds), n_max))
             arr = workloads.poisson_arrivals(np.random.RandomState(int(load)), rate, n)
-            ids, sched, sizes = [], [], []
+            ids, sched, sizes, late = [], [], [], []
             start = time.monotonic() + 0.05
 
             def submitter():
@@ -659,6 +714,7 @@ def run_serving(args):
                     if dt > 0:
                         time.sleep(dt)
                     t, s = pinned[k % len(pinned)]
+                    late.append(time.monotonic() - at)
                     ids.append(srv.submit(t, s))
                     sched.append(at)
                     sizes.append(t.numel())
@@ -673,24 +729,35 @@ def run_serving(args):
                     continue
                 done[r["id"]] = r
             th.join()
-            lat = []
+            lat, wait_adm, service = [], [], []
             for rid, at in zip(ids, sched):
                 r = done[rid]
                 assert r["status"] == 0
                 lat.append(r["t_done"] - at)
+                wait_adm.append(r["t_admit"] - r["t_submit"])
+                service.append(r["t_done"] - r["t_admit"])
                 srv.release(rid)
             gc.enable()
             t_end = max(done[i]["t_done"] for i in ids)
+            ms = lambda xs, q: round(1e3 * float(np.percentile(xs, q)), 3)
             line = {"impl": "ours", "mode": "serving", "offered_gbps": load,
                     "sustained_gbps": round(8.0 * sum(sizes) / (t_end - start) / 1e9, 3),
-                    "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
-                    "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                    "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
+                    "p99_submit_late_ms": ms(late, 99), "p99_admission_wait_ms": ms(wait_adm, 99),
+                    "p99_on_gpu_ms": ms(service, 99),
                     "requests": n, "mean_request_bytes": int(mean_bytes),
                     "slots": args.serve_slots}
             out.append(line)
-            print(json.dumps(line), flush=True)
+            if verbose:
+                print(json.dumps(line), flush=True)
     table.close()
     return out
+
+
+def run_serving(args):
+    """The serving sweep: one JSON line per offered load."""
+    loads = [float(x) for x in args.loads.split(",")]
+    return serving_levels(args, loads, args.serve_seconds, args.serve_min, args.serve_max)
 
 
 def main():
@@ -704,10 +771,14 @@ def main():
                     help="dram bytes per scan launch from an ncu capture of the current kernel sources")
     ap.add_argument("--ref-sample-mib", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-suffix-merge", action="store_true",
+                    help="skip the merged-trie table (reduction step 2) beside the plain one")
     ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
                     help="with several GPUs: strong = one input split by start position "
                          "(shards with a read halo, merged after the timed region); weak = "
                          "an input of the full size per GPU")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the short serving level timed after the main workload")
     ap.add_argument("--no-sweep-cell", action="store_true",
                     help="skip the alphabet-256 x 1,000-pattern cell timed after the main "
                          "workload")

@@ -93,6 +93,13 @@ typedef struct {
 /* Build flag: build the table on the host only (no device memory, no CUDA
  * call); the table then answers pfac_table_info but cannot match. */
 #define PFAC_BUILD_HOST_ONLY 1u
+/* Build flag (compressed layout): reduction step 2 of Section 3.2, equal
+ * subtrees of the last three trie levels stored once (the trie becomes a
+ * DAG).  A walk that stops inside a shared subtree finds its pattern ids in
+ * a side table keyed by its last unshared node and the symbols after it.
+ * Matches are the same; merged_trie_nodes in pfac_table_info counts the
+ * nodes kept. */
+#define PFAC_BUILD_SUFFIX_MERGE 2u
 
 /* Match options; a NULL pointer means library defaults (the table's
  * autotuned choice when pfac_autotune has run). */
@@ -187,6 +194,10 @@ typedef struct {
     uint32_t gram_len;         /* g: symbols per gram-filter string (0: none) */
     uint32_t gram_bits;        /* log2 of the gram filter's bits */
     uint64_t gram_strings;     /* g-symbol strings whose walk does something */
+    uint64_t merged_trie_nodes; /* with PFAC_BUILD_SUFFIX_MERGE: nodes after
+                                   reduction step 2 (unshared nodes plus one per
+                                   class of equal subtrees); else 0 */
+    uint64_t side_entries;     /* side-table entries of the merged trie */
 } pfac_table_info_t;
 
 /*

@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpfac.so")
+CHECKED_LIB = os.path.join(BUILD, "libpfac_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
           "--expt-relaxed-constexpr"]
@@ -48,17 +49,23 @@ def _stale(obj, src, deps):
     return any(os.path.getmtime(d) > t for d in [src] + deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checked: bool = False) -> str:
+    """Builds libpfac.so; with checked=True the bounds-checked library
+    (PFAC_CHECKED: every table, shared-memory, queue and input index of the
+    compressed-layout kernels range-checked) as libpfac_checked.so."""
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib = CHECKED_LIB if checked else LIB
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     deps = headers()
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         objs.append(obj)
         if force or _stale(obj, src, deps):
-            cmd = [cc, *COMMON, *ARCH, "-c", src, "-o", obj]
+            cmd = [cc, *COMMON, *ARCH, *(["-DPFAC_CHECKED"] if checked else []), "-c", src, "-o", obj]
             if ptxas_info and src.endswith(".cu"):
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
@@ -72,16 +79,17 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError("nvcc failed:\n" + " ".join(c) + "\n" + r.stdout + r.stderr)
-    stale_lib = not os.path.exists(LIB) or any(
-        os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    stale_lib = not os.path.exists(lib) or any(
+        os.path.getmtime(o) > os.path.getmtime(lib) for o in objs)
     if force or jobs or stale_lib:
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         r = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

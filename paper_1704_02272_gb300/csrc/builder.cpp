@@ -13,6 +13,7 @@
 #include <cmath>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -114,6 +115,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
     if (opts) o = *opts;
     if (o.layout > PFAC_LAYOUT_DENSE)
         return set_error(PFAC_EINVAL, "pfac_build: unknown layout %u", o.layout);
+    if (o.layout == PFAC_LAYOUT_DENSE && (o.flags & PFAC_BUILD_SUFFIX_MERGE))
+        return set_error(PFAC_EINVAL, "pfac_build: PFAC_BUILD_SUFFIX_MERGE needs the compressed layout");
     const uint32_t sigma = alphabet_size;
 
     try {
@@ -217,12 +220,62 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         }
         if (pool.empty()) pool.push_back(0);
 
+        // ---- reduction step 2 (Section 3.2): equal subtrees of the last three
+        // levels merged.  A node whose subtree is at most three levels tall
+        // (height 0 to 2) is a tail node; tail nodes with equal finality and
+        // equal children (symbols and merged children, compared bottom up)
+        // become one merged node, so the leaves become one (step 1, Eq. 2).  The other nodes (the root and every node of height >= 3)
+        // stay tree nodes.  Merged nodes cannot hold path-dependent outputs:
+        // a walk that stops below its last tree node u after d symbols finds
+        // its output in a side table keyed by (u, d, those d symbols).
+        const bool dag = (o.flags & PFAC_BUILD_SUFFIX_MERGE) != 0;
+        std::vector<uint8_t> upper;      // per tree node: kept as a tree node
+        std::vector<uint32_t> canon;     // per tail node: its merged node
+        std::vector<uint32_t> canon_rep; // per merged node: a tree node it stands for
+        if (dag) {
+            std::vector<uint32_t> h(Q, 0);
+            for (uint64_t v = Q; v-- > 0;) {  // breadth-first: children after parents
+                uint32_t m = 0;
+                for (uint32_t c = 0; c < nodes[v].n_child; c++)
+                    m = std::max(m, h[nodes[v].first_child + c] + 1);
+                h[v] = m;
+            }
+            upper.assign(Q, 0);
+            canon.assign(Q, 0xFFFFFFFFu);
+            for (uint64_t v = 0; v < Q; v++) upper[v] = v == 0 || h[v] >= 3;
+            std::unordered_map<std::string, uint32_t> sig;
+            std::string key;
+            for (uint32_t hh = 0; hh < 3; hh++)
+                for (uint64_t v = 1; v < Q; v++) {
+                    if (h[v] != hh) continue;
+                    key.clear();
+                    key.push_back(nodes[v].fin_lo != nodes[v].fin_hi ? 1 : 0);
+                    const uint32_t *b = &bm[(uint64_t)v * W];
+                    uint32_t ci = nodes[v].first_child;
+                    for (uint32_t w = 0; w < W; w++)
+                        for (uint32_t m = b[w]; m; m &= m - 1) {
+                            const uint32_t c = 32 * w + (uint32_t)__builtin_ctz(m);
+                            const uint32_t cc = canon[ci++];
+                            key.push_back((char)c);
+                            key.append(reinterpret_cast<const char *>(&cc), 4);
+                        }
+                    auto it = sig.find(key);
+                    if (it != sig.end()) {
+                        canon[v] = it->second;
+                    } else {
+                        canon[v] = (uint32_t)canon_rep.size();
+                        sig.emplace(key, canon[v]);
+                        canon_rep.push_back((uint32_t)v);
+                    }
+                }
+        }
+
         // ---- leaf merge (Eq. 2) and record numbering ----------------------
         std::vector<uint8_t> all_leaf(Q, 0);
         uint64_t n_leaves = 0;
         for (uint64_t v = 0; v < Q; v++) {
             if (v > 0 && nodes[v].n_child == 0) n_leaves++;
-            if (nodes[v].n_child) {
+            if (nodes[v].n_child && !dag) {
                 bool all = true;
                 for (uint32_t c = 0; c < nodes[v].n_child && all; c++)
                     all = nodes[nodes[v].first_child + c].n_child == 0;
@@ -237,27 +290,44 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         std::vector<uint32_t> rec_of(Q, NOREC);
         uint32_t n_rec = 0;
         uint64_t merged = 0;
-        for (uint64_t v = 1; v < Q; v++)
+        for (uint64_t v = 1; v < Q && !dag; v++)
             if (nodes[v].n_child == 0 && all_leaf[nodes[v].parent]) merged++;
+        // With the merge, only tree nodes are placed this way (a tail node's
+        // record is its merged node's, after all tree records); the tree
+        // children of a node whose children are all tree nodes stay one
+        // contiguous group.
         auto rec_children = [&](uint32_t v) -> uint32_t {
+            if (dag) return upper[v] ? nodes[v].n_child : 0u;
             return all_leaf[v] ? 0u : nodes[v].n_child;
         };
+        auto placed = [&](uint32_t c) { return !dag || upper[c]; };
         std::vector<uint32_t> groups;  // nodes whose child group is still to place
         groups.reserve(Q / 2 + 1);
         auto place_chain = [&](uint32_t m) {
-            while (rec_children(m) == 1) {
+            while (rec_children(m) == 1 && placed(nodes[m].first_child)) {
                 m = nodes[m].first_child;
                 rec_of[m] = n_rec++;
             }
-            if (rec_children(m) >= 2) groups.push_back(m);
+            if (rec_children(m) >= 1) groups.push_back(m);
         };
+        uint32_t n_upper = 0;
         rec_of[0] = n_rec++;
         place_chain(0);
         for (size_t gi = 0; gi < groups.size(); gi++) {
             const uint32_t v = groups[gi];
             const uint32_t f = nodes[v].first_child, nc = nodes[v].n_child;
-            for (uint32_t c = 0; c < nc; c++) rec_of[f + c] = n_rec++;
-            for (uint32_t c = 0; c < nc; c++) place_chain(f + c);
+            for (uint32_t c = 0; c < nc; c++)
+                if (placed(f + c)) rec_of[f + c] = n_rec++;
+            for (uint32_t c = 0; c < nc; c++)
+                if (placed(f + c)) place_chain(f + c);
+        }
+        if (dag) {
+            n_upper = n_rec;
+            if ((uint64_t)n_upper + canon_rep.size() >= (1ull << 30))
+                return set_error(PFAC_EINVAL, "pfac_build: merged trie too large");
+            for (uint64_t v = 1; v < Q; v++)
+                if (!upper[v]) rec_of[v] = n_upper + canon[v];
+            n_rec = n_upper + (uint32_t)canon_rep.size();
         }
 
         // ---- prefix nodes -------------------------------------------------
@@ -300,10 +370,13 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         // prefix node of depth k: bitmap, block counts, entries (Eq. 1 on the
         // collapsed first k levels)
         std::vector<uint32_t> Fv[KMAX + 1], Cv[KMAX + 1], Ev[KMAX + 1], Mv[KMAX + 1];
+        // merged trie: per entry whose depth-k state is a merged node, its last
+        // tree ancestor's record and the depth below it (0 for tree nodes)
+        std::vector<uint32_t> E2v[KMAX + 1];
         std::vector<uint8_t> Bv[KMAX + 1];
         uint32_t cshift[KMAX + 1] = {0};
         uint64_t sz_F[KMAX + 1] = {0}, sz_C[KMAX + 1] = {0}, sz_E[KMAX + 1] = {0},
-                 sz_M[KMAX + 1] = {0}, sz_B[KMAX + 1] = {0};
+                 sz_M[KMAX + 1] = {0}, sz_B[KMAX + 1] = {0}, sz_E2[KMAX + 1] = {0};
         if (!dense)
             for (uint32_t k = kmin; k <= kmax; k++) {
                 const uint64_t ent = 1ull << (k * bps);
@@ -318,7 +391,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 const bool with_b = k * bps <= BYTES_MAX_BITS;
                 if (with_b) Bv[k].assign(ent < 4 ? 4 : ent, 0);
                 for (uint64_t x = 0; x < ent; x++) {
-                    uint32_t v = 0, e = 0;
+                    uint32_t v = 0, e = 0, e2 = 0;
                     bool stopped = false;
                     for (uint32_t i = 0; i < k; i++) {
                         const int64_t ch = child_of(v, (uint32_t)(x >> (bps * i)) & smask);
@@ -335,6 +408,14 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                             e = fin_code[v];  // a leaf ends the walk
                         } else {
                             e = D_CONT | rec_of[v];
+                            if (dag && !upper[v]) {
+                                uint32_t u = v, d = 0;
+                                while (!upper[u]) {
+                                    u = nodes[u].parent;
+                                    d++;
+                                }
+                                e2 = rec_of[u] | (d << 30);
+                            }
                             if (fin_code[v] == 0) {
                                 mask = 0;
                                 bucket = 0;
@@ -349,6 +430,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                     if (e) {
                         Fv[k][x >> 5] |= 1u << (x & 31);
                         Ev[k].push_back(e);
+                        if (dag) E2v[k].push_back(e2);
                         Mv[k].push_back(mask);
                         if (with_b) Bv[k][x] = (uint8_t)bucket;
                     }
@@ -361,10 +443,12 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 if (Ev[k].empty()) {
                     Ev[k].push_back(0);
                     Mv[k].push_back(0);
+                    if (dag) E2v[k].push_back(0);
                 }
                 sz_F[k] = fw * 4;
                 sz_C[k] = Cv[k].size() * 4;
                 sz_E[k] = Ev[k].size() * 4;
+                sz_E2[k] = E2v[k].size() * 4;
                 // narrow masks for small alphabets: mask_bits(sigma) bits per
                 // entry, packed low entry first (an all-ones mask still means
                 // "keep whatever follows")
@@ -471,16 +555,36 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         uint64_t sz_dfin = dense ? Q * 4 : 0;
 
         // records and merged-leaf outputs
-        std::vector<uint32_t> rec, finv;
+        std::vector<uint32_t> rec, finv, ind;
         if (!dense) {
             rec.assign((uint64_t)n_rec * RW, 0);
             if (W == 1) finv.assign(n_rec, 0);
             for (uint64_t v = 0; v < Q; v++) {
                 uint32_t r = rec_of[v];
                 if (r == NOREC) continue;
+                // a merged node's record comes from the one tree node it keeps
+                if (dag && !upper[v] && canon_rep[canon[v]] != v) continue;
                 uint32_t *R = &rec[(uint64_t)r * RW];
                 uint32_t meta = 0;
-                if (all_leaf[v]) {
+                if (dag && nodes[v].n_child) {
+                    // children through the indirection list unless they are all
+                    // tree nodes (then consecutive records, Eq. 1 directly)
+                    bool direct = upper[v] != 0;
+                    for (uint32_t c = 0; c < nodes[v].n_child && direct; c++)
+                        direct = upper[nodes[v].first_child + c] != 0;
+                    if (direct) {
+                        meta = rec_of[nodes[v].first_child];
+                        for (uint32_t c = 0; c < nodes[v].n_child; c++)
+                            if (rec_of[nodes[v].first_child + c] != meta + c)
+                                return set_error(PFAC_EDEVICE, "pfac_build: internal error (dag)");
+                    } else {
+                        // META_ALL_LEAF marks the record for the walk's slow
+                        // path, which follows ind[] and tracks the tail
+                        meta = META_ALL_LEAF | META_IND | (uint32_t)ind.size();
+                        for (uint32_t c = 0; c < nodes[v].n_child; c++)
+                            ind.push_back(rec_of[nodes[v].first_child + c]);
+                    }
+                } else if (all_leaf[v]) {
                     meta = META_ALL_LEAF | (uint32_t)leaf_fin.size();
                     for (uint32_t c = 0; c < nodes[v].n_child; c++)
                         leaf_fin.push_back(fin_code[nodes[v].first_child + c]);
@@ -493,15 +597,17 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                             return set_error(PFAC_EDEVICE, "pfac_build: internal error (records)");
                 }
                 for (uint32_t w = 0; w < W; w++) R[w] = bm[v * W + w];
+                // a merged node's outputs depend on the path: the side table
+                const uint32_t fv = dag && !upper[v] ? 0u : fin_code[v];
                 if (W == 1) {
                     R[1] = meta;
-                    finv[r] = fin_code[v];
+                    finv[r] = fv;
                 } else if (W == 2) {
                     R[2] = meta;
-                    R[3] = fin_code[v];
+                    R[3] = fv;
                 } else {
                     R[8] = meta;
-                    R[9] = fin_code[v];
+                    R[9] = fv;
                     uint32_t cum = 0;
                     uint32_t c4[2] = {0, 0};
                     for (uint32_t w = 0; w < 8; w++) {
@@ -515,6 +621,43 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         }
         if (leaf_fin.empty()) leaf_fin.push_back(0);
         uint64_t sz_leaf = dense ? 0 : leaf_fin.size() * 4;
+        if (ind.empty()) ind.push_back(0);
+        const uint64_t sz_ind = dag ? ind.size() * 4 : 0;
+
+        // side table of the merged trie: for every tail node with output, the
+        // output under the key (its last tree ancestor's record, the depth
+        // below it, the symbols from there); open addressing, linear probes
+        std::vector<uint64_t> side_keys;
+        std::vector<uint32_t> side_vals;
+        uint32_t side_log = 0;
+        uint64_t side_n = 0;
+        if (dag) {
+            std::vector<uint64_t> ks;
+            std::vector<uint32_t> vs;
+            for (uint64_t v = 1; v < Q; v++) {
+                if (upper[v] || !fin_code[v]) continue;
+                uint32_t u = (uint32_t)v, tp = 0, d = 0;
+                uint32_t syms[4] = {0, 0, 0, 0};
+                while (!upper[u]) {
+                    syms[d++] = sym_at(nodes[u].lo, nodes[u].depth - 1);
+                    u = nodes[u].parent;
+                }
+                for (uint32_t i = 0; i < d; i++) tp |= syms[d - 1 - i] << (bps * i);
+                ks.push_back(dag_side_key(rec_of[u], d, tp));
+                vs.push_back(fin_code[v]);
+            }
+            side_n = ks.size();
+            while ((1ull << side_log) < 2 * std::max<uint64_t>(side_n, 8)) side_log++;
+            side_keys.assign(1ull << side_log, DAG_SIDE_EMPTY);
+            side_vals.assign(1ull << side_log, 0);
+            for (size_t i = 0; i < ks.size(); i++) {
+                uint64_t h = dag_side_slot(ks[i], side_log);
+                while (side_keys[h] != DAG_SIDE_EMPTY) h = (h + 1) & ((1ull << side_log) - 1);
+                side_keys[h] = ks[i];
+                side_vals[h] = vs[i];
+            }
+        }
+        const uint64_t sz_sk = side_keys.size() * 8, sz_sv = side_vals.size() * 4;
 
         // blob layout
         uint64_t off = 0;
@@ -525,8 +668,9 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         };
         uint64_t o_rec = place(sz_rec), o_fin = place(sz_fin), o_leaf = place(sz_leaf),
                  o_pool = place(sz_pool);
+        const uint64_t o_ind = place(sz_ind), o_sk = place(sz_sk), o_sv = place(sz_sv);
         uint64_t o_F[KMAX + 1] = {0}, o_C[KMAX + 1] = {0}, o_E[KMAX + 1] = {0},
-                 o_M[KMAX + 1] = {0}, o_B[KMAX + 1] = {0};
+                 o_M[KMAX + 1] = {0}, o_B[KMAX + 1] = {0}, o_E2[KMAX + 1] = {0};
         if (!dense)
             for (uint32_t k = kmin; k <= kmax; k++) {
                 o_F[k] = place(sz_F[k]);
@@ -534,6 +678,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 o_E[k] = place(sz_E[k]);
                 o_M[k] = place(sz_M[k]);
                 o_B[k] = place(sz_B[k]);
+                o_E2[k] = place(sz_E2[k]);
             }
         const uint64_t o_G = place(sz_G);
         const uint64_t o_po = place(sz_po), o_pb = place(sz_pb);
@@ -549,8 +694,12 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         put(o_fin, finv.data(), sz_fin);
         put(o_leaf, leaf_fin.data(), sz_leaf);
         put(o_pool, pool.data(), sz_pool);
+        put(o_ind, ind.data(), sz_ind);
+        put(o_sk, side_keys.data(), sz_sk);
+        put(o_sv, side_vals.data(), sz_sv);
         if (!dense)
             for (uint32_t k = kmin; k <= kmax; k++) {
+                put(o_E2[k], E2v[k].data(), sz_E2[k]);
                 put(o_F[k], Fv[k].data(), sz_F[k]);
                 put(o_C[k], Cv[k].data(), sz_C[k]);
                 put(o_E[k], Ev[k].data(), sz_E[k]);
@@ -613,6 +762,15 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         dv.fin = (const uint32_t *)(B + o_fin);
         dv.leaf_fin = (const uint32_t *)(B + o_leaf);
         dv.pool = (const uint32_t *)(B + o_pool);
+        dv.pool_words = (uint32_t)pool.size();
+        dv.leaf_words = (uint32_t)leaf_fin.size();
+        dv.dag = dag ? 1u : 0u;
+        dv.n_upper = dag ? n_upper : n_rec;
+        dv.ind = (const uint32_t *)(B + o_ind);
+        dv.ind_words = dag ? (uint32_t)ind.size() : 0u;
+        dv.side_keys = dag ? (const uint64_t *)(B + o_sk) : nullptr;
+        dv.side_vals = dag ? (const uint32_t *)(B + o_sv) : nullptr;
+        dv.side_log = side_log;
         if (!dense)
             for (uint32_t k = kmin; k <= kmax; k++) {
                 dv.F[k] = (const uint32_t *)(B + o_F[k]);
@@ -623,6 +781,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 dv.n_e[k] = (uint32_t)Ev[k].size();
                 dv.m_words[k] = (uint32_t)Mv[k].size();
                 dv.B[k] = sz_B[k] ? (const uint8_t *)(B + o_B[k]) : nullptr;
+                dv.E2[k] = dag ? (const uint32_t *)(B + o_E2[k]) : nullptr;
             }
         dv.G = g_len ? (const uint32_t *)(B + o_G) : nullptr;
         dv.trunc = o.truncate_depth;
@@ -657,6 +816,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         I.gram_len = g_len;
         I.gram_bits = g_bits;
         I.gram_strings = g_set;
+        I.merged_trie_nodes = dag ? (uint64_t)n_upper + canon_rep.size() : 0;
+        I.side_entries = side_n;
         *out = t;
         return PFAC_OK;
     } catch (const std::bad_alloc &) {

@@ -83,6 +83,7 @@ struct MatchParams {
     const uint32_t *F;    // prefix node of depth k: bitmap,
     const uint32_t *C;    //   block counts,
     const uint32_t *E;    //   entries
+    const uint32_t *E2;   //   merged trie: last tree record | depth << 30 per entry
     const uint32_t *M;    //   child masks of the entries
     uint32_t tbl_words;   // shared-memory words: bitmap copies (or dense rows)
     uint32_t tbl_c_words;
@@ -108,6 +109,24 @@ struct MatchParams {
 };
 
 constexpr uint32_t UNIT_NONE = 0xFFFFFFFFu;
+
+// The bounds-checked build (compiled with PFAC_CHECKED, a separate library):
+// the compressed-layout kernels pass every table, shared-memory, queue and
+// input index through chk(), which, for an index at or past its bound,
+// records ST_DEVICE in the call's status word (the call then reports
+// PFAC_EDEVICE) and returns 0, always a valid index, so that no access leaves
+// its array.  In the regular build chk() is the index itself.
+#ifdef PFAC_CHECKED
+constexpr bool CHECKED = true;
+__device__ __forceinline__ uint64_t chk(const MatchParams &P, uint64_t i, uint64_t n) {
+    if (i < n) return i;
+    atomicOr(&P.hdr->status, ST_DEVICE);
+    return 0;
+}
+#else
+constexpr bool CHECKED = false;
+__device__ __forceinline__ uint64_t chk(const MatchParams &, uint64_t i, uint64_t) { return i; }
+#endif
 
 // ------------------------------------------------------------ PTX helpers --
 
@@ -204,6 +223,24 @@ __device__ __forceinline__ uint32_t fin_len(const uint32_t *__restrict__ pool, u
 
 __device__ __forceinline__ const uint32_t *fin_ids(const uint32_t *__restrict__ pool, uint32_t f) {
     return pool + (f >> FIN_LEN_BITS) + (((f & FIN_LEN_ESC) == FIN_LEN_ESC) ? 1 : 0);
+}
+
+// fin_len / fin_ids of the table's pool with the list's words checked
+// against the pool (a list past the pool reads as empty).
+__device__ __forceinline__ uint32_t fin_len_c(const MatchParams &P, uint32_t f) {
+    const uint32_t off = (uint32_t)chk(P, f >> FIN_LEN_BITS, P.T.pool_words);
+    const bool esc = (f & FIN_LEN_ESC) == FIN_LEN_ESC;
+    uint32_t l = esc ? __ldg(P.T.pool + off) : (f & FIN_LEN_ESC);
+    if (CHECKED && (uint64_t)off + (esc ? 1u : 0u) + l > P.T.pool_words) {
+        chk(P, 1, 0);
+        l = 0;
+    }
+    return l;
+}
+
+__device__ __forceinline__ const uint32_t *fin_ids_c(const MatchParams &P, uint32_t f) {
+    const uint32_t off = (uint32_t)chk(P, f >> FIN_LEN_BITS, P.T.pool_words);
+    return P.T.pool + off + (((f & FIN_LEN_ESC) == FIN_LEN_ESC) ? 1 : 0);
 }
 
 // ------------------------------------------------------------ walks --------
@@ -489,7 +526,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_scan_dense(const MatchParams P,
         for (int j = 0; j < BPT; j++) {
             if (fr[j]) {
                 nm++;
-                nk += fin_len(P.T.pool, fr[j]);
+                nk += fin_len_c(P, fr[j]);
             }
         }
         uint64_t total;
@@ -515,8 +552,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_scan_dense(const MatchParams P,
             for (int j = 0; j < BPT; j++) {
                 const uint32_t f = fr[j];
                 if (!f) continue;
-                const uint32_t L = fin_len(P.T.pool, f);
-                const uint32_t *ids = fin_ids(P.T.pool, f);
+                const uint32_t L = fin_len_c(P, f);
+                const uint32_t *ids = fin_ids_c(P, f);
                 const uint64_t pk = (P.pos_base + tile_start + p0 + j) << PFAC_ID_BITS;
                 for (uint32_t e = 0; e < L; e++, o++)
                     if (o < P.cap) P.out[o] = pk | __ldg(ids + e);

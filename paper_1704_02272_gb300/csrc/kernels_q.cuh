@@ -132,6 +132,54 @@ __device__ __forceinline__ int take_step(uint32_t sigma, uint32_t c, uint32_t wo
     return (meta & META_ALL_LEAF) ? 2 : 0;
 }
 
+// Walk of the merged trie (reduction step 2 of Section 3.2) from tree record
+// s at slice offset q: records with META_IND reach their children through
+// ind[]; below the last tree record u the walk counts its depth d and packs
+// the symbols taken, and a stop there takes its output from the side table
+// under (u, d, symbols), absent meaning none.  Every walk that reaches an
+// indirect record, or a prefix entry whose state is a tail record, ends
+// here; they are the walks that come within three levels of a pattern's
+// end.
+template <int W>
+__device__ __noinline__ uint32_t dag_walk(const MatchParams *PP, uint32_t s, uint32_t q,
+                                          uint32_t lim, uint32_t unit) {
+    const MatchParams &P = *PP;
+    const uint64_t ub = (uint64_t)unit << SLICE_SHIFT;
+    const uint32_t sigma = P.T.sigma, n_upper = P.T.n_upper, bps = P.T.bps;
+    uint32_t u = s, d = 0, tp = 0, f = 0;
+    for (;;) {
+        const uint32_t c = q < lim ? (uint32_t)__ldg(P.in + chk(P, ub + q, P.n)) : 0x100u;
+        uint32_t word, below, meta;
+        load_step<W>(P.T.rec, (uint32_t)chk(P, s, P.T.n_rec), c, word, below, meta, f);
+        const uint32_t bit = c & 31;
+        if (c >= sigma || !((word >> bit) & 1u)) break;
+        const uint32_t i = (meta & META_BASE_MASK) + below +
+                           (uint32_t)__popc(word & ((1u << bit) - 1u));
+        s = (meta & META_IND) ? __ldg(P.T.ind + chk(P, i, P.T.ind_words)) : i;
+        q++;
+        if (s < n_upper) {
+            u = s;
+            d = 0;
+            tp = 0;
+        } else {
+            tp |= c << (bps * d);
+            d++;
+        }
+    }
+    if (s < n_upper) return W == 1 ? __ldg(P.T.fin + chk(P, s, P.T.n_rec)) : f;
+    const uint64_t key = dag_side_key(u, d, tp);
+    const uint64_t m = (1ull << P.T.side_log) - 1u;
+    uint64_t h = dag_side_slot(key, P.T.side_log);
+    // at most half the slots are taken, so a probe meets the key or a hole
+    for (uint64_t i = 0; i <= m; i++) {
+        const uint64_t kk = __ldg(reinterpret_cast<const unsigned long long *>(P.T.side_keys) + h);
+        if (kk == key) return __ldg(P.T.side_vals + h);
+        if (kk == DAG_SIDE_EMPTY) break;
+        h = (h + 1u) & m;
+    }
+    return 0;
+}
+
 // Resolves queue entries [e0, e0 + 32 * walks_per_lane(W)): a few rounds
 // with every lane advancing its walks together (most walks end within one or
 // two levels), then the walks still running are compacted one per lane, so
@@ -147,7 +195,9 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
     const uint32_t sigma = P.T.sigma, k = P.k, rep = P.rep_log2;
     const uint32_t *__restrict__ rec = P.T.rec;
     uint32_t st[QU], qq[QU], lim[QU], fin[QU], unit[QU];
-    int state[QU];  // -1 idle, 0 walking, 1 stopped at st, 2 stopped on merged leaf st, 3 done
+    // -1 idle, 0 walking, 1 stopped at st, 2 stopped on merged leaf st, 3 done,
+    // 4 to finish on the merged trie's slow path from tree record st at qq
+    int state[QU];
     // ---- phase A: prefix entries (independent loads for all entries)
 #pragma unroll
     for (int u = 0; u < QU; u++) {
@@ -167,12 +217,22 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                 state[u] = 0;
                 qq[u] = p;
             } else {
-                const uint32_t r = prefix_rank(Fs, rep, Cs, P.c_shift, en.x);
+                const uint32_t xx = (uint32_t)chk(P, en.x, 1ull << (k * P.T.bps));
+                const uint32_t r = (uint32_t)chk(P, prefix_rank(Fs, rep, Cs, P.c_shift, xx),
+                                                 P.T.n_e[k]);
                 const uint32_t ev = VAR == VAR_FE ? Es[r] : __ldg(P.E + r);
                 qq[u] = p + k;
                 if (ev & D_CONT) {
                     state[u] = 0;
                     st[u] = ev & D_VAL_MASK;
+                    if (st[u] >= P.T.n_upper) {
+                        // a tail record of the merged trie: walk again from
+                        // the last tree record, d symbols back
+                        const uint32_t e2 = __ldg(P.E2 + r);
+                        state[u] = 4;
+                        st[u] = e2 & 0x3FFFFFFFu;
+                        qq[u] -= e2 >> 30;
+                    }
                 } else {
                     state[u] = 3;
                     fin[u] = ev;
@@ -191,12 +251,12 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
         for (int u = 0; u < QU; u++) {
             if (state[u] != 0) continue;
             const uint64_t ab = ((uint64_t)unit[u] << SLICE_SHIFT) + qq[u];
-            c[u] = qq[u] < lim[u] ? (uint32_t)__ldg(P.in + ab) : 0x100u;
+            c[u] = qq[u] < lim[u] ? (uint32_t)__ldg(P.in + chk(P, ab, P.n)) : 0x100u;
         }
 #pragma unroll
         for (int u = 0; u < QU; u++) {
             if (state[u] != 0) continue;
-            load_step<W>(rec, st[u], c[u], wd[u], bl[u], mt[u], f1[u]);
+            load_step<W>(rec, (uint32_t)chk(P, st[u], P.T.n_rec), c[u], wd[u], bl[u], mt[u], f1[u]);
         }
 #pragma unroll
         for (int u = 0; u < QU; u++) {
@@ -209,6 +269,9 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                 if (W == 1) st[u] = cur;
                 else fin[u] = f1[u];
                 state[u] = W == 1 ? 1 : 3;
+            } else if (P.T.dag) {
+                st[u] = cur;
+                state[u] = 4;
             } else {
                 state[u] = 2;
             }
@@ -234,8 +297,9 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
     // stored after phase D so the loads' latency overlaps the long walks
 #pragma unroll
     for (int u = 0; u < QU; u++) {
-        if (state[u] == 1) fin[u] = __ldg(P.T.fin + st[u]);
-        else if (state[u] == 2) fin[u] = __ldg(P.T.leaf_fin + st[u]);
+        if (state[u] == 1) fin[u] = __ldg(P.T.fin + chk(P, st[u], P.T.n_rec));
+        else if (state[u] == 2) fin[u] = __ldg(P.T.leaf_fin + chk(P, st[u], P.T.leaf_words));
+        else if (state[u] == 4) fin[u] = dag_walk<W>(&P, st[u], qq[u], lim[u], unit[u]);
     }
     // ---- phase D: the long walks, one per lane
     for (uint32_t t0 = 0; t0 < nt; t0 += 32) {
@@ -257,9 +321,10 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                 uint32_t c[TS], wd[TS], bl[TS], mt[TS], f1[TS];
 #pragma unroll
                 for (int i = 0; i < TS; i++) {
-                    c[i] = q1 + i < en.lim ? (uint32_t)__ldg(P.in + ub + q1 + i) : 0x100u;
+                    c[i] = q1 + i < en.lim ? (uint32_t)__ldg(P.in + chk(P, ub + q1 + i, P.n)) : 0x100u;
                     if (i == 0 || s1 + i < n_rec) {
-                        load_step<W>(rec, s1 + i, c[i], wd[i], bl[i], mt[i], f1[i]);
+                        load_step<W>(rec, (uint32_t)chk(P, s1 + i, n_rec), c[i], wd[i], bl[i],
+                                     mt[i], f1[i]);
                     } else {
                         wd[i] = bl[i] = mt[i] = f1[i] = 0;
                     }
@@ -272,12 +337,13 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                     const uint32_t cur = s1 + i;
                     const int r = take_step(sigma, c[i], wd[i], bl[i], mt[i], nx);
                     if (r == 1) {
-                        f = W == 1 ? __ldg(P.T.fin + cur) : f1[i];
+                        f = W == 1 ? __ldg(P.T.fin + chk(P, cur, n_rec)) : f1[i];
                         done = true;
                         break;
                     }
                     if (r == 2) {
-                        f = __ldg(P.T.leaf_fin + nx);
+                        f = P.T.dag ? dag_walk<W>(&P, cur, q1 + i, en.lim, en.unit)
+                                    : __ldg(P.T.leaf_fin + chk(P, nx, P.T.leaf_words));
                         done = true;
                         break;
                     }
@@ -339,7 +405,7 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
         const uint8_t *Bb = reinterpret_cast<const uint8_t *>(Bs);
 #pragma unroll
         for (int j = 0; j < QBPT; j++)
-            if (Bb[symbols_at<BPS>(bs, j) & kmask]) surv |= 1u << j;
+            if (Bb[chk(P, symbols_at<BPS>(bs, j) & kmask, P.tbl_b_words * 4ull)]) surv |= 1u << j;
     } else if (P.tbl_g_words == 0) {
         const uint32_t kmask = (1u << (BPS * k)) - 1u;  // k * BPS >= 5
         // Byte offset of the word of index t in copy `copy`:
@@ -358,7 +424,7 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
         for (int j = 0; j < QBPT; j++) {
             const uint32_t t = symbols_at<BPS>(bs, j);
             const uint32_t w = *reinterpret_cast<const uint32_t *>(
-                Fb + ((__funnelshift_r(t, t, ramt) & wmask) | c4));
+                Fb + chk(P, (__funnelshift_r(t, t, ramt) & wmask) | c4, P.tbl_words * 4ull));
             acc = __funnelshift_r(acc, __funnelshift_r(w, w, t), 1);
         }
         surv = acc >> (32 - QBPT);
@@ -377,8 +443,8 @@ __device__ __forceinline__ void filter_slice(const MatchParams &P, const uint8_t
         for (int j = 0; j < QBPT; j++) {
             const uint32_t t = symbols_at<BPS>(bs, j);
             const uint32_t y = t * gm;
-            const uint32_t w =
-                *reinterpret_cast<const uint32_t *>(Gb + (((y >> gsh) & gwm) | c4));
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(
+                Gb + chk(P, ((y >> gsh) & gwm) | c4, P.tbl_g_words * 4ull));
             acc = __funnelshift_r(acc, __funnelshift_r(w, w, t), 1);  // bit t & 31
         }
         surv = acc >> (32 - QBPT);
@@ -497,21 +563,23 @@ __device__ __forceinline__ bool mask_keep(const MatchParams &P, uint32_t x, uint
         const uint32_t qb = p + P.k, sigma = P.T.sigma;
         if (qb < staged && qb < lim) {
             extern __shared__ __align__(128) uint8_t smem[];
-            const uint32_t v = smem[x], cs = sb[qb];
+            const uint32_t v = smem[chk(P, x, P.tbl_b_words * 4ull)], cs = sb[chk(P, qb, QSTAGE)];
             if (v != 0xFFu && (cs >= sigma || !((v >> byte_bucket(cs, sigma)) & 1u))) return false;
         }
     }
     if (P.tbl_g_words) {
-        const uint32_t fwd = Fs[(x >> 5) << P.rep_log2];
+        const uint32_t fwd = Fs[chk(P, (x >> 5) << P.rep_log2, P.tbl_words)];
         if (!((fwd >> (x & 31)) & 1u)) return false;
     }
     if (!P.tbl_m_words) return true;
     const uint32_t qn1 = p + P.k, sigma = P.T.sigma;
     if (qn1 >= staged || qn1 >= lim) return true;
-    const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, x);
+    const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift,
+                                   (uint32_t)chk(P, x, 1ull << (P.k * P.T.bps)));
     const uint32_t mb = mask_bits(sigma), ones = mb == 32 ? 0xFFFFFFFFu : (1u << mb) - 1u;
-    const uint32_t mr = mb == 32 ? Ms[r] : (Ms[(r * mb) >> 5] >> ((r * mb) & 31)) & ones;
-    const uint32_t cs = sb[qn1];
+    const uint32_t mi = (uint32_t)chk(P, mb == 32 ? r : (r * mb) >> 5, P.tbl_m_words);
+    const uint32_t mr = mb == 32 ? Ms[mi] : (Ms[mi] >> ((r * mb) & 31)) & ones;
+    const uint32_t cs = sb[chk(P, qn1, QSTAGE)];
     return cs < sigma ? ((mr >> child_hash(cs, sigma)) & 1u) != 0 : mr == ones;
 }
 
@@ -571,19 +639,18 @@ __device__ __forceinline__ void flush_records_c(const MatchParams &P, QEntry *q,
         const bool last = (pos[u] & LAST_FLAG) != 0;
         const uint32_t base = q[e - slot].x;
         const uint32_t rank = pre[u] - base + (unit[u] == carry_unit ? carry : 0u);
+        const uint32_t uu = (uint32_t)chk(P, unit[u], P.n_tiles);
         if (fin[u]) {
-            if (rank < cap)
-                P.recs[(size_t)unit[u] * cap + rank] = ((uint64_t)p << 32) | fin[u];
-            atomicAdd((unsigned long long *)(P.tile_k + unit[u]),
-                      (unsigned long long)fin_len(P.T.pool, fin[u]));
+            if (rank < cap) P.recs[(size_t)uu * cap + rank] = ((uint64_t)p << 32) | fin[u];
+            atomicAdd((unsigned long long *)(P.tile_k + uu), (unsigned long long)fin_len_c(P, fin[u]));
         }
         const uint32_t m = rank + (fin[u] ? 1u : 0u);
         if (last) {
             if (m > cap) {
-                P.tile_m[unit[u]] = UNIT_OVF;
-                P.ovf_list[atomicAdd(&P.hdr->ovf_count, 1u)] = unit[u];
+                P.tile_m[uu] = UNIT_OVF;
+                P.ovf_list[chk(P, atomicAdd(&P.hdr->ovf_count, 1u), P.n_tiles)] = uu;
             } else {
-                P.tile_m[unit[u]] = m;
+                P.tile_m[uu] = m;
             }
         } else if (e == n - 1) {
             cu = unit[u];
@@ -846,7 +913,7 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
                         ((uint64_t)(pos[u] & 0x3FFu) << 32) | fin[u];
                 nrec += __popc(b);
             }
-            const uint32_t L = fin[u] ? fin_len(P.T.pool, fin[u]) : 0u;
+            const uint32_t L = fin[u] ? fin_len_c(P, fin[u]) : 0u;
             uint32_t inc = L;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -855,7 +922,7 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
             }
             const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
             if (emit && L) {
-                const uint32_t *ids = fin_ids(P.T.pool, fin[u]);
+                const uint32_t *ids = fin_ids_c(P, fin[u]);
                 const uint64_t pk = (P.pos_base + ustart + (pos[u] & 0x3FFu)) << PFAC_ID_BITS;
                 uint64_t o = obase + keys + inc - L;
                 for (uint32_t e = 0; e < L; e++, o++)
@@ -875,7 +942,7 @@ __device__ __forceinline__ uint64_t resolve_slice(const MatchParams &P, QEntry *
 // tables leave room in shared memory).  The int argument is unused (the
 // launch signature is shared with the uncompressed kernel).
 template <int W, int BPS, int VAR, int EMIT, int NW>
-__global__ void __launch_bounds__(NW * 32, 1) k_scanq(const MatchParams P, const int) {
+__global__ void __launch_bounds__(NW * 32, 1) k_scanq(const __grid_constant__ MatchParams P, const int) {
     constexpr uint32_t QTHREADS = NW * 32;
     constexpr bool emit = EMIT != 0;
     extern __shared__ __align__(128) uint8_t smem[];

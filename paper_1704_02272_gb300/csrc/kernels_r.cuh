@@ -162,15 +162,16 @@ __device__ __forceinline__ uint32_t r_addr(uint32_t t, uint32_t c4, uint32_t ama
 // set when position j's window passes the filter): fewer registers than the
 // two-slice form, for the wider CTA.
 template <int BPS, int REP, int GRAM>
-__device__ __forceinline__ uint32_t r_first_stage1(const uint32_t (&w)[5], uint32_t c4,
-                                                   uint32_t amask, uint32_t gm, uint32_t gmh) {
+__device__ __forceinline__ uint32_t r_first_stage1(const MatchParams &P, const uint32_t (&w)[5],
+                                                   uint32_t c4, uint32_t amask, uint32_t gm,
+                                                   uint32_t gmh, uint32_t tbytes) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint32_t acc[2] = {0, 0};
 #pragma unroll
     for (int j = 0; j < 16; j++) {
         const uint32_t t = r_twin<BPS>(w, j);
-        const uint32_t x =
-            *reinterpret_cast<const uint32_t *>(smem + r_addr<REP, GRAM>(t, c4, amask, gm, gmh));
+        const uint32_t x = *reinterpret_cast<const uint32_t *>(
+            smem + chk(P, r_addr<REP, GRAM>(t, c4, amask, gm, gmh), tbytes));
         acc[j >> 3] = __funnelshift_r(acc[j >> 3], __funnelshift_r(x, x, t), 1);
     }
     return (acc[0] >> 24) | ((acc[1] >> 16) & 0xFF00u);
@@ -182,18 +183,19 @@ __device__ __forceinline__ uint32_t r_first_stage1(const uint32_t (&w)[5], uint3
 // sits at the start of the dynamic shared memory, so a lookup needs no base
 // register.  Each slice's bits gather in two chains of eight.
 template <int BPS, int REP, int GRAM>
-__device__ __forceinline__ void r_first_stage2(const uint32_t (&wa)[5], const uint32_t (&wb)[5],
-                                               uint32_t c4, uint32_t amask, uint32_t gm,
-                                               uint32_t gmh, uint32_t &sa, uint32_t &sb) {
+__device__ __forceinline__ void r_first_stage2(const MatchParams &P, const uint32_t (&wa)[5],
+                                               const uint32_t (&wb)[5], uint32_t c4,
+                                               uint32_t amask, uint32_t gm, uint32_t gmh,
+                                               uint32_t tbytes, uint32_t &sa, uint32_t &sb) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint32_t acc_a[2] = {0, 0}, acc_b[2] = {0, 0};
 #pragma unroll
     for (int j = 0; j < 16; j++) {
         const uint32_t ta = r_twin<BPS>(wa, j), tb = r_twin<BPS>(wb, j);
-        const uint32_t xa =
-            *reinterpret_cast<const uint32_t *>(smem + r_addr<REP, GRAM>(ta, c4, amask, gm, gmh));
-        const uint32_t xb =
-            *reinterpret_cast<const uint32_t *>(smem + r_addr<REP, GRAM>(tb, c4, amask, gm, gmh));
+        const uint32_t xa = *reinterpret_cast<const uint32_t *>(
+            smem + chk(P, r_addr<REP, GRAM>(ta, c4, amask, gm, gmh), tbytes));
+        const uint32_t xb = *reinterpret_cast<const uint32_t *>(
+            smem + chk(P, r_addr<REP, GRAM>(tb, c4, amask, gm, gmh), tbytes));
         // bit t & 31 of each word to bit 0, then into the top of acc
         acc_a[j >> 3] = __funnelshift_r(acc_a[j >> 3], __funnelshift_r(xa, xa, ta), 1);
         acc_b[j >> 3] = __funnelshift_r(acc_b[j >> 3], __funnelshift_r(xb, xb, tb), 1);
@@ -215,15 +217,17 @@ __device__ __forceinline__ bool r_keep(const MatchParams &P, uint32_t t, bool ha
                                        uint32_t &x) {
     const uint32_t kb = BPS * P.k;
     x = kb >= 32 ? t : (t & ((1u << kb) - 1u));
+    x = (uint32_t)chk(P, x, 1ull << kb);
     if (GRAM) {
         const uint32_t fw = Fs[(x >> 5) << P.rep_log2];
         if (!((fw >> (x & 31)) & 1u)) return false;
     }
     if (!P.tbl_m_words || !has_next) return true;
-    const uint32_t r = prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, x);
+    const uint32_t r = (uint32_t)chk(P, prefix_rank(Fs, P.rep_log2, Cs, P.c_shift, x), P.T.n_e[P.k]);
     const uint32_t sigma = P.T.sigma;
     const uint32_t mb = mask_bits(sigma), ones = mb == 32 ? 0xFFFFFFFFu : (1u << mb) - 1u;
-    const uint32_t mr = mb == 32 ? Ms[r] : (Ms[(r * mb) >> 5] >> ((r * mb) & 31)) & ones;
+    const uint32_t mi = (uint32_t)chk(P, mb == 32 ? r : (r * mb) >> 5, P.tbl_m_words);
+    const uint32_t mr = mb == 32 ? Ms[mi] : (Ms[mi] >> ((r * mb) & 31)) & ones;
     const uint32_t c = (t >> kb) & ((1u << BPS) - 1u);
     return c < sigma ? ((mr >> child_hash(c, sigma)) & 1u) != 0 : mr == ones;
 }
@@ -378,7 +382,7 @@ __device__ __forceinline__ void r_append(const MatchParams &P, RWarpArea &A, RQu
                 en.x = ((root >> j) & 1u) ? ROOT_X : (r_window<BPS>(w, j) & kmask);
                 const uint32_t lj = lim_of(P, p, lima, limb, general, ustart, rem);
                 en.lim = lj < rem_x ? lj : rem_x;
-                A.q[Q.qn + slot] = en;
+                A.q[chk(P, Q.qn + slot, QCAP)] = en;
             }
             e++;
         }
@@ -499,8 +503,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanr(const __grid_constant__ Ma
     __syncthreads();
     RWarpArea &A = areas[warp];
 
-    // first-stage constants: the lane's copy, the address mask, the hash
+    // first-stage constants: the lane's copy, the address mask, the hash,
+    // the table's bytes
     const uint32_t c4 = (lane & ((1u << REP) - 1u)) << 2;
+    const uint32_t tbytes = (GRAM ? P.tbl_g_words : P.tbl_words) * 4u;
     uint32_t amask, gm = 0, gmh = 0;
     if (GRAM) {
         const uint32_t hbw = P.g_hb - 5;
@@ -598,10 +604,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanr(const __grid_constant__ Ma
         }
         uint32_t sa, sb;
         if (NW == RNW) {
-            r_first_stage2<BPS, REP, GRAM>(wa, wb, c4, amask, gm, gmh, sa, sb);
+            r_first_stage2<BPS, REP, GRAM>(P, wa, wb, c4, amask, gm, gmh, tbytes, sa, sb);
         } else {
-            sa = r_first_stage1<BPS, REP, GRAM>(wa, c4, amask, gm, gmh);
-            sb = r_first_stage1<BPS, REP, GRAM>(wb, c4, amask, gm, gmh);
+            sa = r_first_stage1<BPS, REP, GRAM>(P, wa, c4, amask, gm, gmh, tbytes);
+            sb = r_first_stage1<BPS, REP, GRAM>(P, wb, c4, amask, gm, gmh, tbytes);
         }
         // the head of slice 2g + 1 is held when its lane 0 chunk was loaded,
         // that of the next pair when lane 31 loaded it

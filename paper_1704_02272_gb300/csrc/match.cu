@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
         const uint64_t tile_start = t << P.unit_shift;
         for (uint32_t i = 0; i < m; i++) {
             const uint64_t r = rr[i];
-            const uint32_t L = fin_len(pool, (uint32_t)r);
-            const uint32_t *ids = fin_ids(pool, (uint32_t)r);
+            const uint32_t L = fin_len_c(P, (uint32_t)r);
+            const uint32_t *ids = fin_ids_c(P, (uint32_t)r);
             const uint64_t pk = (P.pos_base + tile_start + (r >> 32)) << PFAC_ID_BITS;
             for (uint32_t e = 0; e < L; e++, o++)
                 if (o < P.cap) P.out[o] = pk | __ldg(ids + e);
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
                     uint32_t L = 0;
                     if (i < m) {
                         r = rr[i];
-                        L = fin_len(pool, (uint32_t)r);
+                        L = fin_len_c(P, (uint32_t)r);
                     }
                     uint32_t inc = L;
 #pragma unroll
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(256) k_expand(const MatchParams P) {
                         if (lane >= (uint32_t)s) inc += nb;
                     }
                     if (L) {
-                        const uint32_t *ids = fin_ids(pool, (uint32_t)r);
+                        const uint32_t *ids = fin_ids_c(P, (uint32_t)r);
                         const uint64_t pk = (P.pos_base + tile_start + (r >> 32)) << PFAC_ID_BITS;
                         uint64_t oo = o + inc - L;
                         for (uint32_t e = 0; e < L; e++, oo++)
@@ -937,6 +937,7 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.F = pl.k ? t->dev.F[pl.k] : nullptr;
     P.C = pl.k ? t->dev.C[pl.k] : nullptr;
     P.E = pl.k ? t->dev.E[pl.k] : nullptr;
+    P.E2 = pl.k && t->dev.dag ? t->dev.E2[pl.k] : nullptr;
     P.M = pl.k ? t->dev.M[pl.k] : nullptr;
     P.c_shift = pl.k ? t->dev.c_shift[pl.k] : 0u;
     P.tbl_m_words = pl.tbl_m_words;

@@ -9,8 +9,14 @@
 // as soon as a slot and memory free up, and copies of one request overlap the
 // matching of another.  Each request completes in two stream-ordered phases:
 // H2D of its input, pfac_match_async, D2H of its count; then D2H of its keys
-// (re-matched into a larger buffer in the rare case the first estimate was too
-// small).  Latency is stamped at submit, admission and completion.
+// (in the rare case the first estimate was too small, re-matched into a
+// buffer of exactly its count first, asynchronously on its slot with its own
+// status check).  Latency is stamped at submit, admission and completion.
+//
+// Threads: submitters, pollers and waiters share one lock over the request
+// queue and the completed list; the dispatcher owns the slots and the pool
+// and takes the lock only to pick up new requests and to publish finished
+// ones, so no copy, launch or host copy of keys happens under it.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -93,7 +99,7 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     Request *req = nullptr;
-    int phase = 0;  // 0 idle, 1 matching, 2 copying keys out
+    int phase = 0;  // 0 idle, 1 matching, 2 copying keys out, 3 failed, 4 re-matching
     uint64_t off = 0, bytes = 0;
     uint64_t *d_out = nullptr;
     uint64_t cap = 0;
@@ -101,6 +107,9 @@ struct Slot {
     uint64_t *h_keys = nullptr;   // pinned staging of the keys
     uint64_t h_cap = 0;
     uint64_t count = 0;
+    uint64_t *d_big = nullptr;    // re-match buffer (phase 4)
+    bool big_in_pool = false;
+    uint64_t big_off = 0;
 };
 
 }  // namespace
@@ -138,7 +147,8 @@ uint64_t request_bytes(const pfac_table *t, uint64_t n, uint32_t nseg, uint64_t 
 
 uint64_t first_capacity(uint64_t n) { return n / 8 > 4096 ? n / 8 : 4096; }
 
-// Issues phase 1 of a request on its slot.  Called with the lock held.
+// Issues phase 1 of a request on its slot (the dispatcher's thread; the slots
+// and the pool are the dispatcher's, so no lock is held).
 bool admit(pfac_server *s, Slot &sl, Request *r) {
     const uint64_t cap = first_capacity(r->n);
     uint64_t ws = 0;
@@ -179,23 +189,105 @@ bool admit(pfac_server *s, Slot &sl, Request *r) {
     return true;
 }
 
+// Publishes a finished request (its keys already in place) and frees its
+// slot and memory.
 void finish(pfac_server *s, Slot &sl) {
     Request *r = sl.req;
-    r->t_done = now_s();
-    r->done = true;
     s->pool.release(sl.off, sl.bytes);
-    s->completed.push_back(r->id);
+    if (sl.d_big) {
+        if (sl.big_in_pool) s->pool.release(sl.big_off, 8 * sl.count);
+        else cudaFreeAsync(sl.d_big, sl.stream);
+        sl.d_big = nullptr;
+    }
     sl.req = nullptr;
     sl.phase = 0;
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->t_done = now_s();
+    r->done = true;
+    s->completed.push_back(r->id);
+}
+
+// The device block of a slot's request: input, offsets, workspace, count
+// and status words.
+struct Block {
+    uint8_t *in;
+    uint64_t *seg, *small;
+    uint8_t *ws;
+    uint64_t ws_bytes;
+};
+Block block_of(pfac_server *s, const Slot &sl, const Request *r) {
+    auto a = [](uint64_t x) { return (x + 255) & ~255ull; };
+    Block b;
+    b.in = s->pool.base + sl.off;
+    b.seg = (uint64_t *)(b.in + a(r->n));
+    b.ws_bytes = 0;
+    pfac_workspace_bytes(s->t, r->n, r->nseg, nullptr, &b.ws_bytes);
+    b.ws = (uint8_t *)b.seg + a(8ull * (r->nseg + 1));
+    b.small = (uint64_t *)(b.ws + a(b.ws_bytes));
+    return b;
+}
+
+// Phase 1 done with more keys than the output buffer or the pinned staging
+// holds: grow the staging, match again into a buffer of exactly cnt keys
+// (from the pool when it has room), copy count, status and keys back; the
+// slot moves to phase 4.  Returns false on failure (status set).
+bool rematch(pfac_server *s, Slot &sl, Request *r, uint64_t cnt) {
+    if (cnt > sl.h_cap) {
+        cudaStreamSynchronize(sl.stream);
+        cudaFreeHost(sl.h_keys);
+        sl.h_keys = nullptr;
+        if (cudaHostAlloc((void **)&sl.h_keys, 8 * cnt, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            sl.h_cap = 0;
+            r->status = PFAC_ENOMEM;
+            return false;
+        }
+        sl.h_cap = cnt;
+    }
+    const Block b = block_of(s, sl, r);
+    sl.count = cnt;
+    sl.big_in_pool = s->pool.alloc(8 * cnt, &sl.big_off);
+    if (sl.big_in_pool) {
+        sl.d_big = (uint64_t *)(s->pool.base + sl.big_off);
+    } else if (cudaMallocAsync((void **)&sl.d_big, 8 * cnt, sl.stream) != cudaSuccess) {
+        cudaGetLastError();
+        sl.d_big = nullptr;
+        r->status = PFAC_ENOMEM;
+        return false;
+    }
+    const int rc = pfac_match_async(s->t, b.in, r->n, b.seg, r->nseg, sl.d_big, cnt, b.small,
+                                    (int32_t *)(b.small + 1), b.ws, b.ws_bytes, nullptr, sl.stream);
+    cudaError_t e = cudaSuccess;
+    if (rc == PFAC_OK)
+        e = cudaMemcpyAsync(sl.h_small, b.small, 16, cudaMemcpyDeviceToHost, sl.stream);
+    if (rc == PFAC_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(sl.h_keys, sl.d_big, 8 * cnt, cudaMemcpyDeviceToHost, sl.stream);
+    if (rc == PFAC_OK && e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
+    if (rc != PFAC_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        r->status = rc != PFAC_OK ? rc : PFAC_ECUDA;
+        cudaStreamSynchronize(sl.stream);
+        return false;
+    }
+    sl.phase = 4;
+    return true;
 }
 
 void dispatcher(pfac_server *s) {
     cudaSetDevice(s->device);
-    std::unique_lock<std::mutex> lk(s->mu);
-    while (!s->stop) {
+    std::deque<Request *> local;  // requests picked up, not yet admitted (oldest first)
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->stop) break;
+            while (!s->pending.empty()) {
+                local.push_back(s->pending.front());
+                s->pending.pop_front();
+            }
+        }
         bool progressed = false;
         // admissions, oldest first, while a slot and memory are free
-        while (!s->pending.empty()) {
+        while (!local.empty()) {
             Slot *free_slot = nullptr;
             for (Slot &sl : s->slots)
                 if (sl.phase == 0) {
@@ -203,8 +295,8 @@ void dispatcher(pfac_server *s) {
                     break;
                 }
             if (!free_slot) break;
-            if (!admit(s, *free_slot, s->pending.front())) break;
-            s->pending.pop_front();
+            if (!admit(s, *free_slot, local.front())) break;
+            local.pop_front();
             progressed = true;
         }
         // completions
@@ -229,29 +321,7 @@ void dispatcher(pfac_server *s) {
                 }
                 sl.count = cnt;
                 if (cnt > sl.cap || cnt > sl.h_cap) {
-                    // the first estimate was short: match again into a buffer
-                    // of exactly cnt keys (synchronously on this slot)
-                    auto a = [](uint64_t x) { return (x + 255) & ~255ull; };
-                    uint8_t *p = s->pool.base + sl.off;
-                    uint64_t *d_seg = (uint64_t *)(p + a(r->n));
-                    uint64_t ws = 0;
-                    pfac_workspace_bytes(s->t, r->n, r->nseg, nullptr, &ws);
-                    uint8_t *d_ws = (uint8_t *)d_seg + a(8ull * (r->nseg + 1));
-                    uint64_t *d_small = (uint64_t *)(d_ws + a(ws));
-                    uint64_t *d_big = nullptr;
-                    cudaError_t e = cudaMallocAsync((void **)&d_big, 8 * cnt, sl.stream);
-                    int rc = e == cudaSuccess ? pfac_match_async(s->t, p, r->n, d_seg, r->nseg, d_big,
-                                                                 cnt, d_small, nullptr, d_ws, ws,
-                                                                 nullptr, sl.stream)
-                                              : PFAC_ENOMEM;
-                    r->keys.resize(cnt);
-                    if (rc == PFAC_OK)
-                        e = cudaMemcpyAsync(r->keys.data(), d_big, 8 * cnt, cudaMemcpyDeviceToHost,
-                                            sl.stream);
-                    if (d_big) cudaFreeAsync(d_big, sl.stream);
-                    cudaStreamSynchronize(sl.stream);
-                    if (rc != PFAC_OK || e != cudaSuccess) r->status = rc ? rc : PFAC_ECUDA;
-                    finish(s, sl);
+                    if (!rematch(s, sl, r, cnt)) finish(s, sl);
                     continue;
                 }
                 cudaError_t e = cudaSuccess;
@@ -265,15 +335,22 @@ void dispatcher(pfac_server *s) {
                     continue;
                 }
                 sl.phase = 2;
-            } else if (sl.phase == 2) {
-                r->keys.assign(sl.h_keys, sl.h_keys + sl.count);
+            } else if (sl.phase == 2 || sl.phase == 4) {
+                const int32_t st = (int32_t)(uint32_t)sl.h_small[1];
+                if (sl.phase == 4 && (st != PFAC_OK || sl.h_small[0] != sl.count))
+                    r->status = st != PFAC_OK ? st : PFAC_EDEVICE;
+                else
+                    r->keys.assign(sl.h_keys, sl.h_keys + sl.count);
                 finish(s, sl);
             }
         }
-        if (progressed) s->cv_done.notify_all();
-        if (!progressed) {
+        if (progressed) {
+            s->cv_done.notify_all();
+        } else {
             // nothing moved: wait briefly for a submit or a completion
-            s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (!s->stop && s->pending.empty())
+                s->cv_work.wait_for(lk, std::chrono::microseconds(20));
         }
     }
 }

@@ -37,6 +37,16 @@
 // 2^(g*b) is far beyond shared memory; collisions only let extra positions
 // through to the exact prefix-node test.
 //
+// Merged trie (reduction step 2 of Section 3.2, build flag
+// PFAC_BUILD_SUFFIX_MERGE): equal subtrees of at most three levels share one
+// record each (tail records, numbered from n_upper on).  A record whose
+// children are not all consecutive tree records carries META_IND: child c is
+// ind[base + rank(c)].  Tail records hold no output; a walk that stops
+// below its last tree record u after d symbols s_0 .. s_{d-1} finds its
+// output (the fin of the tree node it reached) in the side table under
+// dag_side_key(u, d, s_0 | s_1 << bps | ...), absent meaning none.  A
+// prefix entry whose depth-k state is a tail record has E2 = u | d << 30.
+//
 // Dense layout (uncompressed PFAC): stt[s * sigma + c] = child or 0 (the root
 // is never a child), dfin[s] = fin(s).
 #pragma once
@@ -47,7 +57,8 @@ namespace pfac {
 constexpr int KMAX = 16;                 // largest prefix depth held
 constexpr uint64_t MASKS_MAX_BYTES = 96 * 1024;  // child masks kept up to this size
 constexpr uint32_t META_ALL_LEAF = 0x80000000u;
-constexpr uint32_t META_BASE_MASK = 0x7FFFFFFFu;
+constexpr uint32_t META_IND = 0x40000000u;        // merged trie: children through ind[]
+constexpr uint32_t META_BASE_MASK = 0x3FFFFFFFu;
 constexpr uint32_t D_CONT = 0x80000000u;  // prefix entry: continue at record
 constexpr uint32_t D_VAL_MASK = 0x7FFFFFFFu;
 // fin encoding: 0 = empty; else (off << FIN_LEN_BITS) | len, len < FIN_LEN_ESC
@@ -63,6 +74,17 @@ constexpr uint32_t FIN_MAX_OFF = (1u << (31 - FIN_LEN_BITS)) - 1;
 //   W == 8: {bm0..bm7, meta, fin, cum0..3, cum4..7} (cum: popcount of the
 //           words before each word, one byte per word)
 __host__ __device__ constexpr int rec_words(int W) { return W == 1 ? 2 : (W == 2 ? 4 : 12); }
+
+// Side table of the merged trie: key of (tree record u, depth d below it,
+// packed symbols tp), its slot (Fibonacci hashing of the key over 2^log
+// slots; linear probing from there), the empty key.
+constexpr uint64_t DAG_SIDE_EMPTY = ~0ull;
+__host__ __device__ inline uint64_t dag_side_key(uint32_t u, uint32_t d, uint32_t tp) {
+    return ((uint64_t)u << 32) | ((uint64_t)d << 28) | tp;
+}
+__host__ __device__ inline uint64_t dag_side_slot(uint64_t key, uint32_t log) {
+    return log ? (key * 0x9E3779B97F4A7C15ull) >> (64 - log) : 0;
+}
 
 // Gram filter hash of a string x of n = g * bps <= 32 bits: y = x * m with
 // m = GRAM_MUL << (32 - n) (Knuth's multiplicative hashing with the
@@ -107,6 +129,8 @@ struct DevTable {
     uint32_t max_len;
     uint32_t n_rec;
     uint32_t n_nodes;     // dense layout: states
+    uint32_t pool_words;  // words of the output-list pool
+    uint32_t leaf_words;  // words of leaf_fin
     const uint32_t *rec;
     const uint32_t *fin;      // W == 1 only
     const uint32_t *leaf_fin;
@@ -130,6 +154,15 @@ struct DevTable {
     uint32_t n_pat;
     const uint32_t *stt;      // dense layout
     const uint32_t *dfin;
+    // merged trie
+    uint32_t dag;             // 1: records of the merged trie
+    uint32_t n_upper;         // records below it are tree records (all, without the merge)
+    const uint32_t *ind;      // child indirection
+    uint32_t ind_words;
+    uint32_t side_log;        // log2 of the side table's slots
+    const uint64_t *side_keys;
+    const uint32_t *side_vals;
+    const uint32_t *E2[KMAX + 1];  // per prefix entry: last tree record | depth << 30
 };
 
 }  // namespace pfac

@@ -100,3 +100,38 @@ def test_request_larger_than_pool_rejected(serving_setup):
         with pytest.raises(pfac.PfacError) as ei:
             srv.submit(big, np.array([0, big.size], np.uint64))
         assert ei.value.status == -4
+
+
+def test_requests_with_more_keys_than_their_first_buffer():
+    # requests whose matches outnumber the server's first key estimate (one
+    # key per 8 input bytes) take the re-match path: a buffer of exactly
+    # their count, matched again on their slot with its status checked; they
+    # share the server with ordinary requests and both kinds must give the
+    # oracle's keys
+    import itertools
+    pats = [bytes(p) for L in range(1, 6) for p in itertools.product((0, 1), repeat=L)]
+    rs = np.random.RandomState(77)
+    reqs = []
+    for k in range(12):
+        n = int(rs.randint(2000, 60000))
+        if k % 3 == 0:
+            text = rs.randint(0, 2, size=n).astype(np.uint8)        # about 5 keys a byte
+        else:
+            text = rs.randint(0, 256, size=n).astype(np.uint8)      # a few keys
+        cuts = np.sort(rs.randint(0, n + 1, size=int(rs.randint(0, 20))))
+        seg = np.concatenate([[0], cuts, [n]]).astype(np.uint64)
+        reqs.append((text, seg))
+    with pfac.Table(pats, 256) as table:
+        with pfac.Server(table, n_slots=3, device_bytes=64 << 20,
+                         max_request_bytes=1 << 20) as srv:
+            ids = [srv.submit(t, s) for t, s in reqs]
+            got = [srv.wait(i, timeout=120) for i in ids]
+            for i in ids:
+                srv.release(i)
+    for k, (g, (t, s)) in enumerate(zip(got, reqs)):
+        assert g["status"] == 0, k
+        pos, ids_ = oracle.match_ac(pats, t, s)
+        ref = oracle.pack_keys(pos, ids_)
+        if k % 3 == 0:
+            assert ref.size > t.size // 8  # really past the first estimate
+        assert_same(g["keys"], ref, f"request {k}")

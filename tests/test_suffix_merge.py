@@ -113,3 +113,44 @@ def test_distinct_two_symbol_chains_follow_the_occupancy_law(sigma, n):
         assert counts[-1] == len({p[-2:] for p in pats})
     mean, se = np.mean(counts), np.std(counts) / np.sqrt(len(counts))
     assert abs(mean - expect) < 4 * se + 0.01 * expect, (mean, expect, se)
+
+
+def _library():
+    return pytest.importorskip("paper_1704_02272_gb300")
+
+
+LIB_CASES = CASES + [
+    ("dna-like", lambda: workloads.uniform_patterns(np.random.RandomState(41), 800, 4, 8, 30)),
+    ("sigma256", lambda: workloads.uniform_patterns(np.random.RandomState(42), 300, 256, 1, 12)),
+    ("sigma40", lambda: workloads.uniform_patterns(np.random.RandomState(43), 500, 40, 2, 9)),
+]
+
+
+@pytest.mark.parametrize("name,make", LIB_CASES, ids=[c[0] for c in LIB_CASES])
+def test_library_merged_node_count_equals_model(name, make):
+    # the library's merged trie (built on the host) keeps as many nodes as the
+    # storage model of step 2 counts
+    pfac = _library()
+    pats = make()
+    sigma = max(max(p) for p in pats) + 1
+    t = T.build_paper_trie(pats, sigma)
+    want = T.suffix_merge(t, 3).n_nodes
+    with pfac.Table(pats, sigma, host_only=True, suffix_merge=True) as lt:
+        info = lt.info()
+    assert info["trie_nodes"] == t.n_nodes
+    assert info["merged_trie_nodes"] == want
+    # one record per merged node: the unshared nodes and one per class
+    assert info["records"] == want
+    # the side table holds an output for each tail node on whose path a
+    # pattern ends, at most every tail node
+    h = T.heights(t)
+    n_tail = sum(1 for v in range(1, t.n_nodes) if h[v] < 3)
+    n_final_tail = sum(1 for v in range(1, t.n_nodes) if h[v] < 3 and t.final_id[v] >= 0)
+    assert n_final_tail <= info["side_entries"] <= n_tail
+
+
+def test_library_merge_flag_needs_compressed_layout():
+    pfac = _library()
+    with pytest.raises(pfac.PfacError):
+        pfac.Table([b"\x01\x02"], 4, layout=pfac.binding.LAYOUT_DENSE, host_only=True,
+                   suffix_merge=True)
