@@ -98,8 +98,16 @@ typedef struct {
  * DAG).  A walk that stops inside a shared subtree finds its pattern ids in
  * a side table keyed by its last unshared node and the symbols after it.
  * Matches are the same; merged_trie_nodes in pfac_table_info counts the
- * nodes kept. */
+ * nodes kept.  Such a table is matched by the queued scan kernel with its
+ * prefix entries in L2 (variant 1) and 16 warps per CTA; other requests
+ * return PFAC_EINVAL. */
 #define PFAC_BUILD_SUFFIX_MERGE 2u
+/* Build flag (compressed layout, alphabets of up to 8 symbols): keep the
+ * two-word records of the 32-symbol format instead of one packed word per
+ * node.  Packed records are the default where the trie fits them (fewer
+ * than 2^26 nodes for alphabets of up to 4 symbols, 2^22 for 5 to 8); this
+ * flag exists for comparison and testing. */
+#define PFAC_BUILD_WIDE_RECORDS 4u
 
 /* Match options; a NULL pointer means library defaults (the table's
  * autotuned choice when pfac_autotune has run). */
@@ -198,6 +206,17 @@ typedef struct {
                                    reduction step 2 (unshared nodes plus one per
                                    class of equal subtrees); else 0 */
     uint64_t side_entries;     /* side-table entries of the merged trie */
+    /* device_bytes by part (each part's sections, before alignment): */
+    uint64_t trie_bytes;       /* node records, outputs (lists, merged leaves),
+                                  merged-trie indirection and side table */
+    uint64_t index_bytes;      /* prefix nodes of every depth held (bitmaps,
+                                  counts, entries, child masks, prefix bytes)
+                                  and the gram filter */
+    uint64_t other_bytes;      /* patterns kept for verification (truncated
+                                  tables), dense transition table */
+    uint32_t record_bytes;     /* bytes per node record (4, 8, 16 or 48; 0 for
+                                  the dense layout) */
+    uint32_t reserved_info;
 } pfac_table_info_t;
 
 /*

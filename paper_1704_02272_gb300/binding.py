@@ -42,6 +42,7 @@ class BuildOpts(ctypes.Structure):
 
 BUILD_HOST_ONLY = 1
 BUILD_SUFFIX_MERGE = 2
+BUILD_WIDE_RECORDS = 4
 
 
 class MatchOpts(ctypes.Structure):
@@ -67,7 +68,10 @@ class TableInfo(ctypes.Structure):
                 ("dense_bytes", ctypes.c_uint64), ("output_lists", ctypes.c_uint64),
                 ("output_list_words", ctypes.c_uint64), ("gram_len", ctypes.c_uint32),
                 ("gram_bits", ctypes.c_uint32), ("gram_strings", ctypes.c_uint64),
-                ("merged_trie_nodes", ctypes.c_uint64), ("side_entries", ctypes.c_uint64)]
+                ("merged_trie_nodes", ctypes.c_uint64), ("side_entries", ctypes.c_uint64),
+                ("trie_bytes", ctypes.c_uint64), ("index_bytes", ctypes.c_uint64),
+                ("other_bytes", ctypes.c_uint64), ("record_bytes", ctypes.c_uint32),
+                ("reserved_info", ctypes.c_uint32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -211,7 +215,8 @@ class Table:
 
     def __init__(self, patterns, alphabet_size: int, layout: int = LAYOUT_COMPRESSED,
                  prefix_depth: int = 0, stream=None, host_only: bool = False,
-                 truncate_depth: int = 0, suffix_merge: bool = False):
+                 truncate_depth: int = 0, suffix_merge: bool = False,
+                 wide_records: bool = False):
         n = len(patterns)
         bufs = [ctypes.create_string_buffer(bytes(p), len(p)) for p in patterns]
         arr = (ctypes.POINTER(ctypes.c_uint8) * max(n, 1))()
@@ -221,7 +226,8 @@ class Table:
             lens[i] = len(p)
         o = BuildOpts()
         o.layout, o.prefix_depth = layout, prefix_depth
-        o.flags = (BUILD_HOST_ONLY if host_only else 0) | (BUILD_SUFFIX_MERGE if suffix_merge else 0)
+        o.flags = ((BUILD_HOST_ONLY if host_only else 0) | (BUILD_SUFFIX_MERGE if suffix_merge else 0)
+                   | (BUILD_WIDE_RECORDS if wide_records else 0))
         o.truncate_depth = truncate_depth
         h = ctypes.c_void_p()
         st = 0 if host_only else _stream(stream)

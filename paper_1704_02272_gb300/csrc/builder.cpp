@@ -92,7 +92,8 @@ void get_list(const std::vector<uint32_t> &pool, uint32_t code, std::vector<uint
     ids.assign(pool.begin() + off, pool.begin() + off + len);
 }
 
-inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+// sections start on 16-byte boundaries (the widest load of any of them)
+inline uint64_t align16(uint64_t x) { return (x + 15) & ~15ull; }
 
 }  // namespace
 }  // namespace pfac
@@ -343,7 +344,46 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         if (o.prefix_depth && o.prefix_depth < kfloor)
             return set_error(PFAC_EINVAL, "pfac_build: prefix_depth %u < %u for this alphabet",
                              o.prefix_depth, kfloor);
-        const uint32_t kdef = o.prefix_depth ? o.prefix_depth : klim;
+        // record format: one packed word per node for alphabets of up to 8
+        // symbols when every base fits below the bitmap (bases index records,
+        // merged-leaf outputs or the indirection list, each fewer than Q)
+        const bool dense = o.layout == PFAC_LAYOUT_DENSE;
+        const uint32_t psh = pk_shift(sigma);
+        const bool packed = !dense && sigma <= 8 && !(o.flags & PFAC_BUILD_WIDE_RECORDS) &&
+                            Q < (1ull << psh);
+        const uint32_t F = packed ? 0u : W;
+        const int RW = rec_words((int)F);
+        // entries of the prefix node of each depth: the indices whose walk
+        // reaches depth k, plus those that stop earlier after a final (a
+        // node of depth d < k with output, on a symbol value it has no child
+        // on, any symbols after)
+        uint64_t n_ent[KMAX + 1] = {0};
+        for (uint64_t v = 0; v < Q; v++) {
+            const uint32_t d = nodes[v].depth;
+            if (d > klim) continue;
+            const uint64_t miss = (1ull << bps) - nodes[v].n_child;
+            for (uint32_t k = std::max(d, kfloor); k <= klim; k++) {
+                if (k == d) n_ent[k] += 1;
+                else if (fin_code[v]) n_ent[k] += miss << ((k - d - 1) * bps);
+            }
+        }
+        // Default depth: the shallowest that passes at most 1/256 of uniform
+        // windows, among the depths whose entries stay within a quarter of
+        // the records' bytes (64 KiB at least); the deepest of those when
+        // none is that selective.
+        uint32_t kdef = o.prefix_depth;
+        if (!kdef) {
+            const uint64_t budget = std::max<uint64_t>(64 * 1024, (uint64_t)n_rec * RW);
+            uint32_t kcap = kfloor;
+            for (uint32_t k = kfloor; k <= klim; k++)
+                if (n_ent[k] * 4 <= budget) kcap = k;
+            kdef = kcap;
+            for (uint32_t k = kfloor; k <= kcap; k++)
+                if (n_ent[k] * 256 <= (1ull << (k * bps))) {
+                    kdef = k;
+                    break;
+                }
+        }
         const uint32_t kmin = std::max(kdef > 2 ? kdef - 2 : 1u, kfloor);
         const uint32_t kmax = kdef;
         // walk the node-level trie over k symbols packed in x
@@ -358,10 +398,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         };
 
         // ---- section sizes ------------------------------------------------
-        const bool dense = o.layout == PFAC_LAYOUT_DENSE;
-        const int RW = rec_words((int)W);
         uint64_t sz_rec = dense ? 0 : (uint64_t)n_rec * RW * 4;
-        uint64_t sz_fin = (!dense && W == 1) ? (uint64_t)n_rec * 4 : 0;
+        uint64_t sz_fin = (!dense && F == 1) ? (uint64_t)n_rec * 4 : 0;
         std::vector<uint32_t> leaf_fin;
         if (!dense) {
             leaf_fin.reserve(merged);
@@ -388,7 +426,9 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 Fv[k].assign(fw, 0);
                 Cv[k].assign((fw + (1ull << cs) - 1) >> cs, 0);
                 cshift[k] = cs;
-                const bool with_b = k * bps <= BYTES_MAX_BITS;
+                // prefix bytes where the planner would use them (the bitmap
+                // passes at least 1% of windows)
+                const bool with_b = k * bps <= BYTES_MAX_BITS && n_ent[k] * 100 >= ent;
                 if (with_b) Bv[k].assign(ent < 4 ? 4 : ent, 0);
                 for (uint64_t x = 0; x < ent; x++) {
                     uint32_t v = 0, e = 0, e2 = 0;
@@ -558,7 +598,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         std::vector<uint32_t> rec, finv, ind;
         if (!dense) {
             rec.assign((uint64_t)n_rec * RW, 0);
-            if (W == 1) finv.assign(n_rec, 0);
+            if (F <= 1) finv.assign(n_rec, 0);
             for (uint64_t v = 0; v < Q; v++) {
                 uint32_t r = rec_of[v];
                 if (r == NOREC) continue;
@@ -596,9 +636,17 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                         if (rec_of[nodes[v].first_child + c] != meta + c)
                             return set_error(PFAC_EDEVICE, "pfac_build: internal error (records)");
                 }
-                for (uint32_t w = 0; w < W; w++) R[w] = bm[v * W + w];
                 // a merged node's outputs depend on the path: the side table
                 const uint32_t fv = dag && !upper[v] ? 0u : fin_code[v];
+                if (F == 0) {
+                    // on a merged trie the flag marks the records with
+                    // indirect children (leaf merge is off there)
+                    R[0] = (meta & META_ALL_LEAF) | (fv ? PK_FIN : 0u) | (bm[v * W] << psh) |
+                           (meta & META_BASE_MASK);
+                    finv[r] = fv;
+                    continue;
+                }
+                for (uint32_t w = 0; w < W; w++) R[w] = bm[v * W + w];
                 if (W == 1) {
                     R[1] = meta;
                     finv[r] = fv;
@@ -621,6 +669,26 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         }
         if (leaf_fin.empty()) leaf_fin.push_back(0);
         uint64_t sz_leaf = dense ? 0 : leaf_fin.size() * 4;
+        // packed records: outputs of the records that have one, by rank
+        std::vector<uint32_t> fbc, fvals;
+        if (F == 0) {
+            const uint64_t nw = (uint64_t)n_rec / 32 + 1;
+            fbc.assign(2 * nw, 0);
+            uint32_t cnt = 0;
+            for (uint64_t w = 0; w < nw; w++) {
+                fbc[2 * w + 1] = cnt;
+                for (uint32_t b = 0; b < 32; b++) {
+                    const uint64_t r = 32 * w + b;
+                    if (r < n_rec && finv[r]) {
+                        fbc[2 * w] |= 1u << b;
+                        fvals.push_back(finv[r]);
+                        cnt++;
+                    }
+                }
+            }
+            if (fvals.empty()) fvals.push_back(0);
+        }
+        const uint64_t sz_fbc = fbc.size() * 4, sz_fv = F == 0 ? fvals.size() * 4 : 0;
         if (ind.empty()) ind.push_back(0);
         const uint64_t sz_ind = dag ? ind.size() * 4 : 0;
 
@@ -663,11 +731,11 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         uint64_t off = 0;
         auto place = [&](uint64_t sz) {
             uint64_t at = off;
-            off = align256(off + sz);
+            off = align16(off + sz);
             return at;
         };
         uint64_t o_rec = place(sz_rec), o_fin = place(sz_fin), o_leaf = place(sz_leaf),
-                 o_pool = place(sz_pool);
+                 o_pool = place(sz_pool), o_fbc = place(sz_fbc), o_fv = place(sz_fv);
         const uint64_t o_ind = place(sz_ind), o_sk = place(sz_sk), o_sv = place(sz_sv);
         uint64_t o_F[KMAX + 1] = {0}, o_C[KMAX + 1] = {0}, o_E[KMAX + 1] = {0},
                  o_M[KMAX + 1] = {0}, o_B[KMAX + 1] = {0}, o_E2[KMAX + 1] = {0};
@@ -692,6 +760,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         };
         put(o_rec, rec.data(), sz_rec);
         put(o_fin, finv.data(), sz_fin);
+        put(o_fbc, fbc.data(), sz_fbc);
+        put(o_fv, fvals.data(), sz_fv);
         put(o_leaf, leaf_fin.data(), sz_leaf);
         put(o_pool, pool.data(), sz_pool);
         put(o_ind, ind.data(), sz_ind);
@@ -750,7 +820,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         DevTable &dv = t->dev;
         memset(&dv, 0, sizeof(dv));
         dv.sigma = sigma;
-        dv.W = W;
+        dv.W = F;
+        dv.pk_shift = psh;
         dv.bps = bps;
         dv.kdef = kdef;
         dv.kmin = kmin;
@@ -760,6 +831,9 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         dv.n_nodes = (uint32_t)Q;
         dv.rec = (const uint32_t *)(B + o_rec);
         dv.fin = (const uint32_t *)(B + o_fin);
+        dv.fbc = F == 0 ? (const uint32_t *)(B + o_fbc) : nullptr;
+        dv.fvals = F == 0 ? (const uint32_t *)(B + o_fv) : nullptr;
+        dv.n_fvals = F == 0 ? (uint32_t)fvals.size() : 0u;
         dv.leaf_fin = (const uint32_t *)(B + o_leaf);
         dv.pool = (const uint32_t *)(B + o_pool);
         dv.pool_words = (uint32_t)pool.size();
@@ -818,6 +892,13 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         I.gram_strings = g_set;
         I.merged_trie_nodes = dag ? (uint64_t)n_upper + canon_rep.size() : 0;
         I.side_entries = side_n;
+        I.trie_bytes = sz_rec + sz_fin + sz_fbc + sz_fv + sz_leaf + sz_pool + sz_ind + sz_sk + sz_sv;
+        I.index_bytes = sz_G;
+        if (!dense)
+            for (uint32_t k = kmin; k <= kmax; k++)
+                I.index_bytes += sz_F[k] + sz_C[k] + sz_E[k] + sz_M[k] + sz_B[k] + sz_E2[k];
+        I.other_bytes = sz_po + sz_pb + sz_stt + sz_dfin;
+        I.record_bytes = dense ? 0u : (uint32_t)RW * 4u;
         *out = t;
         return PFAC_OK;
     } catch (const std::bad_alloc &) {

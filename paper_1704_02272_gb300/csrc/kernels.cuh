@@ -45,6 +45,9 @@ constexpr int ST_BADSEG = 1, ST_TIMEOUT = 2, ST_DEVICE = 4;
 // scan variants: prefix bitmap in shared memory with its entries in global
 // memory (VAR_F) or in shared memory too (VAR_FE); uncompressed table (VAR_DENSE)
 enum { VAR_F = 1, VAR_FE = 2, VAR_DENSE = 4 };
+// kernel instances for merged tries (reduction step 2): VAR_F | VAR_MERGED;
+// the others leave the merged-trie slow path out
+constexpr int VAR_MERGED = 8;
 
 struct WsHeader {
     int32_t status;

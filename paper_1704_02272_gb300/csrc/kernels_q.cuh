@@ -46,6 +46,14 @@ constexpr int QU = QCAP / 32;            // queue entries per lane per batch
 // walks a lane advances together while resolving: fewer for 48-byte records
 __host__ __device__ constexpr int walks_per_lane(int W) { return W == 8 ? 2 : 4; }
 constexpr uint32_t ROOT_X = 0xFFFFFFFFu; // queue entry: walk from the root
+constexpr uint32_t DAG_PENDING = 0x80000000u;  // resolved entry: merged-trie walk still to run
+
+// Entries after which warp `warp` of `nw` resolves its queue the first time
+// (later resolutions wait for a full queue): 8 .. QCAP, spread over the
+// warps.
+__device__ __forceinline__ uint32_t first_flush(uint32_t warp, uint32_t nw) {
+    return 8u + (warp * (uint32_t)(QCAP - 8)) / nw;
+}
 constexpr uint32_t LAST_FLAG = 0x80000000u;  // queue entry: the slice's last
 constexpr uint32_t UNIT_OVF = 0xFFFFFFFFu;
 constexpr uint32_t LIM_MAX = 0xFFFFFFF0u;
@@ -90,14 +98,22 @@ __device__ __forceinline__ uint32_t prefix_rank(const uint32_t *Fs, uint32_t rep
 
 // Record words of state r needed to take a step on symbol c: the word
 // holding c's bit, the rank base below that word, the meta word and (for
-// sigma > 32) the state's output.
+// sigma > 32) the state's output.  A packed record (W == 0) is its own meta
+// word: the all-leaf flag at bit 31 and the base below bit psh, the bitmap
+// between.
 template <int W>
 __device__ __forceinline__ void load_step(const uint32_t *__restrict__ rec, uint32_t r, uint32_t c,
                                           uint32_t &word, uint32_t &below, uint32_t &meta,
-                                          uint32_t &f) {
+                                          uint32_t &f, uint32_t psh = 0) {
     constexpr int RW = rec_words(W);
     const uint32_t *R = rec + (size_t)r * RW;
-    if (W == 1) {
+    if (W == 0) {
+        const uint32_t v = __ldg(R);
+        word = v >> psh;  // the flag lands above the bitmap, past every symbol
+        below = 0;
+        meta = v;
+        f = 0;
+    } else if (W == 1) {
         const uint2 v = __ldg(reinterpret_cast<const uint2 *>(R));
         word = v.x;
         below = 0;
@@ -123,13 +139,38 @@ __device__ __forceinline__ void load_step(const uint32_t *__restrict__ rec, uint
 // One step of a walk at state st on symbol c (c >= sigma or past the limit
 // ends it).  Returns 0 = moved to st, 1 = stopped at st (output of st),
 // 2 = stopped on a merged leaf (output leaf_fin[st]).
+// bmask: META_BASE_MASK, or (1 << psh) - 1 for packed records.
 __device__ __forceinline__ int take_step(uint32_t sigma, uint32_t c, uint32_t word,
-                                         uint32_t below, uint32_t meta, uint32_t &st) {
+                                         uint32_t below, uint32_t meta, uint32_t &st,
+                                         uint32_t bmask = META_BASE_MASK) {
     const uint32_t bit = c & 31;
     if (c >= sigma || !((word >> bit) & 1u)) return 1;
     const uint32_t rank = below + (uint32_t)__popc(word & ((1u << bit) - 1u));
-    st = (meta & META_BASE_MASK) + rank;
+    st = (meta & bmask) + rank;
     return (meta & META_ALL_LEAF) ? 2 : 0;
+}
+
+// Output of a record in the packed format: its bit in fbc, then its rank
+// among the records with an output.  The second load is taken whatever the
+// bit (clamped to the array), so that a batch of these overlaps.
+__device__ __forceinline__ uint32_t pk_fin(const MatchParams &P, uint32_t r) {
+    const uint2 b = __ldg(reinterpret_cast<const uint2 *>(P.T.fbc) + (r >> 5));
+    const uint32_t bit = r & 31;
+    const uint32_t i = b.y + (uint32_t)__popc(b.x & ((1u << bit) - 1u));
+    const uint32_t last = P.T.n_fvals - 1u;
+    const uint32_t v = __ldg(P.T.fvals + (i < last ? i : last));
+    return ((b.x >> bit) & 1u) ? v : 0u;
+}
+
+// Output of record r when the walk stops there: the separate array (W == 1),
+// the packed format's rank lookup when its meta word says it has one
+// (W == 0), or the word loaded with the record (f, wider records).
+template <int W>
+__device__ __forceinline__ uint32_t rec_fin(const MatchParams &P, uint32_t r, uint32_t f,
+                                            uint32_t meta) {
+    if (W == 0) return (meta & PK_FIN) ? pk_fin(P, (uint32_t)chk(P, r, P.T.n_rec)) : 0u;
+    if (W == 1) return __ldg(P.T.fin + chk(P, r, P.T.n_rec));
+    return f;
 }
 
 // Walk of the merged trie (reduction step 2 of Section 3.2) from tree record
@@ -145,17 +186,19 @@ __device__ __noinline__ uint32_t dag_walk(const MatchParams *PP, uint32_t s, uin
                                           uint32_t lim, uint32_t unit) {
     const MatchParams &P = *PP;
     const uint64_t ub = (uint64_t)unit << SLICE_SHIFT;
-    const uint32_t sigma = P.T.sigma, n_upper = P.T.n_upper, bps = P.T.bps;
-    uint32_t u = s, d = 0, tp = 0, f = 0;
+    const uint32_t sigma = P.T.sigma, n_upper = P.T.n_upper, bps = P.T.bps, psh = P.T.pk_shift;
+    // packed records mark the indirect ones with the all-leaf flag
+    const uint32_t bmask = W == 0 ? (1u << psh) - 1u : META_BASE_MASK;
+    const uint32_t indf = W == 0 ? META_ALL_LEAF : META_IND;
+    uint32_t u = s, d = 0, tp = 0, f = 0, meta = 0;
     for (;;) {
         const uint32_t c = q < lim ? (uint32_t)__ldg(P.in + chk(P, ub + q, P.n)) : 0x100u;
-        uint32_t word, below, meta;
-        load_step<W>(P.T.rec, (uint32_t)chk(P, s, P.T.n_rec), c, word, below, meta, f);
+        uint32_t word, below;
+        load_step<W>(P.T.rec, (uint32_t)chk(P, s, P.T.n_rec), c, word, below, meta, f, psh);
         const uint32_t bit = c & 31;
         if (c >= sigma || !((word >> bit) & 1u)) break;
-        const uint32_t i = (meta & META_BASE_MASK) + below +
-                           (uint32_t)__popc(word & ((1u << bit) - 1u));
-        s = (meta & META_IND) ? __ldg(P.T.ind + chk(P, i, P.T.ind_words)) : i;
+        const uint32_t i = (meta & bmask) + below + (uint32_t)__popc(word & ((1u << bit) - 1u));
+        s = (meta & indf) ? __ldg(P.T.ind + chk(P, i, P.T.ind_words)) : i;
         q++;
         if (s < n_upper) {
             u = s;
@@ -166,7 +209,7 @@ __device__ __noinline__ uint32_t dag_walk(const MatchParams *PP, uint32_t s, uin
             d++;
         }
     }
-    if (s < n_upper) return W == 1 ? __ldg(P.T.fin + chk(P, s, P.T.n_rec)) : f;
+    if (s < n_upper) return rec_fin<W>(P, s, f, meta);
     const uint64_t key = dag_side_key(u, d, tp);
     const uint64_t m = (1ull << P.T.side_log) - 1u;
     uint64_t h = dag_side_slot(key, P.T.side_log);
@@ -192,7 +235,9 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                                              uint32_t lane) {
     constexpr int QU = walks_per_lane(W);
     constexpr int LOCK_ROUNDS = 3;
+    constexpr bool DAG = (VAR & VAR_MERGED) != 0;
     const uint32_t sigma = P.T.sigma, k = P.k, rep = P.rep_log2;
+    const uint32_t psh = P.T.pk_shift, bmask = W == 0 ? (1u << psh) - 1u : META_BASE_MASK;
     const uint32_t *__restrict__ rec = P.T.rec;
     uint32_t st[QU], qq[QU], lim[QU], fin[QU], unit[QU];
     // -1 idle, 0 walking, 1 stopped at st, 2 stopped on merged leaf st, 3 done,
@@ -220,12 +265,12 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                 const uint32_t xx = (uint32_t)chk(P, en.x, 1ull << (k * P.T.bps));
                 const uint32_t r = (uint32_t)chk(P, prefix_rank(Fs, rep, Cs, P.c_shift, xx),
                                                  P.T.n_e[k]);
-                const uint32_t ev = VAR == VAR_FE ? Es[r] : __ldg(P.E + r);
+                const uint32_t ev = (VAR & 7) == VAR_FE ? Es[r] : __ldg(P.E + r);
                 qq[u] = p + k;
                 if (ev & D_CONT) {
                     state[u] = 0;
                     st[u] = ev & D_VAL_MASK;
-                    if (st[u] >= P.T.n_upper) {
+                    if (DAG && st[u] >= P.T.n_upper) {
                         // a tail record of the merged trie: walk again from
                         // the last tree record, d symbols back
                         const uint32_t e2 = __ldg(P.E2 + r);
@@ -256,20 +301,28 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
 #pragma unroll
         for (int u = 0; u < QU; u++) {
             if (state[u] != 0) continue;
-            load_step<W>(rec, (uint32_t)chk(P, st[u], P.T.n_rec), c[u], wd[u], bl[u], mt[u], f1[u]);
+            load_step<W>(rec, (uint32_t)chk(P, st[u], P.T.n_rec), c[u], wd[u], bl[u], mt[u], f1[u],
+                         psh);
         }
 #pragma unroll
         for (int u = 0; u < QU; u++) {
             if (state[u] != 0) continue;
             const uint32_t cur = st[u];
-            const int r = take_step(sigma, c[u], wd[u], bl[u], mt[u], st[u]);
+            const int r = take_step(sigma, c[u], wd[u], bl[u], mt[u], st[u], bmask);
             if (r == 0) {
                 qq[u]++;
             } else if (r == 1) {
-                if (W == 1) st[u] = cur;
-                else fin[u] = f1[u];
-                state[u] = W == 1 ? 1 : 3;
-            } else if (P.T.dag) {
+                // the output: loaded after phase C (separate arrays), known
+                // now (a packed record without one, or the wider records)
+                if (W == 0 && !(mt[u] & PK_FIN)) {
+                    fin[u] = 0;
+                    state[u] = 3;
+                } else {
+                    if (W <= 1) st[u] = cur;
+                    else fin[u] = f1[u];
+                    state[u] = W <= 1 ? 1 : 3;
+                }
+            } else if (DAG) {
                 st[u] = cur;
                 state[u] = 4;
             } else {
@@ -297,9 +350,8 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
     // stored after phase D so the loads' latency overlaps the long walks
 #pragma unroll
     for (int u = 0; u < QU; u++) {
-        if (state[u] == 1) fin[u] = __ldg(P.T.fin + chk(P, st[u], P.T.n_rec));
+        if (state[u] == 1) fin[u] = rec_fin<W>(P, st[u], 0, PK_FIN);
         else if (state[u] == 2) fin[u] = __ldg(P.T.leaf_fin + chk(P, st[u], P.T.leaf_words));
-        else if (state[u] == 4) fin[u] = dag_walk<W>(&P, st[u], qq[u], lim[u], unit[u]);
     }
     // ---- phase D: the long walks, one per lane
     for (uint32_t t0 = 0; t0 < nt; t0 += 32) {
@@ -324,7 +376,7 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                     c[i] = q1 + i < en.lim ? (uint32_t)__ldg(P.in + chk(P, ub + q1 + i, P.n)) : 0x100u;
                     if (i == 0 || s1 + i < n_rec) {
                         load_step<W>(rec, (uint32_t)chk(P, s1 + i, n_rec), c[i], wd[i], bl[i],
-                                     mt[i], f1[i]);
+                                     mt[i], f1[i], psh);
                     } else {
                         wd[i] = bl[i] = mt[i] = f1[i] = 0;
                     }
@@ -335,15 +387,21 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                     // walk stays on the consecutive chain
                     uint32_t nx = 0;
                     const uint32_t cur = s1 + i;
-                    const int r = take_step(sigma, c[i], wd[i], bl[i], mt[i], nx);
+                    const int r = take_step(sigma, c[i], wd[i], bl[i], mt[i], nx, bmask);
                     if (r == 1) {
-                        f = W == 1 ? __ldg(P.T.fin + chk(P, cur, n_rec)) : f1[i];
+                        f = rec_fin<W>(P, cur, f1[i], mt[i]);
                         done = true;
                         break;
                     }
                     if (r == 2) {
-                        f = P.T.dag ? dag_walk<W>(&P, cur, q1 + i, en.lim, en.unit)
-                                    : __ldg(P.T.leaf_fin + chk(P, nx, P.T.leaf_words));
+                        if (DAG) {
+                            // finished on the merged trie's slow path below,
+                            // from record cur at q1 + i
+                            tail[t] = (tail[t] & 0x7Fu) | ((q1 + i) << 7);
+                            f = DAG_PENDING | cur;
+                        } else {
+                            f = __ldg(P.T.leaf_fin + chk(P, nx, P.T.leaf_words));
+                        }
                         done = true;
                         break;
                     }
@@ -355,6 +413,21 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
             }
             q[e].x = f;
         }
+    }
+    // ---- the merged trie's slow path, out of the loops above: walks that
+    // reached an indirect record (phase B and D) or a prefix entry on a tail
+    // record (phase A)
+    if (DAG) {
+        __syncwarp();
+        for (uint32_t t = lane; t < nt; t += 32) {
+            const uint32_t e = e0 + (tail[t] & 0x7Fu);
+            const QEntry en = q[e];
+            if (en.x & DAG_PENDING)
+                q[e].x = dag_walk<W>(&P, en.x & ~DAG_PENDING, tail[t] >> 7, en.lim, en.unit);
+        }
+#pragma unroll
+        for (int u = 0; u < QU; u++)
+            if (state[u] == 4) fin[u] = dag_walk<W>(&P, st[u], qq[u], lim[u], unit[u]);
     }
 #pragma unroll
     for (int u = 0; u < QU; u++)
@@ -965,7 +1038,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const __grid_constant__ Ma
         const uint32_t rep = P.rep_log2;
         for (uint32_t i = threadIdx.x; i < P.tbl_words; i += QTHREADS) Fs[i] = __ldg(P.F + (i >> rep));
         for (uint32_t i = threadIdx.x; i < P.tbl_c_words; i += QTHREADS) Cs[i] = __ldg(P.C + i);
-        if (VAR == VAR_FE)
+        if ((VAR & 7) == VAR_FE)
             for (uint32_t i = threadIdx.x; i < P.tbl_e_words; i += QTHREADS) Es[i] = __ldg(P.E + i);
         for (uint32_t i = threadIdx.x; i < P.tbl_m_words; i += QTHREADS) Ms[i] = __ldg(P.M + i);
         const uint32_t *bsrc = reinterpret_cast<const uint32_t *>(P.Bt);
@@ -1022,6 +1095,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const __grid_constant__ Ma
         if (gw + gstride < n_units) sf_n = __ldg(P.unit_seg + unit_of(1));
     }
     uint32_t qn = 0;  // queued entries (warp-uniform)
+    // The first resolution of each warp comes after a number of entries that
+    // grows with the warp index, so that the warps of a CTA resolve their
+    // queues (long chains of L2 loads) at different times, not all at once.
+    uint32_t qsoft = first_flush(warp, NW);
     uint32_t i_fail = 0;
     bool failed = false;
     for (uint32_t i = 0; gw + i * gstride < n_units; i++) {
@@ -1121,6 +1198,11 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const __grid_constant__ Ma
                     qn = 0;
                 }
                 if (ar == AP_DONE) qn += ast.kept;
+                if (ar == AP_DONE && qn >= qsoft) {
+                    flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
+                    qn = 0;
+                    qsoft = QCAP + 1;
+                }
             }
             if (ar == AP_OVER) {
                 // more survivors than the (now empty) queue holds: resolved

@@ -13,14 +13,14 @@
 
 namespace pfac {
 
-void *scan_kernel_bps1(int, int, int);
-void *scan_kernel_bps2(int, int, int);
-void *scan_kernel_bps3(int, int, int);
-void *scan_kernel_bps4(int, int, int);
-void *scan_kernel_bps5(int, int, int);
-void *scan_kernel_bps6(int, int, int);
-void *scan_kernel_bps7(int, int, int);
-void *scan_kernel_bps8(int, int, int);
+void *scan_kernel_bps1(int, int, int, int);
+void *scan_kernel_bps2(int, int, int, int);
+void *scan_kernel_bps3(int, int, int, int);
+void *scan_kernel_bps4(int, int, int, int);
+void *scan_kernel_bps5(int, int, int, int);
+void *scan_kernel_bps6(int, int, int, int);
+void *scan_kernel_bps7(int, int, int, int);
+void *scan_kernel_bps8(int, int, int, int);
 void *scan_kernel_dense();
 void *scan_kernel_r8_g0_f(int rep, int nw);
 void *scan_kernel_r8_g0_fe(int rep, int nw);
@@ -32,8 +32,9 @@ void *scan_kernel_r2_g1_f(int rep, int nw);
 void *scan_kernel_r2_g1_fe(int rep, int nw);
 
 // the register-staged kernel for 8-bit or 2-bit symbols
-static void *scan_kernel_r(uint32_t bps, int rep, bool gram, int var, int nw) {
+static void *scan_kernel_r(uint32_t bps, uint32_t w, int rep, bool gram, int var, int nw) {
     if (bps == 2) {
+        if (w != 0) return nullptr;  // packed records only
         if (gram) return var == VAR_FE ? scan_kernel_r2_g1_fe(rep, nw) : scan_kernel_r2_g1_f(rep, nw);
         return var == VAR_FE ? scan_kernel_r2_g0_fe(rep, nw) : scan_kernel_r2_g0_f(rep, nw);
     }
@@ -346,16 +347,16 @@ static WsLayout ws_layout(uint64_t n_bytes, uint32_t n_seg, const Plan &pl) {
     return L;
 }
 
-static void *scan_kernel_for(uint32_t bps, int var, int emit, int nw) {
+static void *scan_kernel_for(uint32_t bps, int var, int emit, int nw, int w) {
     switch (bps) {
-        case 1: return scan_kernel_bps1(var, emit, nw);
-        case 2: return scan_kernel_bps2(var, emit, nw);
-        case 3: return scan_kernel_bps3(var, emit, nw);
-        case 4: return scan_kernel_bps4(var, emit, nw);
-        case 5: return scan_kernel_bps5(var, emit, nw);
-        case 6: return scan_kernel_bps6(var, emit, nw);
-        case 7: return scan_kernel_bps7(var, emit, nw);
-        case 8: return scan_kernel_bps8(var, emit, nw);
+        case 1: return scan_kernel_bps1(var, emit, nw, w);
+        case 2: return scan_kernel_bps2(var, emit, nw, w);
+        case 3: return scan_kernel_bps3(var, emit, nw, w);
+        case 4: return scan_kernel_bps4(var, emit, nw, w);
+        case 5: return scan_kernel_bps5(var, emit, nw, w);
+        case 6: return scan_kernel_bps6(var, emit, nw, w);
+        case 7: return scan_kernel_bps7(var, emit, nw, w);
+        case 8: return scan_kernel_bps8(var, emit, nw, w);
         default: return nullptr;
     }
 }
@@ -489,7 +490,7 @@ static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks,
     }
     pl->nw = nw;
     pl->kind = SCAN_REGISTER;
-    pl->kernel = scan_kernel_r(T.bps, b_rep, b_gram, b_var, (int)nw);
+    pl->kernel = scan_kernel_r(T.bps, T.W, b_rep, b_gram, b_var, (int)nw);
     pl->smem = r_smem((uint64_t)pl->tbl_words + pl->tbl_c_words + pl->tbl_e_words +
                       pl->tbl_m_words + pl->tbl_g_words, nw);
     // the emit pass: the queued kernel, one bitmap copy, entries through L2,
@@ -497,7 +498,7 @@ static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks,
     pl->e_tbl_words = fw;
     pl->e_tbl_m_words = (have_m && queued_smem((uint64_t)fw + cw + mw, QW) <= SMEM_LIMIT) ? mw : 0u;
     pl->smem_emit = queued_smem((uint64_t)fw + cw + pl->e_tbl_m_words, QW);
-    pl->kernel_emit = scan_kernel_for(T.bps, VAR_F, 1, QW);
+    pl->kernel_emit = scan_kernel_for(T.bps, VAR_F, 1, QW, (int)T.W);
     pl->unit_shift = SLICE_SHIFT;
     pl->unit_cap = SCAP;
     pl->queued = true;
@@ -577,6 +578,13 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                          copies);
     if (var != 0 && var != VAR_F && var != VAR_FE)
         return set_error(PFAC_EINVAL, "pfac_match: unknown variant %d", var);
+    // a merged trie (reduction step 2) runs the queued kernel's merged-trie
+    // instance: entries through L2, the default CTA width
+    if (T.dag && var == VAR_FE)
+        return set_error(PFAC_EINVAL, "pfac_match: a merged trie takes variant 1 (entries in L2)");
+    if (T.dag && nwant != QW)
+        return set_error(PFAC_EINVAL, "pfac_match: a merged trie takes %u warps per CTA", QW);
+    if (T.dag) var = VAR_F;
 
     // ---- records kept per slice: 32, or 512 (one per position, so that no
     // slice is scanned twice) where many matches are likely
@@ -593,10 +601,11 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     const uint32_t want_kind = opts && opts->scan_kernel ? opts->scan_kernel
                                                          : (use_tuned ? t->tuned_kernel : 0u);
     if (want_kind > 2) return set_error(PFAC_EINVAL, "pfac_match: scan_kernel %u", want_kind);
-    const bool r_usable = (T.bps == 8 || T.bps == 2) && pbytes != 2;
+    const bool r_usable = (T.bps == 8 || T.bps == 2) && pbytes != 2 && !T.dag;
     if (want_kind == SCAN_REGISTER && !r_usable)
         return set_error(PFAC_EINVAL, "pfac_match: the register-staged kernel needs 8-bit or 2-bit "
-                         "symbols (alphabets of 129 to 256, or of up to 4) and no prefix bytes");
+                         "symbols (alphabets of 129 to 256, or of up to 4), no prefix bytes and "
+                         "no merged trie");
     if (want_kind == SCAN_REGISTER || (want_kind == 0 && r_usable && T.bps == 8 && R_BY_DEFAULT)) {
         const uint32_t rnw = opts && opts->warps_per_cta
                                  ? opts->warps_per_cta
@@ -748,8 +757,9 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
         return set_error(PFAC_EINVAL, "pfac_match: %u warps do not fit next to the tables", nwant);
     pl->nw = nwant;
     pl->kind = SCAN_QUEUED;
-    pl->kernel = scan_kernel_for(T.bps, var, 0, (int)nwant);
-    pl->kernel_emit = scan_kernel_for(T.bps, var, 1, (int)nwant);
+    const int kvar = T.dag ? (VAR_F | VAR_MERGED) : var;
+    pl->kernel = scan_kernel_for(T.bps, kvar, 0, (int)nwant, (int)T.W);
+    pl->kernel_emit = scan_kernel_for(T.bps, kvar, 1, (int)nwant, (int)T.W);
     pl->smem = queued_smem(tw, nwant);
     pl->unit_shift = SLICE_SHIFT;
     pl->unit_cap = recs;

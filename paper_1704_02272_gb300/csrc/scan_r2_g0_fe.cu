@@ -8,11 +8,11 @@ namespace pfac {
 template <int NW>
 static void *pick(int rep) {
     switch (rep) {
-        case 0: return (void *)k_scanr<2, 1, 0, 0, VAR_FE, NW>;
-        case 1: return (void *)k_scanr<2, 1, 1, 0, VAR_FE, NW>;
-        case 2: return (void *)k_scanr<2, 1, 2, 0, VAR_FE, NW>;
-        case 3: return (void *)k_scanr<2, 1, 3, 0, VAR_FE, NW>;
-        case 4: return (void *)k_scanr<2, 1, 4, 0, VAR_FE, NW>;
+        case 0: return (void *)k_scanr<2, 0, 0, 0, VAR_FE, NW>;
+        case 1: return (void *)k_scanr<2, 0, 1, 0, VAR_FE, NW>;
+        case 2: return (void *)k_scanr<2, 0, 2, 0, VAR_FE, NW>;
+        case 3: return (void *)k_scanr<2, 0, 3, 0, VAR_FE, NW>;
+        case 4: return (void *)k_scanr<2, 0, 4, 0, VAR_FE, NW>;
         default: return nullptr;
     }
 }

@@ -69,11 +69,23 @@ constexpr uint32_t FIN_LEN_ESC = (1u << FIN_LEN_BITS) - 1;
 constexpr uint32_t FIN_MAX_OFF = (1u << (31 - FIN_LEN_BITS)) - 1;
 
 // 32-bit words per record for W bitmap words
+//   W == 0: one packed word for alphabets of up to 8 symbols: bit 31 the
+//           all-leaf flag (on a merged trie: children through ind[]), bit 30
+//           set when the record has an output (PK_FIN), the bitmap's SB bits
+//           (SB = 4 for sigma <= 4, else 8) at bits PK_SHIFT .. 29
+//           (PK_SHIFT = 30 - SB), the base below PK_SHIFT; the outputs of
+//           the records with one in fvals[], found by rank:
+//           fbc[r >> 5] = {bit r & 31 set when record r has an output, the
+//           number of such records before the word}
 //   W == 1: {bm, meta}                          (fin in a separate array)
 //   W == 2: {bm0, bm1, meta, fin}
 //   W == 8: {bm0..bm7, meta, fin, cum0..3, cum4..7} (cum: popcount of the
 //           words before each word, one byte per word)
-__host__ __device__ constexpr int rec_words(int W) { return W == 1 ? 2 : (W == 2 ? 4 : 12); }
+__host__ __device__ constexpr int rec_words(int W) {
+    return W == 0 ? 1 : (W == 1 ? 2 : (W == 2 ? 4 : 12));
+}
+__host__ __device__ constexpr uint32_t pk_shift(uint32_t sigma) { return sigma <= 4 ? 26u : 22u; }
+constexpr uint32_t PK_FIN = 0x40000000u;
 
 // Side table of the merged trie: key of (tree record u, depth d below it,
 // packed symbols tp), its slot (Fibonacci hashing of the key over 2^log
@@ -121,7 +133,8 @@ __host__ __device__ inline uint32_t child_hash(uint32_t c, uint32_t sigma) {
 
 struct DevTable {
     uint32_t sigma;
-    uint32_t W;           // 1, 2 or 8 (bitmap words per record)
+    uint32_t W;           // record format: 0 (packed), 1, 2 or 8 (bitmap words)
+    uint32_t pk_shift;    // W == 0: bit of the bitmap's symbol 0
     uint32_t bps;         // bits per symbol in prefix indices
     uint32_t kdef;        // default prefix depth
     uint32_t kmin;        // shallowest prefix depth held
@@ -133,6 +146,9 @@ struct DevTable {
     uint32_t leaf_words;  // words of leaf_fin
     const uint32_t *rec;
     const uint32_t *fin;      // W == 1 only
+    const uint32_t *fbc;      // W == 0 only: {bits, count} word pairs per 32 records
+    const uint32_t *fvals;    // W == 0 only: outputs of the records that have one
+    uint32_t n_fvals;
     const uint32_t *leaf_fin;
     const uint32_t *pool;
     const uint32_t *F[KMAX + 1];   // prefix bitmap of depth k

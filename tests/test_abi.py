@@ -223,3 +223,38 @@ def test_async_entry_points_check_their_tensors(fn):
         # well-formed host tensors: refused because the path needs device memory
         with pytest.raises(ValueError, match="CUDA device"):
             call(t, z, s, out, cnt, st, *ws)
+
+
+@pytest.mark.parametrize("sigma,n", [(2, 50), (4, 800), (7, 600), (8, 300), (20, 500),
+                                     (64, 400), (256, 300)])
+def test_record_formats_and_table_parts(sigma, n):
+    # alphabets of up to 8 symbols pack a node into one word (4 bytes); the
+    # 32-symbol format takes 8, the 64- and 256-symbol ones 16 and 48; the
+    # parts add up to the device bytes up to the 16-byte section alignment
+    pats = workloads.uniform_patterns(np.random.RandomState(sigma * 7 + n), n, sigma, 2, 14)
+    pats = list(dict.fromkeys(pats))
+    with host_table(pats, sigma) as t:
+        i = t.info()
+    want = 4 if sigma <= 8 else (8 if sigma <= 32 else (16 if sigma <= 64 else 48))
+    assert i["record_bytes"] == want
+    parts = i["trie_bytes"] + i["index_bytes"] + i["other_bytes"]
+    assert parts <= i["device_bytes"] <= parts + 16 * 64
+    if sigma <= 8:
+        with host_table(pats, sigma, wide_records=True) as tw:
+            iw = tw.info()
+        assert iw["record_bytes"] == 8 and iw["records"] == i["records"]
+        # the packed records take half the bytes; the outputs move to the
+        # ranked list of the records that have one
+        assert i["trie_bytes"] < iw["trie_bytes"]
+
+
+@pytest.mark.parametrize("sigma,n,lo,hi", [(4, 1000, 4, 64), (4, 10000, 4, 64),
+                                           (4, 10000, 8, 64), (52, 1, 20, 20), (52, 10, 20, 20),
+                                           (20, 1000, 4, 64), (256, 1000, 4, 64)])
+def test_compressed_table_smaller_than_dense(sigma, n, lo, hi):
+    # the compressed device table, with its prefix nodes and filter, takes
+    # fewer bytes than the uncompressed transition table of the same trie
+    pats = workloads.uniform_patterns(np.random.RandomState(sigma + n), n, sigma, lo, hi)
+    pats = list(dict.fromkeys(pats))
+    with host_table(pats, sigma) as t, host_table(pats, sigma, layout=pfac.LAYOUT_DENSE) as d:
+        assert t.info()["device_bytes"] < d.info()["device_bytes"]

@@ -1,6 +1,7 @@
 """GPU parity of the merged trie (reduction step 2 of Section 3.2): tables
 built with suffix_merge=True against the CPU oracle, element by element,
-through both scan kernels and every plan that fits, on pattern sets whose
+through the queued kernel's merged-trie instance and every plan that fits
+(the register-staged kernel refuses merged tries), on pattern sets whose
 walks end inside shared subtrees at every depth (prefix entries whose state
 is a merged node, walks that stop one to three levels below their last
 unshared node, patterns that are prefixes of others), and at the full size
@@ -108,8 +109,10 @@ def test_merged_trie_edges():
             text = rs.randint(0, 4, size=n).astype(np.uint8)
             w = workloads.Workload(f"edge-{n}", 4, pats, text, workloads.single_segment(n))
             tt, sg = to_device(w)
-            for kern in KERNELS:
-                assert_same(run(t, tt, sg, scan_kernel=kern), oracle_keys(w), f"n={n} {kern}")
+            assert_same(run(t, tt, sg), oracle_keys(w), f"n={n}")
+        with pytest.raises(pfac.PfacError) as ei:
+            pfac.plan(t, scan_kernel=pfac.binding.KERNEL_REGISTER)
+        assert ei.value.status == -1
 
 
 def test_merged_trie_full_size_dna():
@@ -124,7 +127,7 @@ def test_merged_trie_full_size_dna():
         ref = np.concatenate([oracle_keys(w, lo=a, hi=min(a + step, w.n_bytes), ac=ac)
                               for a in range(0, w.n_bytes, step)])
         with pfac.Table(w.patterns, 4, suffix_merge=True) as t:
-            for kern in KERNELS:
-                assert_same(run(t, text, seg, scan_kernel=kern), ref, f"dna merged {kern}")
+            for opt in ({}, {"child_masks": 1}, {"prefix_depth": 8}):
+                assert_same(run(t, text, seg, **opt), ref, f"dna merged {opt}")
     finally:
         ac.close()
