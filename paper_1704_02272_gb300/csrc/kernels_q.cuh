@@ -47,13 +47,6 @@ constexpr int QU = QCAP / 32;            // queue entries per lane per batch
 __host__ __device__ constexpr int walks_per_lane(int W) { return W == 8 ? 2 : 4; }
 constexpr uint32_t ROOT_X = 0xFFFFFFFFu; // queue entry: walk from the root
 constexpr uint32_t DAG_PENDING = 0x80000000u;  // resolved entry: merged-trie walk still to run
-
-// Entries after which warp `warp` of `nw` resolves its queue the first time
-// (later resolutions wait for a full queue): 8 .. QCAP, spread over the
-// warps.
-__device__ __forceinline__ uint32_t first_flush(uint32_t warp, uint32_t nw) {
-    return 8u + (warp * (uint32_t)(QCAP - 8)) / nw;
-}
 constexpr uint32_t LAST_FLAG = 0x80000000u;  // queue entry: the slice's last
 constexpr uint32_t UNIT_OVF = 0xFFFFFFFFu;
 constexpr uint32_t LIM_MAX = 0xFFFFFFF0u;
@@ -436,15 +429,22 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
 }
 
 template <int W, int VAR>
-__device__ __forceinline__ void resolve_batch(const MatchParams &P, QEntry *q, uint32_t n,
-                                              const uint32_t *Fs, const uint32_t *Cs,
-                                              const uint32_t *Es, uint32_t lane) {
+__device__ __forceinline__ void resolve_batch_inl(const MatchParams &P, QEntry *q, uint32_t n,
+                                                  const uint32_t *Fs, const uint32_t *Cs,
+                                                  const uint32_t *Es, uint32_t lane) {
     constexpr uint32_t per = 32u * walks_per_lane(W);
     // the tail list lives behind the queue entries of this warp
     uint32_t *tail = reinterpret_cast<uint32_t *>(q + QCAP);
     for (uint32_t e0 = 0; e0 < n; e0 += per)
         resolve_pass<W, VAR>(P, q, n, e0, Fs, Cs, Es, tail, lane);
     __syncwarp();
+}
+
+template <int W, int VAR>
+__device__ __forceinline__ void resolve_batch(const MatchParams &P, QEntry *q, uint32_t n,
+                                              const uint32_t *Fs, const uint32_t *Cs,
+                                              const uint32_t *Es, uint32_t lane) {
+    resolve_batch_inl<W, VAR>(P, q, n, Fs, Cs, Es, lane);
 }
 
 // Filter of one slice by one warp.  Fills the survivor masks of the lane's
@@ -1095,10 +1095,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const __grid_constant__ Ma
         if (gw + gstride < n_units) sf_n = __ldg(P.unit_seg + unit_of(1));
     }
     uint32_t qn = 0;  // queued entries (warp-uniform)
-    // The first resolution of each warp comes after a number of entries that
-    // grows with the warp index, so that the warps of a CTA resolve their
-    // queues (long chains of L2 loads) at different times, not all at once.
-    uint32_t qsoft = first_flush(warp, NW);
     uint32_t i_fail = 0;
     bool failed = false;
     for (uint32_t i = 0; gw + i * gstride < n_units; i++) {
@@ -1198,11 +1194,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const __grid_constant__ Ma
                     qn = 0;
                 }
                 if (ar == AP_DONE) qn += ast.kept;
-                if (ar == AP_DONE && qn >= qsoft) {
-                    flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
-                    qn = 0;
-                    qsoft = QCAP + 1;
-                }
             }
             if (ar == AP_OVER) {
                 // more survivors than the (now empty) queue holds: resolved

@@ -314,7 +314,6 @@ __device__ __forceinline__ void r_seg_limits(const MatchParams &P, uint32_t u, u
 
 struct RQueue {
     uint32_t qn;          // entries queued (warp-uniform)
-    uint32_t soft;        // resolve once qn reaches this (first_flush, then past QCAP)
     uint32_t carry_unit;  // slice continued into the next batch (UNIT_OVF: none)
     uint32_t carry;       // its records in earlier batches
 };
@@ -393,10 +392,6 @@ __device__ __forceinline__ void r_append(const MatchParams &P, RWarpArea &A, RQu
         if (done == tot) break;
         // the queue is full and the slice goes on: resolve, carrying its ranks
         r_flush_queue<W, VAR>(P, A, Q, Fs, Cs, Es, lane);
-    }
-    if (Q.qn >= Q.soft) {
-        r_flush_queue<W, VAR>(P, A, Q, Fs, Cs, Es, lane);
-        Q.soft = QCAP + 1;
     }
 }
 
@@ -566,7 +561,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanr(const __grid_constant__ Ma
     for (uint32_t i = 0; i < RPF && i < it_clean; i++)
         prefetch_l2_if(l0, pair_ptr + i * step_b, 2 * SLICE);
 
-    RQueue Q{0u, first_flush(warp, NW), UNIT_OVF, 0u};
+    RQueue Q{0u, UNIT_OVF, 0u};
     // one step: pair i, its registers loaded the step before
     auto step = [&](uint32_t i, const uint4 &ca, const uint4 &cb, const uint4 &ch) {
         prefetch_l2_if(l0 && i + RPF < it_clean, pair_ptr + (i + RPF) * step_b, 2 * SLICE);
