@@ -286,7 +286,7 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
     dense_build_s = time.perf_counter() - t0
     dinfo = dense.info()
 
-    tune = None
+    tune = dense_tune = None
     if not args.no_autotune and not user_opt:
         # the autotuner on a bounded prefix sample of the input (whole
         # segments, at most TUNE_SAMPLE bytes); untimed
@@ -295,6 +295,8 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
         cut = int(np.searchsorted(offs, nb, side="left"))  # offsets below nb
         s_offs = torch.from_numpy(np.concatenate([offs[:cut], [nb]])).to(dev)
         tune = pfac.autotune(table, text[:nb], s_offs)
+        # the uncompressed table gets the same search over the same kernels
+        dense_tune = pfac.autotune(dense, text[:nb], s_offs)
     call_opt = call_opt or {}
     # the untimed reference call runs the plan the steps run
     with torch.cuda.stream(stream):
@@ -316,7 +318,9 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
 
     plan = pfac.plan(table, **user_opt)
     ws = torch.empty(max(pfac.workspace_bytes(table, N, S, **user_opt),
-                         pfac.workspace_bytes(dense, N, S)), dtype=torch.uint8, device=dev)
+                         pfac.workspace_bytes(dense, N, S),
+                         pfac.workspace_bytes(dense, N, S, scan_kernel=pfac.binding.KERNEL_SERIAL)),
+                     dtype=torch.uint8, device=dev)
 
     def step(i=None, tbl=table):
         opt = dict(user_opt) if tbl is table else {}
@@ -379,17 +383,30 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
     stream.synchronize()
     exact = bool(torch.equal(dk, keys))
     del dk
-    for _ in range(W):
-        step(tbl=dense)
+
+    def timed(tbl, opt=None):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        o = dict(call_opt)
+        o.update(opt or {})
+        for _ in range(W):
+            pfac.match_async(tbl, text, seg, out, cnt, st, ws, stream=stream, **o)
+        e0.record(stream)
+        for _ in range(K):
+            pfac.match_async(tbl, text, seg, out, cnt, st, ws, stream=stream, **o)
+        e1.record(stream)
+        stream.synchronize()
+        return 8.0 * n_starts * K / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    dense_gbps = timed(dense)
+    dense_plan = pfac.plan(dense)
+    # the thread-serial kernel (one thread walks its positions in turn)
+    serial = {"scan_kernel": pfac.binding.KERNEL_SERIAL}
+    dk = pfac.match(dense, text, seg, stream=stream, **call_opt, **serial)
     stream.synchronize()
-    d0 = torch.cuda.Event(enable_timing=True)
-    d1 = torch.cuda.Event(enable_timing=True)
-    d0.record(stream)
-    for _ in range(K):
-        step(tbl=dense)
-    d1.record(stream)
-    stream.synchronize()
-    dense_gbps = 8.0 * n_starts * K / (d0.elapsed_time(d1) / 1e3) / 1e9
+    serial_exact = bool(torch.equal(dk, keys))
+    del dk
+    serial_gbps = timed(dense, serial)
     merged = None if args.no_suffix_merge or args.truncate else time_merged(
         pfac, torch, w, text, seg, keys, stream, args, call_opt, n_starts)
 
@@ -423,7 +440,11 @@ def time_cell(pfac, torch, w, dev, stream, args, user_opt, workload_name, graph_
         "table_bytes": {"compressed": info["device_bytes"], "dense": dinfo["device_bytes"],
                         "paper_model": info["paper_bytes"], "trie_nodes": info["trie_nodes"],
                         "records": info["records"], "merged_leaves": info["merged_leaves"]},
-        "dense": {"value": round(dense_gbps, 3), "unit": "Gbps", "bit_exact_vs_compressed": exact},
+        "dense": {"value": round(dense_gbps, 3), "unit": "Gbps", "bit_exact_vs_compressed": exact,
+                  "kernel": "the compressed table's kernels over the dense transition table",
+                  "scan_plan": dense_plan, "autotuned": dense_tune,
+                  "thread_serial": {"value": round(serial_gbps, 3), "unit": "Gbps",
+                                    "bit_exact_vs_compressed": serial_exact}},
         "suffix_merge": merged,
         "build_s": {"compressed": round(build_s, 3), "dense": round(dense_build_s, 3)},
         "roofline": roofline,
@@ -649,6 +670,7 @@ def run_ours(args):
         "p50_ms": cell["p50_ms"], "p99_ms": cell["p99_ms"],
         "matches": cell["matches"], "matched_position_frac": cell["matched_position_frac"],
         "table_bytes": cell["table_bytes"], "dense": cell["dense"],
+        "suffix_merge": cell["suffix_merge"],
         "prefix_matching": prefix_line,
         "shards": shard_line,
         "build_s": cell["build_s"],

@@ -156,13 +156,19 @@ typedef struct {
                               re-scans the slices whose matches did not fit
                               their record space, for profiling */
     void *ev_emit_end;     /* optional cudaEvent_t recorded right after it */
-    uint32_t scan_kernel;  /* which scan kernel runs the first stages (compressed
-                              layout): 0 = library choice (or the autotuner's),
-                              1 = queued kernel (input staged in shared memory
-                              by bulk copies), 2 = register-staged kernel
-                              (input read into registers; alphabets of 129 to
-                              256 symbols; excludes prefix_bytes = 2 and
-                              warps_per_cta) */
+    uint32_t scan_kernel;  /* which scan kernel runs the first stages: 0 =
+                              library choice (or the autotuner's), 1 = queued
+                              kernel (input staged in shared memory by bulk
+                              copies), 2 = register-staged kernel (input read
+                              into registers; alphabets of 129 to 256 symbols
+                              or of up to 4; excludes prefix_bytes = 2 and
+                              warps_per_cta), 3 = the dense layout's
+                              thread-serial kernel (one thread walks its
+                              positions one after another, the transition table
+                              from shared memory where it fits; for
+                              comparison).  Both layouts run kernels 1 and 2,
+                              the dense one over its transition table (16 warps
+                              per CTA). */
     uint32_t reserved_scan;
     /* Testing aids for the failure path of the queued kernel's bounded waits
      * (they change no result of a call that does not set them): */
@@ -207,13 +213,15 @@ typedef struct {
                                    class of equal subtrees); else 0 */
     uint64_t side_entries;     /* side-table entries of the merged trie */
     /* device_bytes by part (each part's sections, before alignment): */
-    uint64_t trie_bytes;       /* node records, outputs (lists, merged leaves),
-                                  merged-trie indirection and side table */
+    uint64_t trie_bytes;       /* node records (the dense layout: its
+                                  transition table), outputs (lists, merged
+                                  leaves), merged-trie indirection and side
+                                  table */
     uint64_t index_bytes;      /* prefix nodes of every depth held (bitmaps,
                                   counts, entries, child masks, prefix bytes)
-                                  and the gram filter */
+                                  and the gram filter; both layouts */
     uint64_t other_bytes;      /* patterns kept for verification (truncated
-                                  tables), dense transition table */
+                                  tables) */
     uint32_t record_bytes;     /* bytes per node record (4, 8, 16 or 48; 0 for
                                   the dense layout) */
     uint32_t reserved_info;
@@ -264,7 +272,7 @@ typedef struct {
     uint32_t smem_bytes;     /* dynamic shared memory per CTA of the scan kernel */
     uint32_t prefix_bytes;   /* 1 = off, 2 = on */
     uint32_t warps_per_cta;  /* warps per CTA of the scan kernel (0: uncompressed) */
-    uint32_t scan_kernel;    /* 1 = queued, 2 = register-staged (0: uncompressed) */
+    uint32_t scan_kernel;    /* 1 = queued, 2 = register-staged, 3 = thread-serial */
     uint32_t records_per_slice; /* 32 or 512 (compressed layout) */
     uint32_t reserved;
 } pfac_plan_info;

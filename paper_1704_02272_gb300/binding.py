@@ -183,7 +183,7 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-KERNEL_QUEUED, KERNEL_REGISTER = 1, 2
+KERNEL_QUEUED, KERNEL_REGISTER, KERNEL_SERIAL = 1, 2, 3
 
 
 def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,

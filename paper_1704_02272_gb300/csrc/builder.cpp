@@ -272,11 +272,13 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         }
 
         // ---- leaf merge (Eq. 2) and record numbering ----------------------
+        // (the dense layout numbers every node the same way, without merges)
+        const bool dense = o.layout == PFAC_LAYOUT_DENSE;
         std::vector<uint8_t> all_leaf(Q, 0);
         uint64_t n_leaves = 0;
         for (uint64_t v = 0; v < Q; v++) {
             if (v > 0 && nodes[v].n_child == 0) n_leaves++;
-            if (nodes[v].n_child && !dag) {
+            if (nodes[v].n_child && !dag && !dense) {
                 bool all = true;
                 for (uint32_t c = 0; c < nodes[v].n_child && all; c++)
                     all = nodes[nodes[v].first_child + c].n_child == 0;
@@ -347,7 +349,6 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         // record format: one packed word per node for alphabets of up to 8
         // symbols when every base fits below the bitmap (bases index records,
         // merged-leaf outputs or the indirection list, each fewer than Q)
-        const bool dense = o.layout == PFAC_LAYOUT_DENSE;
         const uint32_t psh = pk_shift(sigma);
         const bool packed = !dense && sigma <= 8 && !(o.flags & PFAC_BUILD_WIDE_RECORDS) &&
                             Q < (1ull << psh);
@@ -373,7 +374,9 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         // none is that selective.
         uint32_t kdef = o.prefix_depth;
         if (!kdef) {
-            const uint64_t budget = std::max<uint64_t>(64 * 1024, (uint64_t)n_rec * RW);
+            // (the dense layout takes the depth its compressed table would)
+            const int rw_c = (sigma <= 8 && Q < (1ull << psh)) ? 1 : rec_words((int)W);
+            const uint64_t budget = std::max<uint64_t>(64 * 1024, (uint64_t)n_rec * rw_c);
             uint32_t kcap = kfloor;
             for (uint32_t k = kfloor; k <= klim; k++)
                 if (n_ent[k] * 4 <= budget) kcap = k;
@@ -415,102 +418,101 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         uint32_t cshift[KMAX + 1] = {0};
         uint64_t sz_F[KMAX + 1] = {0}, sz_C[KMAX + 1] = {0}, sz_E[KMAX + 1] = {0},
                  sz_M[KMAX + 1] = {0}, sz_B[KMAX + 1] = {0}, sz_E2[KMAX + 1] = {0};
-        if (!dense)
-            for (uint32_t k = kmin; k <= kmax; k++) {
-                const uint64_t ent = 1ull << (k * bps);
-                const uint32_t smask = (1u << bps) - 1;
-                const uint64_t fw = ent >= 32 ? ent / 32 : 1;
-                // a count per word keeps the rank to one count and one popcount;
-                // large bitmaps count per 8 words
-                const uint32_t cs = fw <= 8192 ? 0u : 3u;
-                Fv[k].assign(fw, 0);
-                Cv[k].assign((fw + (1ull << cs) - 1) >> cs, 0);
-                cshift[k] = cs;
-                // prefix bytes where the planner would use them (the bitmap
-                // passes at least 1% of windows)
-                const bool with_b = k * bps <= BYTES_MAX_BITS && n_ent[k] * 100 >= ent;
-                if (with_b) Bv[k].assign(ent < 4 ? 4 : ent, 0);
-                for (uint64_t x = 0; x < ent; x++) {
-                    uint32_t v = 0, e = 0, e2 = 0;
-                    bool stopped = false;
-                    for (uint32_t i = 0; i < k; i++) {
-                        const int64_t ch = child_of(v, (uint32_t)(x >> (bps * i)) & smask);
-                        if (ch < 0) {
-                            e = fin_code[v];
-                            stopped = true;
-                            break;
-                        }
-                        v = (uint32_t)ch;
+        for (uint32_t k = kmin; k <= kmax; k++) {
+            const uint64_t ent = 1ull << (k * bps);
+            const uint32_t smask = (1u << bps) - 1;
+            const uint64_t fw = ent >= 32 ? ent / 32 : 1;
+            // a count per word keeps the rank to one count and one popcount;
+            // large bitmaps count per 8 words
+            const uint32_t cs = fw <= 8192 ? 0u : 3u;
+            Fv[k].assign(fw, 0);
+            Cv[k].assign((fw + (1ull << cs) - 1) >> cs, 0);
+            cshift[k] = cs;
+            // prefix bytes where the planner would use them (the bitmap
+            // passes at least 1% of windows)
+            const bool with_b = k * bps <= BYTES_MAX_BITS && n_ent[k] * 100 >= ent;
+            if (with_b) Bv[k].assign(ent < 4 ? 4 : ent, 0);
+            for (uint64_t x = 0; x < ent; x++) {
+                uint32_t v = 0, e = 0, e2 = 0;
+                bool stopped = false;
+                for (uint32_t i = 0; i < k; i++) {
+                    const int64_t ch = child_of(v, (uint32_t)(x >> (bps * i)) & smask);
+                    if (ch < 0) {
+                        e = fin_code[v];
+                        stopped = true;
+                        break;
                     }
-                    uint32_t mask = 0xFFFFFFFFu, bucket = 0xFFu;
-                    if (!stopped) {
-                        if (nodes[v].n_child == 0) {
-                            e = fin_code[v];  // a leaf ends the walk
-                        } else {
-                            e = D_CONT | rec_of[v];
-                            if (dag && !upper[v]) {
-                                uint32_t u = v, d = 0;
-                                while (!upper[u]) {
-                                    u = nodes[u].parent;
-                                    d++;
+                    v = (uint32_t)ch;
+                }
+                uint32_t mask = 0xFFFFFFFFu, bucket = 0xFFu;
+                if (!stopped) {
+                    if (nodes[v].n_child == 0) {
+                        e = fin_code[v];  // a leaf ends the walk
+                    } else {
+                        e = D_CONT | rec_of[v];
+                        if (dag && !upper[v]) {
+                            uint32_t u = v, d = 0;
+                            while (!upper[u]) {
+                                u = nodes[u].parent;
+                                d++;
+                            }
+                            e2 = rec_of[u] | (d << 30);
+                        }
+                        if (fin_code[v] == 0) {
+                            mask = 0;
+                            bucket = 0;
+                            for (uint32_t c = 0; c < sigma; c++)
+                                if ((bm[(uint64_t)v * W + (c >> 5)] >> (c & 31)) & 1) {
+                                    mask |= 1u << child_hash(c, sigma);
+                                    bucket |= 1u << byte_bucket(c, sigma);
                                 }
-                                e2 = rec_of[u] | (d << 30);
-                            }
-                            if (fin_code[v] == 0) {
-                                mask = 0;
-                                bucket = 0;
-                                for (uint32_t c = 0; c < sigma; c++)
-                                    if ((bm[(uint64_t)v * W + (c >> 5)] >> (c & 31)) & 1) {
-                                        mask |= 1u << child_hash(c, sigma);
-                                        bucket |= 1u << byte_bucket(c, sigma);
-                                    }
-                            }
                         }
                     }
-                    if (e) {
-                        Fv[k][x >> 5] |= 1u << (x & 31);
-                        Ev[k].push_back(e);
-                        if (dag) E2v[k].push_back(e2);
-                        Mv[k].push_back(mask);
-                        if (with_b) Bv[k][x] = (uint8_t)bucket;
-                    }
                 }
-                uint32_t run = 0;
-                for (uint64_t w = 0; w < fw; w++) {
-                    if ((w & ((1u << cs) - 1)) == 0) Cv[k][w >> cs] = run;
-                    run += __builtin_popcount(Fv[k][w]);
+                if (e) {
+                    Fv[k][x >> 5] |= 1u << (x & 31);
+                    Ev[k].push_back(e);
+                    if (dag) E2v[k].push_back(e2);
+                    Mv[k].push_back(mask);
+                    if (with_b) Bv[k][x] = (uint8_t)bucket;
                 }
-                if (Ev[k].empty()) {
-                    Ev[k].push_back(0);
-                    Mv[k].push_back(0);
-                    if (dag) E2v[k].push_back(0);
-                }
-                sz_F[k] = fw * 4;
-                sz_C[k] = Cv[k].size() * 4;
-                sz_E[k] = Ev[k].size() * 4;
-                sz_E2[k] = E2v[k].size() * 4;
-                // narrow masks for small alphabets: mask_bits(sigma) bits per
-                // entry, packed low entry first (an all-ones mask still means
-                // "keep whatever follows")
-                const uint32_t mb = mask_bits(sigma);
-                if (mb < 32) {
-                    std::vector<uint32_t> packed((Mv[k].size() * mb + 31) / 32, 0);
-                    const uint32_t ones = (1u << mb) - 1u;
-                    for (size_t r = 0; r < Mv[k].size(); r++)
-                        packed[(r * mb) >> 5] |= (Mv[k][r] & ones) << ((r * mb) & 31);
-                    Mv[k].swap(packed);
-                }
-                // child masks are only used from shared memory: none when the
-                // entries could never fit there
-                if (Mv[k].size() * 4 > MASKS_MAX_BYTES) Mv[k].clear();
-                sz_M[k] = Mv[k].size() * 4;
-                sz_B[k] = Bv[k].size();
             }
+            uint32_t run = 0;
+            for (uint64_t w = 0; w < fw; w++) {
+                if ((w & ((1u << cs) - 1)) == 0) Cv[k][w >> cs] = run;
+                run += __builtin_popcount(Fv[k][w]);
+            }
+            if (Ev[k].empty()) {
+                Ev[k].push_back(0);
+                Mv[k].push_back(0);
+                if (dag) E2v[k].push_back(0);
+            }
+            sz_F[k] = fw * 4;
+            sz_C[k] = Cv[k].size() * 4;
+            sz_E[k] = Ev[k].size() * 4;
+            sz_E2[k] = E2v[k].size() * 4;
+            // narrow masks for small alphabets: mask_bits(sigma) bits per
+            // entry, packed low entry first (an all-ones mask still means
+            // "keep whatever follows")
+            const uint32_t mb = mask_bits(sigma);
+            if (mb < 32) {
+                std::vector<uint32_t> packed((Mv[k].size() * mb + 31) / 32, 0);
+                const uint32_t ones = (1u << mb) - 1u;
+                for (size_t r = 0; r < Mv[k].size(); r++)
+                    packed[(r * mb) >> 5] |= (Mv[k][r] & ones) << ((r * mb) & 31);
+                Mv[k].swap(packed);
+            }
+            // child masks are only used from shared memory: none when the
+            // entries could never fit there
+            if (Mv[k].size() * 4 > MASKS_MAX_BYTES) Mv[k].clear();
+            sz_M[k] = Mv[k].size() * 4;
+            sz_B[k] = Bv[k].size();
+        }
         // ---- gram filter over g = kmax + 1 symbols (see table.h) -----------
         uint32_t g_len = 0, g_bits = 0;
         uint64_t g_set = 0;
         std::vector<uint32_t> Gv;
-        if (!dense && (kmax + 1) * bps <= 32) {
+        if ((kmax + 1) * bps <= 32) {
             g_len = kmax + 1;
             const uint32_t A = 1u << bps;  // packed symbol values (>= sigma: no child)
             // pass 0 counts the strings, pass 1 sets their bits
@@ -739,15 +741,14 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         const uint64_t o_ind = place(sz_ind), o_sk = place(sz_sk), o_sv = place(sz_sv);
         uint64_t o_F[KMAX + 1] = {0}, o_C[KMAX + 1] = {0}, o_E[KMAX + 1] = {0},
                  o_M[KMAX + 1] = {0}, o_B[KMAX + 1] = {0}, o_E2[KMAX + 1] = {0};
-        if (!dense)
-            for (uint32_t k = kmin; k <= kmax; k++) {
-                o_F[k] = place(sz_F[k]);
-                o_C[k] = place(sz_C[k]);
-                o_E[k] = place(sz_E[k]);
-                o_M[k] = place(sz_M[k]);
-                o_B[k] = place(sz_B[k]);
-                o_E2[k] = place(sz_E2[k]);
-            }
+        for (uint32_t k = kmin; k <= kmax; k++) {
+            o_F[k] = place(sz_F[k]);
+            o_C[k] = place(sz_C[k]);
+            o_E[k] = place(sz_E[k]);
+            o_M[k] = place(sz_M[k]);
+            o_B[k] = place(sz_B[k]);
+            o_E2[k] = place(sz_E2[k]);
+        }
         const uint64_t o_G = place(sz_G);
         const uint64_t o_po = place(sz_po), o_pb = place(sz_pb);
         uint64_t o_stt = place(sz_stt), o_dfin = place(sz_dfin);
@@ -767,27 +768,29 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         put(o_ind, ind.data(), sz_ind);
         put(o_sk, side_keys.data(), sz_sk);
         put(o_sv, side_vals.data(), sz_sv);
-        if (!dense)
-            for (uint32_t k = kmin; k <= kmax; k++) {
-                put(o_E2[k], E2v[k].data(), sz_E2[k]);
-                put(o_F[k], Fv[k].data(), sz_F[k]);
-                put(o_C[k], Cv[k].data(), sz_C[k]);
-                put(o_E[k], Ev[k].data(), sz_E[k]);
-                put(o_M[k], Mv[k].data(), sz_M[k]);
-                put(o_B[k], Bv[k].data(), sz_B[k]);
-            }
+        for (uint32_t k = kmin; k <= kmax; k++) {
+            put(o_E2[k], E2v[k].data(), sz_E2[k]);
+            put(o_F[k], Fv[k].data(), sz_F[k]);
+            put(o_C[k], Cv[k].data(), sz_C[k]);
+            put(o_E[k], Ev[k].data(), sz_E[k]);
+            put(o_M[k], Mv[k].data(), sz_M[k]);
+            put(o_B[k], Bv[k].data(), sz_B[k]);
+        }
         put(o_G, Gv.data(), sz_G);
         put(o_po, pat_off.data(), sz_po);
         put(o_pb, pat_bytes.data(), sz_pb);
         if (dense) {
             uint32_t *S = (uint32_t *)(host.data() + o_stt);
             uint32_t *DF = (uint32_t *)(host.data() + o_dfin);
+            // state numbers are the record numbers (chains consecutive); the
+            // root is 0 and never a child, so 0 marks "no child"
             for (uint64_t v = 0; v < Q; v++) {
-                DF[v] = fin_code[v];
+                const uint64_t sv = rec_of[v];
+                DF[sv] = fin_code[v];
                 uint32_t r = 0;
                 for (uint32_t c = 0; c < sigma; c++)
                     if ((bm[v * W + (c >> 5)] >> (c & 31)) & 1)
-                        S[v * sigma + c] = nodes[v].first_child + r++;
+                        S[sv * sigma + c] = rec_of[nodes[v].first_child + r++];
             }
         }
 
@@ -820,7 +823,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         DevTable &dv = t->dev;
         memset(&dv, 0, sizeof(dv));
         dv.sigma = sigma;
-        dv.W = F;
+        dv.W = dense ? 3u : F;  // 3: rows of the dense transition table
         dv.pk_shift = psh;
         dv.bps = bps;
         dv.kdef = kdef;
@@ -829,7 +832,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         dv.max_len = max_len;
         dv.n_rec = n_rec;
         dv.n_nodes = (uint32_t)Q;
-        dv.rec = (const uint32_t *)(B + o_rec);
+        dv.rec = (const uint32_t *)(B + (dense ? o_stt : o_rec));
         dv.fin = (const uint32_t *)(B + o_fin);
         dv.fbc = F == 0 ? (const uint32_t *)(B + o_fbc) : nullptr;
         dv.fvals = F == 0 ? (const uint32_t *)(B + o_fv) : nullptr;
@@ -845,18 +848,17 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         dv.side_keys = dag ? (const uint64_t *)(B + o_sk) : nullptr;
         dv.side_vals = dag ? (const uint32_t *)(B + o_sv) : nullptr;
         dv.side_log = side_log;
-        if (!dense)
-            for (uint32_t k = kmin; k <= kmax; k++) {
-                dv.F[k] = (const uint32_t *)(B + o_F[k]);
-                dv.C[k] = (const uint32_t *)(B + o_C[k]);
-                dv.E[k] = (const uint32_t *)(B + o_E[k]);
-                dv.M[k] = sz_M[k] ? (const uint32_t *)(B + o_M[k]) : nullptr;
-                dv.c_shift[k] = cshift[k];
-                dv.n_e[k] = (uint32_t)Ev[k].size();
-                dv.m_words[k] = (uint32_t)Mv[k].size();
-                dv.B[k] = sz_B[k] ? (const uint8_t *)(B + o_B[k]) : nullptr;
-                dv.E2[k] = dag ? (const uint32_t *)(B + o_E2[k]) : nullptr;
-            }
+        for (uint32_t k = kmin; k <= kmax; k++) {
+            dv.F[k] = (const uint32_t *)(B + o_F[k]);
+            dv.C[k] = (const uint32_t *)(B + o_C[k]);
+            dv.E[k] = (const uint32_t *)(B + o_E[k]);
+            dv.M[k] = sz_M[k] ? (const uint32_t *)(B + o_M[k]) : nullptr;
+            dv.c_shift[k] = cshift[k];
+            dv.n_e[k] = (uint32_t)Ev[k].size();
+            dv.m_words[k] = (uint32_t)Mv[k].size();
+            dv.B[k] = sz_B[k] ? (const uint8_t *)(B + o_B[k]) : nullptr;
+            dv.E2[k] = dag ? (const uint32_t *)(B + o_E2[k]) : nullptr;
+        }
         dv.G = g_len ? (const uint32_t *)(B + o_G) : nullptr;
         dv.trunc = o.truncate_depth;
         dv.n_pat = n_patterns;
@@ -867,8 +869,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         dv.g_set = g_set;
         dv.stt = dense ? (const uint32_t *)(B + o_stt) : nullptr;
         dv.dfin = dense ? (const uint32_t *)(B + o_dfin) : nullptr;
-        t->kmax = dense ? 0 : kmax;
-        t->kmin = dense ? 0 : kmin;
+        t->kmax = kmax;
+        t->kmin = kmin;
 
         t->match_density = match_density;
         pfac_table_info_t &I = t->info;
@@ -877,7 +879,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         I.min_len = min_len;
         I.max_len = max_len;
         I.layout = o.layout;
-        I.prefix_depth = dense ? 0 : dv.kdef;
+        I.prefix_depth = dv.kdef;
         I.trie_nodes = Q;
         I.trie_leaves = n_leaves;
         I.records = dense ? Q : n_rec;
@@ -894,10 +896,11 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         I.side_entries = side_n;
         I.trie_bytes = sz_rec + sz_fin + sz_fbc + sz_fv + sz_leaf + sz_pool + sz_ind + sz_sk + sz_sv;
         I.index_bytes = sz_G;
-        if (!dense)
-            for (uint32_t k = kmin; k <= kmax; k++)
-                I.index_bytes += sz_F[k] + sz_C[k] + sz_E[k] + sz_M[k] + sz_B[k] + sz_E2[k];
-        I.other_bytes = sz_po + sz_pb + sz_stt + sz_dfin;
+        for (uint32_t k = kmin; k <= kmax; k++)
+            I.index_bytes += sz_F[k] + sz_C[k] + sz_E[k] + sz_M[k] + sz_B[k] + sz_E2[k];
+        // the dense layout's transition table and outputs are its trie
+        if (dense) I.trie_bytes += sz_stt + sz_dfin;
+        I.other_bytes = sz_po + sz_pb;
         I.record_bytes = dense ? 0u : (uint32_t)RW * 4u;
         *out = t;
         return PFAC_OK;

@@ -92,15 +92,24 @@ __device__ __forceinline__ uint32_t prefix_rank(const uint32_t *Fs, uint32_t rep
 // Record words of state r needed to take a step on symbol c: the word
 // holding c's bit, the rank base below that word, the meta word and (for
 // sigma > 32) the state's output.  A packed record (W == 0) is its own meta
-// word: the all-leaf flag at bit 31 and the base below bit psh, the bitmap
-// between.
+// word: the all-leaf flag at bit 31 and the base below bit aux, the bitmap
+// between.  A row of the dense transition table (W == 3, aux = sigma) gives
+// the child itself: the step then sees a one-bit bitmap and the child as its
+// base.
 template <int W>
 __device__ __forceinline__ void load_step(const uint32_t *__restrict__ rec, uint32_t r, uint32_t c,
                                           uint32_t &word, uint32_t &below, uint32_t &meta,
-                                          uint32_t &f, uint32_t psh = 0) {
+                                          uint32_t &f, uint32_t aux = 0) {
     constexpr int RW = rec_words(W);
     const uint32_t *R = rec + (size_t)r * RW;
-    if (W == 0) {
+    const uint32_t psh = aux;
+    if (W == 3) {
+        const uint32_t nx = c < aux ? __ldg(rec + (size_t)r * aux + c) : 0u;
+        word = nx ? 1u << (c & 31) : 0u;
+        below = 0;
+        meta = nx;
+        f = 0;
+    } else if (W == 0) {
         const uint32_t v = __ldg(R);
         word = v >> psh;  // the flag lands above the bitmap, past every symbol
         below = 0;
@@ -162,6 +171,7 @@ template <int W>
 __device__ __forceinline__ uint32_t rec_fin(const MatchParams &P, uint32_t r, uint32_t f,
                                             uint32_t meta) {
     if (W == 0) return (meta & PK_FIN) ? pk_fin(P, (uint32_t)chk(P, r, P.T.n_rec)) : 0u;
+    if (W == 3) return __ldg(P.T.dfin + chk(P, r, P.T.n_rec));
     if (W == 1) return __ldg(P.T.fin + chk(P, r, P.T.n_rec));
     return f;
 }
@@ -230,7 +240,8 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
     constexpr int LOCK_ROUNDS = 3;
     constexpr bool DAG = (VAR & VAR_MERGED) != 0;
     const uint32_t sigma = P.T.sigma, k = P.k, rep = P.rep_log2;
-    const uint32_t psh = P.T.pk_shift, bmask = W == 0 ? (1u << psh) - 1u : META_BASE_MASK;
+    const uint32_t psh = W == 3 ? P.T.sigma : P.T.pk_shift;
+    const uint32_t bmask = W == 0 ? (1u << psh) - 1u : META_BASE_MASK;
     const uint32_t *__restrict__ rec = P.T.rec;
     uint32_t st[QU], qq[QU], lim[QU], fin[QU], unit[QU];
     // -1 idle, 0 walking, 1 stopped at st, 2 stopped on merged leaf st, 3 done,
@@ -311,9 +322,10 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                     fin[u] = 0;
                     state[u] = 3;
                 } else {
-                    if (W <= 1) st[u] = cur;
+                    constexpr bool sep = W <= 1 || W == 3;  // outputs in their own array
+                    if (sep) st[u] = cur;
                     else fin[u] = f1[u];
-                    state[u] = W <= 1 ? 1 : 3;
+                    state[u] = sep ? 1 : 3;
                 }
             } else if (DAG) {
                 st[u] = cur;

@@ -31,8 +31,18 @@ void *scan_kernel_r2_g0_fe(int rep, int nw);
 void *scan_kernel_r2_g1_f(int rep, int nw);
 void *scan_kernel_r2_g1_fe(int rep, int nw);
 
+void *scan_kernel_r8_d0(int rep, int var, int nw);
+void *scan_kernel_r8_d1(int rep, int var, int nw);
+void *scan_kernel_r2_d0(int rep, int var, int nw);
+void *scan_kernel_r2_d1(int rep, int var, int nw);
+
 // the register-staged kernel for 8-bit or 2-bit symbols
 static void *scan_kernel_r(uint32_t bps, uint32_t w, int rep, bool gram, int var, int nw) {
+    if (w == 3) {  // the dense layout's transition table
+        if (bps == 2) return gram ? scan_kernel_r2_d1(rep, var, nw) : scan_kernel_r2_d0(rep, var, nw);
+        if (bps == 8) return gram ? scan_kernel_r8_d1(rep, var, nw) : scan_kernel_r8_d0(rep, var, nw);
+        return nullptr;
+    }
     if (bps == 2) {
         if (w != 0) return nullptr;  // packed records only
         if (gram) return var == VAR_FE ? scan_kernel_r2_g1_fe(rep, nw) : scan_kernel_r2_g1_f(rep, nw);
@@ -312,7 +322,7 @@ struct Plan {
     uint32_t e_tbl_words, e_tbl_m_words;
 };
 
-enum { SCAN_QUEUED = 1, SCAN_REGISTER = 2 };
+enum { SCAN_QUEUED = 1, SCAN_REGISTER = 2, SCAN_SERIAL = 3 };
 
 struct WsLayout {
     uint64_t hdr, tile_m, tile_k, key_off, chunk, ovf, recs, bounds, total;
@@ -510,7 +520,11 @@ static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks,
 static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl) {
     const DevTable &T = t->dev;
     memset(pl, 0, sizeof(*pl));
-    if (T.layout == PFAC_LAYOUT_DENSE) {
+    // the dense layout runs the compressed layout's kernels over its
+    // transition table (record format 3), or on request the thread-serial
+    // kernel (scan_kernel 3)
+    if (T.layout == PFAC_LAYOUT_DENSE && opts && opts->scan_kernel == SCAN_SERIAL) {
+        pl->kind = SCAN_SERIAL;
         pl->var = VAR_DENSE;
         uint32_t rows = (uint32_t)(TABLE_SMEM_MAX / (4ull * T.sigma));
         if (rows > T.n_nodes) rows = T.n_nodes;
@@ -600,7 +614,8 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     // default when the caller asks for nothing only the queued kernel has
     const uint32_t want_kind = opts && opts->scan_kernel ? opts->scan_kernel
                                                          : (use_tuned ? t->tuned_kernel : 0u);
-    if (want_kind > 2) return set_error(PFAC_EINVAL, "pfac_match: scan_kernel %u", want_kind);
+    if (want_kind > 2)
+        return set_error(PFAC_EINVAL, "pfac_match: scan_kernel %u (3: dense layout only)", want_kind);
     const bool r_usable = (T.bps == 8 || T.bps == 2) && pbytes != 2 && !T.dag;
     if (want_kind == SCAN_REGISTER && !r_usable)
         return set_error(PFAC_EINVAL, "pfac_match: the register-staged kernel needs 8-bit or 2-bit "

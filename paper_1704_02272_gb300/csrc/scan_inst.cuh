@@ -3,7 +3,8 @@
 // keeps compile times parallel).  Alphabets of up to 8 symbols have two
 // record formats: packed (W = 0) in every configuration, and the two-word
 // records of the 32-symbol format (W = 1, tries too large to pack, or built
-// with wide records) for the default CTA width.
+// with wide records) for the default CTA width.  Rows of the dense layout's
+// transition table (W = 3) run in the same kernel, default CTA width.
 #include "kernels_q.cuh"
 
 #define PFAC_CAT2(a, b) a##b
@@ -37,6 +38,8 @@ void *PFAC_CAT(scan_kernel_bps, PFAC_SCAN_BPS)(int var, int emit, int nw, int w)
         return nullptr;
     }
     if (kW == 0 && w == 1 && nw == QW) return scan_kernel_nw<kW == 0 ? 1 : kW, QW>(var, emit);
+    // the dense layout's transition table in the same kernel
+    if (w == 3 && nw == QW) return scan_kernel_nw<3, QW>(var, emit);
     return nullptr;
 }
 

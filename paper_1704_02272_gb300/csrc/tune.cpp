@@ -32,9 +32,11 @@ std::string cache_key(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments
     uint32_t lg = 0;
     while ((1ull << (lg + 1)) <= n_bytes) lg++;
     char buf[256];
-    snprintf(buf, sizeof buf, "sigma=%u,n=%u,maxlen=%u,segs=%s,bytes=2^%u,gpu=%s",
-             t->info.alphabet_size, t->info.n_patterns, t->info.max_len,
-             n_segments > 1 ? "many" : "one", lg, gpu.c_str());
+    // the record format (packed, wide, dense rows ...) and the merge are part
+    // of the key: each makes its own plans
+    snprintf(buf, sizeof buf, "sigma=%u,n=%u,maxlen=%u,rec=%u%s,segs=%s,bytes=2^%u,gpu=%s",
+             t->info.alphabet_size, t->info.n_patterns, t->info.max_len, t->dev.W,
+             t->dev.dag ? "m" : "", n_segments > 1 ? "many" : "one", lg, gpu.c_str());
     return buf;
 }
 
@@ -94,8 +96,6 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
                              const char *cache_path, void *cuda_stream, pfac_tune_result *out) {
     clear_error();
     if (!t) return set_error(PFAC_EINVAL, "pfac_autotune: NULL table");
-    if (t->info.layout != PFAC_LAYOUT_COMPRESSED)
-        return set_error(PFAC_EINVAL, "pfac_autotune: only the compressed layout has choices");
     pfac_tune_result res;
     memset(&res, 0, sizeof res);
     const std::string key = cache_key(t, n_bytes, n_segments);

@@ -26,19 +26,27 @@ def run(w, **kw):
 def check_all_variants(w, what, depths=None):
     ref = oracle_keys(w)
     assert_same(run(w), ref, f"{what} default")
+    # the dense layout: its transition table in the library's kernels, and
+    # the thread-serial kernel
     assert_same(run(w, layout=pfac.LAYOUT_DENSE), ref, f"{what} dense")
-    for var in (pfac.VARIANT_FILTER, pfac.VARIANT_DSMEM):
-        for k in depths or [0]:
-            try:
-                kk = 0 if k is None else k
-                if k == "min":
-                    with pfac.Table(w.patterns, w.sigma, host_only=True) as th:
-                        kk = max(1, th.info()["prefix_depth"] - 2)
-                got = run(w, variant=var, prefix_depth=kk)
-            except pfac.PfacError as e:  # a prefix node too large for shared memory
-                assert e.status == -1, str(e)
-                continue
-            assert_same(got, ref, f"{what} variant {var} depth {k}")
+    assert_same(run(w, layout=pfac.LAYOUT_DENSE, scan_kernel=pfac.binding.KERNEL_SERIAL), ref,
+                f"{what} dense, thread-serial kernel")
+    ran = 0
+    for layout in (pfac.LAYOUT_COMPRESSED, pfac.LAYOUT_DENSE):
+        for var in (pfac.VARIANT_FILTER, pfac.VARIANT_DSMEM):
+            for k in depths or [0]:
+                try:
+                    kk = 0 if k is None else k
+                    if k == "min":
+                        with pfac.Table(w.patterns, w.sigma, host_only=True) as th:
+                            kk = max(1, th.info()["prefix_depth"] - 2)
+                    got = run(w, layout=layout, variant=var, prefix_depth=kk)
+                except pfac.PfacError as e:  # a prefix node too large for shared memory
+                    assert e.status == -1, str(e)
+                    continue
+                assert_same(got, ref, f"{what} layout {layout} variant {var} depth {k}")
+                ran += 1
+    assert ran >= 2
     return ref
 
 

@@ -18,9 +18,12 @@ pytestmark = pytest.mark.skipif(torch.cuda.is_available(),
 
 def cache_key(t, n_bytes, n_segments):
     i = t.info()
+    # record format: 0 packed, 1 / 2 / 8 bitmap words, 3 dense rows
+    fmt = {4: 0, 8: 1, 16: 2, 48: 8, 0: 3}[i["record_bytes"]]
+    merged = "m" if i["merged_trie_nodes"] else ""
     return (f"sigma={i['alphabet_size']},n={i['n_patterns']},maxlen={i['max_len']},"
-            f"segs={'many' if n_segments > 1 else 'one'},bytes=2^{int(math.log2(n_bytes))},"
-            f"gpu=unknown")
+            f"rec={fmt}{merged},segs={'many' if n_segments > 1 else 'one'},"
+            f"bytes=2^{int(math.log2(n_bytes))},gpu=unknown")
 
 
 def sample():
