@@ -214,6 +214,8 @@ def dist_setup(n_gpus):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
+        # NCCL's own log (rank count, transport) stays on, on stderr
+        os.environ.setdefault("NCCL_DEBUG", "INFO")
         dist.init_process_group("nccl")
     return rank, world, local
 
@@ -791,7 +793,9 @@ def main():
     ap.add_argument("--workload", default="dna")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per scan launch from an ncu capture of the current kernel sources")
-    ap.add_argument("--ref-sample-mib", type=int, default=16)
+    # the reference arm's sample: the same 128 MiB of start positions as the
+    # cpu_baseline leg of the default line
+    ap.add_argument("--ref-sample-mib", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-suffix-merge", action="store_true",
                     help="skip the merged-trie table (reduction step 2) beside the plain one")

@@ -94,6 +94,12 @@ def test_sweep_cell(sigma, n):
     kd = device_keys(w, text, seg, pfac.LAYOUT_DENSE)
     assert kc.numel() == kd.numel() and torch.equal(kc, kd), "compressed != dense"
     del kd
+    # the dense layout's thread-serial kernel: another walk over the same trie
+    with pfac.Table(w.patterns, w.sigma, layout=pfac.LAYOUT_DENSE) as t:
+        ks = pfac.match(t, text, seg, scan_kernel=pfac.binding.KERNEL_SERIAL)
+        torch.cuda.synchronize()
+    assert ks.numel() == kc.numel() and torch.equal(ks, kc), "compressed != thread-serial dense"
+    del ks
     # sorted, unique, in range
     if kc.numel() > 1:
         assert bool((kc[1:] > kc[:-1]).all())

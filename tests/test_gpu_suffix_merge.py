@@ -5,7 +5,8 @@ through the queued kernel's merged-trie instance and every plan that fits
 walks end inside shared subtrees at every depth (prefix entries whose state
 is a merged node, walks that stop one to three levels below their last
 unshared node, patterns that are prefixes of others), and at the full size
-of the DNA-shaped workload."""
+of the DNA-shaped workload and of the alphabet-4 sweep cell with 10,000
+patterns (512 MiB, about 3e8 matches)."""
 import itertools
 
 import numpy as np
@@ -129,5 +130,29 @@ def test_merged_trie_full_size_dna():
         with pfac.Table(w.patterns, 4, suffix_merge=True) as t:
             for opt in ({}, {"child_masks": 1}, {"prefix_depth": 8}):
                 assert_same(run(t, text, seg, **opt), ref, f"dna merged {opt}")
+    finally:
+        ac.close()
+
+
+def test_merged_trie_full_size_sigma4_10k():
+    # the match-dense alphabet-4 cell (patterns from 4 symbols long) at its
+    # full 512 MiB: every key against the oracle, 32 MiB of start positions at
+    # a time
+    from tests.gpu_util import window
+    w = workloads.config4(4, 10000)
+    text, seg = to_device(w)
+    import oracle
+    ac = oracle.ACOracle(w.patterns)
+    try:
+        with pfac.Table(w.patterns, 4, suffix_merge=True) as t:
+            assert t.info()["merged_trie_nodes"] < t.info()["trie_nodes"]
+            kc = pfac.match(t, text, seg)
+            torch.cuda.synchronize()
+        chunk, total = 32 << 20, 0
+        for a in range(0, w.n_bytes, chunk):
+            ref = oracle_keys(w, lo=a, hi=min(a + chunk, w.n_bytes), ac=ac)
+            assert_same(window(kc, a, a + chunk), ref, f"merged sigma4x10k chunk at {a}")
+            total += ref.shape[0]
+        assert total == kc.numel()
     finally:
         ac.close()

@@ -4,6 +4,8 @@ fits the 232,448-byte shared-memory limit of an sm_103a CTA and honours every
 option the caller fixed, or the call fails cleanly with PFAC_EINVAL."""
 import itertools
 
+import numpy as np
+
 import pytest
 
 import workloads
@@ -160,3 +162,64 @@ def test_register_staged_plans_2_bit(n):
             assert p["scan_kernel"] == 2 and p["smem_bytes"] <= SMEM_LIMIT, (opt, p)
             assert p["prefix_depth"] == k
         assert n_ok > 0
+
+
+def _entries_by_enumeration(t, k, bps):
+    """Prefix-node entries of depth k, counted over every k-symbol index: the
+    walk from the root over the index's symbols (b bits each, first symbol
+    lowest; values >= sigma have no child) reaches depth k, or stops earlier
+    at a node on whose path some pattern ends."""
+    import numpy as np
+    n = t.n_nodes
+    A = 1 << bps
+    child = np.full((n, A), -1, dtype=np.int64)
+    for v in range(n):
+        for c in range(t.sigma):
+            u = t.child(v, c)
+            if u is not None:
+                child[v, c] = u
+    # a node "has output" when a pattern ends on its path from the root
+    out = np.zeros(n, dtype=bool)
+    for v in range(n):  # breadth-first: parents first
+        if t.final_id[v] >= 0:
+            out[v] = True
+        for c in range(t.sigma):
+            u = t.child(v, c)
+            if u is not None and out[v]:
+                out[u] = True
+    x = np.arange(1 << (k * bps), dtype=np.int64)
+    state = np.zeros(x.size, dtype=np.int64)
+    alive = np.ones(x.size, dtype=bool)
+    count = 0
+    for i in range(k):
+        sym = (x >> (bps * i)) & (A - 1)
+        nxt = np.where(alive, child[state, sym], -1)
+        stopped = alive & (nxt < 0)
+        count += int(out[state[stopped]].sum())
+        alive &= nxt >= 0
+        state = np.where(alive, nxt, state)
+    return count + int(alive.sum())
+
+
+@pytest.mark.parametrize("seed,sigma,n,lo,hi", [(1, 200, 300, 1, 6), (2, 256, 2000, 2, 9),
+                                                (3, 64, 150, 1, 5), (4, 60, 40, 2, 8),
+                                                (5, 256, 30, 1, 3)])
+def test_default_prefix_depth_rule(seed, sigma, n, lo, hi):
+    # the builder's default depth: the shallowest depth whose entries are at
+    # most 1/256 of its indices, among the depths whose entries take at most
+    # a quarter of the records' bytes (64 KiB at least), else the deepest of
+    # those; entries counted here by enumerating every index
+    from oracle import trie as T
+    pats = workloads.uniform_patterns(np.random.RandomState(seed), n, sigma, lo, hi)
+    pats = list(dict.fromkeys(pats))
+    t = T.build_paper_trie(pats, sigma)
+    bps = max(1, (sigma - 1).bit_length())
+    klim = min(max(1, 20 // bps), 16)
+    kfloor = (5 + bps - 1) // bps
+    with pfac.Table(pats, sigma, host_only=True) as lt:
+        info = lt.info()
+    budget = max(64 * 1024, info["records"] * info["record_bytes"] // 4)
+    ents = {k: _entries_by_enumeration(t, k, bps) for k in range(kfloor, klim + 1)}
+    kcap = max([k for k in ents if 4 * ents[k] <= budget] or [kfloor])
+    want = next((k for k in range(kfloor, kcap + 1) if ents[k] * 256 <= (1 << (k * bps))), kcap)
+    assert info["prefix_depth"] == want, (ents, budget)
