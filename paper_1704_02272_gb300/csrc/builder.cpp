@@ -326,7 +326,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         }
         if (dag) {
             n_upper = n_rec;
-            if ((uint64_t)n_upper + canon_rep.size() >= (1ull << 30))
+            if ((uint64_t)n_upper + canon_rep.size() >= (1ull << D_TAIL_SHIFT))
                 return set_error(PFAC_EINVAL, "pfac_build: merged trie too large");
             for (uint64_t v = 1; v < Q; v++)
                 if (!upper[v]) rec_of[v] = n_upper + canon[v];
@@ -411,13 +411,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         // prefix node of depth k: bitmap, block counts, entries (Eq. 1 on the
         // collapsed first k levels)
         std::vector<uint32_t> Fv[KMAX + 1], Cv[KMAX + 1], Ev[KMAX + 1], Mv[KMAX + 1];
-        // merged trie: per entry whose depth-k state is a merged node, its last
-        // tree ancestor's record and the depth below it (0 for tree nodes)
-        std::vector<uint32_t> E2v[KMAX + 1];
         std::vector<uint8_t> Bv[KMAX + 1];
         uint32_t cshift[KMAX + 1] = {0};
         uint64_t sz_F[KMAX + 1] = {0}, sz_C[KMAX + 1] = {0}, sz_E[KMAX + 1] = {0},
-                 sz_M[KMAX + 1] = {0}, sz_B[KMAX + 1] = {0}, sz_E2[KMAX + 1] = {0};
+                 sz_M[KMAX + 1] = {0}, sz_B[KMAX + 1] = {0};
         for (uint32_t k = kmin; k <= kmax; k++) {
             const uint64_t ent = 1ull << (k * bps);
             const uint32_t smask = (1u << bps) - 1;
@@ -433,7 +430,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
             const bool with_b = k * bps <= BYTES_MAX_BITS && n_ent[k] * 100 >= ent;
             if (with_b) Bv[k].assign(ent < 4 ? 4 : ent, 0);
             for (uint64_t x = 0; x < ent; x++) {
-                uint32_t v = 0, e = 0, e2 = 0;
+                uint32_t v = 0, e = 0;
                 bool stopped = false;
                 for (uint32_t i = 0; i < k; i++) {
                     const int64_t ch = child_of(v, (uint32_t)(x >> (bps * i)) & smask);
@@ -451,12 +448,14 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                     } else {
                         e = D_CONT | rec_of[v];
                         if (dag && !upper[v]) {
+                            // a tail record: the entry names the last tree
+                            // record and the depth below it instead
                             uint32_t u = v, d = 0;
                             while (!upper[u]) {
                                 u = nodes[u].parent;
                                 d++;
                             }
-                            e2 = rec_of[u] | (d << 30);
+                            e = D_CONT | D_TAIL | (d << D_TAIL_SHIFT) | rec_of[u];
                         }
                         if (fin_code[v] == 0) {
                             mask = 0;
@@ -472,7 +471,6 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 if (e) {
                     Fv[k][x >> 5] |= 1u << (x & 31);
                     Ev[k].push_back(e);
-                    if (dag) E2v[k].push_back(e2);
                     Mv[k].push_back(mask);
                     if (with_b) Bv[k][x] = (uint8_t)bucket;
                 }
@@ -485,12 +483,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
             if (Ev[k].empty()) {
                 Ev[k].push_back(0);
                 Mv[k].push_back(0);
-                if (dag) E2v[k].push_back(0);
             }
             sz_F[k] = fw * 4;
             sz_C[k] = Cv[k].size() * 4;
             sz_E[k] = Ev[k].size() * 4;
-            sz_E2[k] = E2v[k].size() * 4;
             // narrow masks for small alphabets: mask_bits(sigma) bits per
             // entry, packed low entry first (an all-ones mask still means
             // "keep whatever follows")
@@ -699,7 +695,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         // below it, the symbols from there); open addressing, linear probes
         std::vector<uint64_t> side_keys;
         std::vector<uint32_t> side_vals;
-        uint32_t side_log = 0;
+        uint32_t side_slots = 0;
         uint64_t side_n = 0;
         if (dag) {
             std::vector<uint64_t> ks;
@@ -717,12 +713,12 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                 vs.push_back(fin_code[v]);
             }
             side_n = ks.size();
-            while ((1ull << side_log) < 2 * std::max<uint64_t>(side_n, 8)) side_log++;
-            side_keys.assign(1ull << side_log, DAG_SIDE_EMPTY);
-            side_vals.assign(1ull << side_log, 0);
+            side_slots = (uint32_t)std::max<uint64_t>(16, side_n + side_n / 4 + 1);
+            side_keys.assign(side_slots, DAG_SIDE_EMPTY);
+            side_vals.assign(side_slots, 0);
             for (size_t i = 0; i < ks.size(); i++) {
-                uint64_t h = dag_side_slot(ks[i], side_log);
-                while (side_keys[h] != DAG_SIDE_EMPTY) h = (h + 1) & ((1ull << side_log) - 1);
+                uint64_t h = dag_side_slot(ks[i], side_slots);
+                while (side_keys[h] != DAG_SIDE_EMPTY) h = h + 1 == side_slots ? 0 : h + 1;
                 side_keys[h] = ks[i];
                 side_vals[h] = vs[i];
             }
@@ -740,14 +736,13 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
                  o_pool = place(sz_pool), o_fbc = place(sz_fbc), o_fv = place(sz_fv);
         const uint64_t o_ind = place(sz_ind), o_sk = place(sz_sk), o_sv = place(sz_sv);
         uint64_t o_F[KMAX + 1] = {0}, o_C[KMAX + 1] = {0}, o_E[KMAX + 1] = {0},
-                 o_M[KMAX + 1] = {0}, o_B[KMAX + 1] = {0}, o_E2[KMAX + 1] = {0};
+                 o_M[KMAX + 1] = {0}, o_B[KMAX + 1] = {0};
         for (uint32_t k = kmin; k <= kmax; k++) {
             o_F[k] = place(sz_F[k]);
             o_C[k] = place(sz_C[k]);
             o_E[k] = place(sz_E[k]);
             o_M[k] = place(sz_M[k]);
             o_B[k] = place(sz_B[k]);
-            o_E2[k] = place(sz_E2[k]);
         }
         const uint64_t o_G = place(sz_G);
         const uint64_t o_po = place(sz_po), o_pb = place(sz_pb);
@@ -769,7 +764,6 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         put(o_sk, side_keys.data(), sz_sk);
         put(o_sv, side_vals.data(), sz_sv);
         for (uint32_t k = kmin; k <= kmax; k++) {
-            put(o_E2[k], E2v[k].data(), sz_E2[k]);
             put(o_F[k], Fv[k].data(), sz_F[k]);
             put(o_C[k], Cv[k].data(), sz_C[k]);
             put(o_E[k], Ev[k].data(), sz_E[k]);
@@ -847,7 +841,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         dv.ind_words = dag ? (uint32_t)ind.size() : 0u;
         dv.side_keys = dag ? (const uint64_t *)(B + o_sk) : nullptr;
         dv.side_vals = dag ? (const uint32_t *)(B + o_sv) : nullptr;
-        dv.side_log = side_log;
+        dv.side_slots = side_slots;
         for (uint32_t k = kmin; k <= kmax; k++) {
             dv.F[k] = (const uint32_t *)(B + o_F[k]);
             dv.C[k] = (const uint32_t *)(B + o_C[k]);
@@ -857,7 +851,6 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
             dv.n_e[k] = (uint32_t)Ev[k].size();
             dv.m_words[k] = (uint32_t)Mv[k].size();
             dv.B[k] = sz_B[k] ? (const uint8_t *)(B + o_B[k]) : nullptr;
-            dv.E2[k] = dag ? (const uint32_t *)(B + o_E2[k]) : nullptr;
         }
         dv.G = g_len ? (const uint32_t *)(B + o_G) : nullptr;
         dv.trunc = o.truncate_depth;
@@ -897,7 +890,7 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         I.trie_bytes = sz_rec + sz_fin + sz_fbc + sz_fv + sz_leaf + sz_pool + sz_ind + sz_sk + sz_sv;
         I.index_bytes = sz_G;
         for (uint32_t k = kmin; k <= kmax; k++)
-            I.index_bytes += sz_F[k] + sz_C[k] + sz_E[k] + sz_M[k] + sz_B[k] + sz_E2[k];
+            I.index_bytes += sz_F[k] + sz_C[k] + sz_E[k] + sz_M[k] + sz_B[k];
         // the dense layout's transition table and outputs are its trie
         if (dense) I.trie_bytes += sz_stt + sz_dfin;
         I.other_bytes = sz_po + sz_pb;

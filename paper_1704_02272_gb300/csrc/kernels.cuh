@@ -86,7 +86,6 @@ struct MatchParams {
     const uint32_t *F;    // prefix node of depth k: bitmap,
     const uint32_t *C;    //   block counts,
     const uint32_t *E;    //   entries
-    const uint32_t *E2;   //   merged trie: last tree record | depth << 30 per entry
     const uint32_t *M;    //   child masks of the entries
     uint32_t tbl_words;   // shared-memory words: bitmap copies (or dense rows)
     uint32_t tbl_c_words;

@@ -214,14 +214,14 @@ __device__ __noinline__ uint32_t dag_walk(const MatchParams *PP, uint32_t s, uin
     }
     if (s < n_upper) return rec_fin<W>(P, s, f, meta);
     const uint64_t key = dag_side_key(u, d, tp);
-    const uint64_t m = (1ull << P.T.side_log) - 1u;
-    uint64_t h = dag_side_slot(key, P.T.side_log);
-    // at most half the slots are taken, so a probe meets the key or a hole
-    for (uint64_t i = 0; i <= m; i++) {
+    const uint32_t n = P.T.side_slots;
+    uint64_t h = dag_side_slot(key, n);
+    // a fifth of the slots at least are empty, so a probe meets the key or a hole
+    for (uint32_t i = 0; i < n; i++) {
         const uint64_t kk = __ldg(reinterpret_cast<const unsigned long long *>(P.T.side_keys) + h);
         if (kk == key) return __ldg(P.T.side_vals + h);
         if (kk == DAG_SIDE_EMPTY) break;
-        h = (h + 1u) & m;
+        h = h + 1 == n ? 0 : h + 1;
     }
     return 0;
 }
@@ -274,13 +274,12 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                 if (ev & D_CONT) {
                     state[u] = 0;
                     st[u] = ev & D_VAL_MASK;
-                    if (DAG && st[u] >= P.T.n_upper) {
+                    if (DAG && (ev & D_TAIL)) {
                         // a tail record of the merged trie: walk again from
                         // the last tree record, d symbols back
-                        const uint32_t e2 = __ldg(P.E2 + r);
                         state[u] = 4;
-                        st[u] = e2 & 0x3FFFFFFFu;
-                        qq[u] -= e2 >> 30;
+                        st[u] = ev & D_TAIL_REC;
+                        qq[u] -= (ev >> D_TAIL_SHIFT) & 3u;
                     }
                 } else {
                     state[u] = 3;
@@ -371,7 +370,7 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
             // Each round fetches TS consecutive records from the current state
             // and the next TS symbols; along a single-child chain (placed in
             // consecutive records) a round advances up to TS levels.
-            constexpr int TS = W == 8 ? 4 : 8;
+            constexpr int TS = (W == 8 || W == 2) ? 4 : 8;  // (wider records: fewer per round, no spills)
             const uint32_t n_rec = P.T.n_rec;
             bool done = false;
             while (!done) {

@@ -962,7 +962,6 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.F = pl.k ? t->dev.F[pl.k] : nullptr;
     P.C = pl.k ? t->dev.C[pl.k] : nullptr;
     P.E = pl.k ? t->dev.E[pl.k] : nullptr;
-    P.E2 = pl.k && t->dev.dag ? t->dev.E2[pl.k] : nullptr;
     P.M = pl.k ? t->dev.M[pl.k] : nullptr;
     P.c_shift = pl.k ? t->dev.c_shift[pl.k] : 0u;
     P.tbl_m_words = pl.tbl_m_words;

@@ -45,7 +45,8 @@
 // below its last tree record u after d symbols s_0 .. s_{d-1} finds its
 // output (the fin of the tree node it reached) in the side table under
 // dag_side_key(u, d, s_0 | s_1 << bps | ...), absent meaning none.  A
-// prefix entry whose depth-k state is a tail record has E2 = u | d << 30.
+// prefix entry whose depth-k state is a tail record names u and d instead
+// (D_TAIL).
 //
 // Dense layout (uncompressed PFAC): stt[s * sigma + c] = child or 0 (the root
 // is never a child), dfin[s] = fin(s).
@@ -61,6 +62,12 @@ constexpr uint32_t META_IND = 0x40000000u;        // merged trie: children throu
 constexpr uint32_t META_BASE_MASK = 0x3FFFFFFFu;
 constexpr uint32_t D_CONT = 0x80000000u;  // prefix entry: continue at record
 constexpr uint32_t D_VAL_MASK = 0x7FFFFFFFu;
+// merged trie: a prefix entry whose state is a tail record holds D_CONT |
+// D_TAIL | d << D_TAIL_SHIFT | u (u the last tree record above the state, d
+// its depth below u; merged tries keep fewer than 2^28 records)
+constexpr uint32_t D_TAIL = 0x40000000u;
+constexpr uint32_t D_TAIL_SHIFT = 28;
+constexpr uint32_t D_TAIL_REC = (1u << D_TAIL_SHIFT) - 1u;
 // fin encoding: 0 = empty; else (off << FIN_LEN_BITS) | len, len < FIN_LEN_ESC
 // with ids at pool[off .. off+len); len == FIN_LEN_ESC means the length is
 // pool[off] and the ids follow it.
@@ -88,14 +95,15 @@ __host__ __device__ constexpr uint32_t pk_shift(uint32_t sigma) { return sigma <
 constexpr uint32_t PK_FIN = 0x40000000u;
 
 // Side table of the merged trie: key of (tree record u, depth d below it,
-// packed symbols tp), its slot (Fibonacci hashing of the key over 2^log
-// slots; linear probing from there), the empty key.
+// packed symbols tp), its slot (the key's Fibonacci hash scaled to the
+// table's n slots, at most 80% of them taken; linear probing from there),
+// the empty key.
 constexpr uint64_t DAG_SIDE_EMPTY = ~0ull;
 __host__ __device__ inline uint64_t dag_side_key(uint32_t u, uint32_t d, uint32_t tp) {
     return ((uint64_t)u << 32) | ((uint64_t)d << 28) | tp;
 }
-__host__ __device__ inline uint64_t dag_side_slot(uint64_t key, uint32_t log) {
-    return log ? (key * 0x9E3779B97F4A7C15ull) >> (64 - log) : 0;
+__host__ __device__ inline uint64_t dag_side_slot(uint64_t key, uint32_t n) {
+    return (((key * 0x9E3779B97F4A7C15ull) >> 32) * (uint64_t)n) >> 32;
 }
 
 // Gram filter hash of a string x of n = g * bps <= 32 bits: y = x * m with
@@ -175,10 +183,9 @@ struct DevTable {
     uint32_t n_upper;         // records below it are tree records (all, without the merge)
     const uint32_t *ind;      // child indirection
     uint32_t ind_words;
-    uint32_t side_log;        // log2 of the side table's slots
+    uint32_t side_slots;      // slots of the side table
     const uint64_t *side_keys;
     const uint32_t *side_vals;
-    const uint32_t *E2[KMAX + 1];  // per prefix entry: last tree record | depth << 30
 };
 
 }  // namespace pfac
