@@ -64,7 +64,7 @@ MEASURED_TRAFFIC = {
              {"variant": 1, "prefix_depth": 2, "bitmap_copies": 2, "child_masks": 2,
               "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 24})],
 }
-KERNEL_SOURCES = ["kernels_q.cuh", "kernels.cuh", "table.h"]
+KERNEL_SOURCES = ["kernels_q.cuh", "kernels_r.cuh", "kernels.cuh", "table.h"]
 TUNE_SAMPLE = 128 << 20
 E2E_CHUNK = 32 << 20
 
@@ -259,7 +259,8 @@ def user_options(args):
     for key, val in (("variant", args.variant), ("prefix_depth", args.prefix_depth),
                      ("bitmap_copies", args.copies), ("child_masks", args.masks),
                      ("gram_filter", args.gram), ("prefix_bytes", args.bytes),
-                     ("warps_per_cta", args.warps), ("scan_kernel", args.kernel)):
+                     ("warps_per_cta", args.warps), ("scan_kernel", args.kernel),
+                     ("records_per_slice", args.records)):
         if val:
             user_opt[key] = val
     return user_opt
@@ -815,6 +816,7 @@ def main():
     ap.add_argument("--gram", type=int, default=0, help="gram filter first stage: 1 off, 2 on")
     ap.add_argument("--bytes", type=int, default=0, help="prefix bytes first stage: 1 off, 2 on")
     ap.add_argument("--warps", type=int, default=0, help="scan-kernel warps per CTA: 16 or 24")
+    ap.add_argument("--records", type=int, default=0, help="records per slice: 32 or 512")
     ap.add_argument("--kernel", type=int, default=0,
                     help="scan kernel: 1 queued (input staged in shared memory), 2 register-staged "
                          "(alphabets of 129-256 symbols)")
