@@ -48,21 +48,14 @@ SCAN_KERNELS_PER_STEP = 5  # scan, key-count reduce, offsets, overflow re-scan, 
 # autotuner settles on one of near-equal plans), with the digest of the
 # kernel sources they were taken on; reported only while the sources match
 MEASURED_TRAFFIC = {
-    "dna": [(306780928, "dc8525eacb2c3b8e",
+    "dna": [(304525824, "0495ffcbb37b5bdb",
              {"variant": 1, "prefix_depth": 10, "bitmap_copies": 1, "child_masks": 1,
-              "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 16})],
-    "sweep-256-1000": [(546757632, "dc8525eacb2c3b8e",
-                        {"variant": 2, "prefix_depth": 2, "bitmap_copies": 1, "child_masks": 1,
-                         "gram_filter": 2, "prefix_bytes": 1, "warps_per_cta": 24}),
-                       (546706176, "dc8525eacb2c3b8e",
+              "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 16, "scan_kernel": 1,
+              "records_per_slice": 512})],
+    "sweep-256-1000": [(554916096, "0495ffcbb37b5bdb",
                         {"variant": 1, "prefix_depth": 2, "bitmap_copies": 1, "child_masks": 1,
-                         "gram_filter": 2, "prefix_bytes": 1, "warps_per_cta": 24})],
-    "ids": [(1292476160, "dc8525eacb2c3b8e",
-             {"variant": 1, "prefix_depth": 2, "bitmap_copies": 1, "child_masks": 2,
-              "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 24}),
-            (1292451584, "dc8525eacb2c3b8e",
-             {"variant": 1, "prefix_depth": 2, "bitmap_copies": 2, "child_masks": 2,
-              "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 24})],
+                         "gram_filter": 2, "prefix_bytes": 1, "warps_per_cta": 16,
+                         "scan_kernel": 2, "records_per_slice": 32})],
 }
 KERNEL_SOURCES = ["kernels_q.cuh", "kernels_r.cuh", "kernels.cuh", "table.h"]
 TUNE_SAMPLE = 128 << 20
