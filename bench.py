@@ -824,7 +824,7 @@ def main():
                          "captured CUDA graph of one call")
     ap.add_argument("--loads", default="10,25,50,100,200,300,400")
     ap.add_argument("--serve-batches", type=int, default=48)
-    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-pool", type=int, default=4096, help="MiB")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-min", type=int, default=30)
