@@ -200,6 +200,10 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         }
         const uint64_t Q = nodes.size();
         if (Q >= 0x7FFFFFF0ull) return set_error(PFAC_EINVAL, "pfac_build: trie too large");
+        // the kernels carry a state number in 30 bits
+        if (Q > META_BASE_MASK)
+            return set_error(PFAC_EINVAL, "pfac_build: %llu trie nodes exceed 2^30",
+                             (unsigned long long)Q);
 
         // ---- output lists: fin(v) = fin(parent) plus v's own id ----------
         std::vector<uint32_t> fin_code(Q, 0), pool;

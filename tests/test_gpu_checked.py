@@ -31,7 +31,7 @@ def test_small_suites_under_the_checked_build():
     r = subprocess.run(
         [sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider",
          "tests/test_gpu_small.py", "tests/test_gpu_register.py", "tests/test_gpu_prefix.py",
-         "tests/test_gpu_suffix_merge.py",
+         "tests/test_gpu_suffix_merge.py", "tests/test_gpu_records.py",
          "-k", "not full_size"],
         cwd=ROOT, env=env, capture_output=True, text=True, timeout=3000)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
