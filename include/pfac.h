@@ -100,7 +100,8 @@ typedef struct {
  * Matches are the same; merged_trie_nodes in pfac_table_info counts the
  * nodes kept.  Such a table is matched by the queued scan kernel with its
  * prefix entries in L2 (variant 1) and 16 warps per CTA; other requests
- * return PFAC_EINVAL. */
+ * return PFAC_EINVAL.  With alphabets of up to 8 symbols the merge takes the
+ * packed records (not with PFAC_BUILD_WIDE_RECORDS). */
 #define PFAC_BUILD_SUFFIX_MERGE 2u
 /* Build flag (compressed layout, alphabets of up to 8 symbols): keep the
  * two-word records of the 32-symbol format instead of one packed word per

@@ -357,6 +357,11 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
         const bool packed = !dense && sigma <= 8 && !(o.flags & PFAC_BUILD_WIDE_RECORDS) &&
                             Q < (1ull << psh);
         const uint32_t F = packed ? 0u : W;
+        // the merged trie's kernel instances take each alphabet's own format
+        if (dag && sigma <= 8 && !packed)
+            return set_error(PFAC_EINVAL, "pfac_build: the suffix merge takes packed records for "
+                             "alphabets of up to 8 symbols (no PFAC_BUILD_WIDE_RECORDS; fewer than "
+                             "2^%u nodes)", psh);
         const int RW = rec_words((int)F);
         // entries of the prefix node of each depth: the indices whose walk
         // reaches depth k, plus those that stop earlier after a final (a

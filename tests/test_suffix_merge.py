@@ -154,3 +154,9 @@ def test_library_merge_flag_needs_compressed_layout():
     with pytest.raises(pfac.PfacError):
         pfac.Table([b"\x01\x02"], 4, layout=pfac.binding.LAYOUT_DENSE, host_only=True,
                    suffix_merge=True)
+
+
+def test_library_merge_with_wide_records_is_refused():
+    pfac = _library()
+    with pytest.raises(pfac.PfacError):
+        pfac.Table([b"\x01\x02\x03"], 4, host_only=True, suffix_merge=True, wide_records=True)
