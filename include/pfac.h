@@ -188,7 +188,14 @@ typedef struct {
                               or 512 (every position: no slice is ever scanned
                               a second time; 8 bytes of workspace per input
                               byte) */
-    uint32_t reserved_rec;
+    uint32_t resolver;     /* who resolves the scan kernel's queues of
+                              survivors: 0 = library choice (the resolver
+                              kernel for plain tries), 1 = the scan kernel's
+                              warps themselves, 2 = the resolver kernel (a
+                              second launch after the scan, which the scan's
+                              warps hand whole queues to while its buffer of
+                              8 entries per slice has room; about 0.27
+                              workspace bytes per input byte) */
 } pfac_match_opts;
 
 typedef struct {

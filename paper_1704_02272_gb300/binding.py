@@ -55,7 +55,7 @@ class MatchOpts(ctypes.Structure):
                 ("ev_emit_begin", ctypes.c_void_p), ("ev_emit_end", ctypes.c_void_p),
                 ("scan_kernel", ctypes.c_uint32), ("reserved_scan", ctypes.c_uint32),
                 ("test_wait_limit_us", ctypes.c_uint32), ("test_withhold_slice", ctypes.c_uint32),
-                ("records_per_slice", ctypes.c_uint32), ("reserved_rec", ctypes.c_uint32)]
+                ("records_per_slice", ctypes.c_uint32), ("resolver", ctypes.c_uint32)]
 
 
 class TableInfo(ctypes.Structure):
@@ -189,7 +189,7 @@ KERNEL_QUEUED, KERNEL_REGISTER, KERNEL_SERIAL = 1, 2, 3
 def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks=0,
           gram_filter=0, prefix_bytes=0, starts_end=0, position_base=0, warps_per_cta=0,
           scan_kernel=0, scan_events=None, emit_events=None, test_wait_limit_us=0,
-          test_withhold_slice=0, records_per_slice=0):
+          test_withhold_slice=0, records_per_slice=0, resolver=0):
     o = MatchOpts()
     o.variant, o.prefix_depth, o.ctas_per_sm = variant, prefix_depth, ctas_per_sm
     o.bitmap_copies, o.child_masks, o.gram_filter = bitmap_copies, child_masks, gram_filter
@@ -197,6 +197,7 @@ def _opts(variant=0, prefix_depth=0, ctas_per_sm=0, bitmap_copies=0, child_masks
     o.warps_per_cta, o.scan_kernel = warps_per_cta, scan_kernel
     o.test_wait_limit_us, o.test_withhold_slice = test_wait_limit_us, test_withhold_slice
     o.records_per_slice = records_per_slice
+    o.resolver = resolver
     if scan_events is not None:  # (begin, end) torch.cuda.Event pair
         o.ev_scan_begin = scan_events[0].cuda_event
         o.ev_scan_end = scan_events[1].cuda_event

@@ -54,7 +54,9 @@ struct WsHeader {
     uint32_t ovf_count;
     uint32_t done_reduce;
     uint32_t done_expand;
-    uint32_t pad[12];
+    uint32_t defer_entries;  // queue entries handed to the resolver kernel
+    uint32_t defer_batches;  // and their batches
+    uint32_t pad[10];
 };
 
 struct MatchParams {
@@ -108,6 +110,12 @@ struct MatchParams {
     // runs out
     uint64_t wait_limit_ns;
     uint32_t withhold_unit;
+    // queues of whole slices handed by the scan kernel to the resolver kernel
+    // (register-staged plans): entries (16 bytes each) and batches {first, n}
+    uint4 *defer;
+    uint32_t defer_cap;
+    uint32_t dbatch_cap;
+    uint2 *dbatch;
 };
 
 constexpr uint32_t UNIT_NONE = 0xFFFFFFFFu;

@@ -667,6 +667,31 @@ __device__ __forceinline__ bool mask_keep(const MatchParams &P, uint32_t x, uint
     return cs < sigma ? ((mr >> child_hash(cs, sigma)) & 1u) != 0 : mr == ones;
 }
 
+// Hands a queue of whole slices (q[0, qn), its last entry ending a slice)
+// to the resolver kernel when the plan has one and its buffers have room:
+// the entries are copied to the next free range of P.defer and a batch
+// {first, n} is recorded (an empty batch when the entries do not fit).
+// Returns true when the queue was handed over; the caller resolves it
+// itself otherwise.
+__device__ __forceinline__ bool defer_queue(const MatchParams &P, const QEntry *q, uint32_t qn,
+                                            uint32_t lane) {
+    if (!P.defer || qn == 0) return false;
+    uint32_t eb = 0, bb = 0;
+    if (lane == 0) {
+        eb = atomicAdd(&P.hdr->defer_entries, qn);
+        bb = atomicAdd(&P.hdr->defer_batches, 1u);
+    }
+    eb = __shfl_sync(0xFFFFFFFFu, eb, 0);
+    bb = __shfl_sync(0xFFFFFFFFu, bb, 0);
+    const bool room = eb + qn <= P.defer_cap && eb + qn >= eb;
+    if (bb < P.dbatch_cap && lane == 0) P.dbatch[bb] = make_uint2(eb, room ? qn : 0u);
+    if (!room || bb >= P.dbatch_cap) return false;
+    for (uint32_t i = lane; i < qn; i += 32)
+        P.defer[chk(P, eb + i, P.defer_cap)] = *reinterpret_cast<const uint4 *>(&q[chk(P, i, QCAP)]);
+    __syncwarp();
+    return true;
+}
+
 // Record-mode flush: resolve the queue, then keep a record (position, fin)
 // for each matched survivor, ranked among its slice's matched survivors (the
 // slice's entries are contiguous in the queue and resolve in one batch).
@@ -1192,8 +1217,10 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const __grid_constant__ Ma
                                            staged, u, lima, limb, general_lims, ustart, rem, Fs, Cs,
                                            Ms, lane);
                     if (ar != AP_FLUSH) break;
-                    // resolve the queue, move the slice's entries to its front
-                    flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
+                    // resolve the queue (or hand it over), move the slice's
+                    // entries to its front
+                    if (!defer_queue(P, A.q, qn, lane))
+                        flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
                     for (uint32_t e0 = 0; e0 < ast.kept; e0 += 32) {
                         const uint32_t e = e0 + lane;
                         QEntry t;
@@ -1232,7 +1259,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanq(const __grid_constant__ Ma
         if (lane == 0) issue(i + QRING);  // every lane's reads of the stage are done
         __syncwarp();
     }
-    if (!failed && !emit) flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
+    if (!failed && !emit && !defer_queue(P, A.q, qn, lane))
+        flush_records<W, VAR>(P, A.q, qn, Fs, Cs, Es, lane);
     if (failed && lane == 0) {
         // wait (bounded) for this warp's copies that may still be in flight:
         // the stages of units i_fail .. i_fail + QRING - 1

@@ -329,10 +329,19 @@ __device__ __noinline__ uint2 r_flush(const MatchParams *P, QEntry *q, uint32_t 
     return make_uint2(carry_unit, carry);
 }
 
+// Empties the warp's queue: a queue of whole slices (whole = its last entry
+// ends a slice, and no slice continues from an earlier batch) goes to the
+// resolver kernel while its buffers have room; otherwise the warp resolves
+// it now.
 template <int W, int VAR>
 __device__ __forceinline__ void r_flush_queue(const MatchParams &P, RWarpArea &A, RQueue &Q,
                                               const uint32_t *Fs, const uint32_t *Cs,
-                                              const uint32_t *Es, uint32_t lane) {
+                                              const uint32_t *Es, uint32_t lane,
+                                              bool whole = true) {
+    if (whole && Q.carry_unit == UNIT_OVF && defer_queue(P, A.q, Q.qn, lane)) {
+        Q.qn = 0;
+        return;
+    }
     const uint2 c = r_flush<W, VAR>(&P, A.q, Q.qn, Fs, Cs, Es, lane, Q.carry_unit, Q.carry);
     Q.carry_unit = c.x;
     Q.carry = c.y;
@@ -391,7 +400,7 @@ __device__ __forceinline__ void r_append(const MatchParams &P, RWarpArea &A, RQu
         done += take;
         if (done == tot) break;
         // the queue is full and the slice goes on: resolve, carrying its ranks
-        r_flush_queue<W, VAR>(P, A, Q, Fs, Cs, Es, lane);
+        r_flush_queue<W, VAR>(P, A, Q, Fs, Cs, Es, lane, false);
     }
 }
 
@@ -632,5 +641,31 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanr(const __grid_constant__ Ma
     if (Q.qn) r_flush_queue<W, VAR>(P, A, Q, Fs, Cs, Es, lane);
 }
 
+
+// The resolver kernel: each warp takes batches the scan kernel handed over (whole slices, in queue order), resolves them with
+// the prefix node's bitmap, counts and entries read through L2 (P has one
+// bitmap copy), and writes their records and counts as the scan kernel would
+// have.
+constexpr int RES_WARPS = 8;
+
+template <int W>
+__global__ void __launch_bounds__(RES_WARPS * 32) k_resolve(const __grid_constant__ MatchParams P) {
+    __shared__ RWarpArea areas[RES_WARPS];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RWarpArea &A = areas[warp];
+    const uint32_t nb0 = *(volatile uint32_t *)&P.hdr->defer_batches;
+    const uint32_t nb = nb0 < P.dbatch_cap ? nb0 : P.dbatch_cap;
+    const uint32_t gw = blockIdx.x * RES_WARPS + warp, gs = gridDim.x * RES_WARPS;
+    for (uint32_t b = gw; b < nb; b += gs) {
+        const uint2 d = P.dbatch[b];
+        if (d.y == 0 || d.y > (uint32_t)QCAP) continue;
+        for (uint32_t i = lane; i < d.y; i += 32)
+            *reinterpret_cast<uint4 *>(&A.q[i]) = P.defer[chk(P, (uint64_t)d.x + i, P.defer_cap)];
+        __syncwarp();
+        uint32_t cu = UNIT_OVF, cc = 0;
+        flush_records_c<W, VAR_F>(P, A.q, d.y, P.F, P.C, nullptr, lane, cu, cc);
+        __syncwarp();
+    }
+}
 
 }  // namespace pfac

@@ -31,6 +31,7 @@ void *scan_kernel_r2_g0_fe(int rep, int nw);
 void *scan_kernel_r2_g1_f(int rep, int nw);
 void *scan_kernel_r2_g1_fe(int rep, int nw);
 
+void *resolve_kernel(int w);
 void *scan_kernel_r8_d0(int rep, int var, int nw);
 void *scan_kernel_r8_d1(int rep, int var, int nw);
 void *scan_kernel_r2_d0(int rep, int var, int nw);
@@ -316,6 +317,8 @@ struct Plan {
     size_t smem;
     bool queued;
     int kind;           // SCAN_QUEUED or SCAN_REGISTER (compressed layout)
+    bool defer;         // the scan hands whole-slice queues to the resolver kernel
+    void *kernel_res;
     // emit pass of a register-staged plan: the queued kernel with tables of
     // its own (one bitmap copy, entries through L2)
     size_t smem_emit;
@@ -325,9 +328,13 @@ struct Plan {
 enum { SCAN_QUEUED = 1, SCAN_REGISTER = 2, SCAN_SERIAL = 3 };
 
 struct WsLayout {
-    uint64_t hdr, tile_m, tile_k, key_off, chunk, ovf, recs, bounds, total;
-    uint32_t n_tiles, n_chunks;
+    uint64_t hdr, tile_m, tile_k, key_off, chunk, ovf, recs, bounds, defer, dbatch, total;
+    uint32_t n_tiles, n_chunks, defer_cap, dbatch_cap;
 };
+
+// entries per slice the resolver kernel's buffer holds (more go to the
+// scan kernel's own resolution)
+constexpr uint32_t DEFER_PER_UNIT = 8;
 
 static inline uint64_t al256(uint64_t x) { return (x + 255) & ~255ull; }
 
@@ -353,6 +360,13 @@ static WsLayout ws_layout(uint64_t n_bytes, uint32_t n_seg, const Plan &pl) {
     // segment data: per-tile lists (tile-synchronous kernel) or the first
     // offset index per unit (queued kernel)
     L.bounds = put(n_seg > 1 ? (pl.queued ? nt * 4 : nt * SEGW * 4) : 0);
+    // register-staged plans: the queues handed to the resolver kernel (at
+    // most one batch per slice, plus each warp's last)
+    const uint64_t dcap = pl.defer ? std::min<uint64_t>(nt * DEFER_PER_UNIT, 0xFFFFFF00ull) : 0;
+    L.defer_cap = (uint32_t)dcap;
+    L.dbatch_cap = pl.defer ? (uint32_t)std::min<uint64_t>(nt + 4096, 0xFFFFFF00ull) : 0u;
+    L.defer = put(dcap * 16);
+    L.dbatch = put((uint64_t)L.dbatch_cap * 8);
     L.total = o;
     return L;
 }
@@ -501,6 +515,8 @@ static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks,
     pl->nw = nw;
     pl->kind = SCAN_REGISTER;
     pl->kernel = scan_kernel_r(T.bps, T.W, b_rep, b_gram, b_var, (int)nw);
+    pl->defer = true;
+    pl->kernel_res = resolve_kernel((int)T.W);
     pl->smem = r_smem((uint64_t)pl->tbl_words + pl->tbl_c_words + pl->tbl_e_words +
                       pl->tbl_m_words + pl->tbl_g_words, nw);
     // the emit pass: the queued kernel, one bitmap copy, entries through L2,
@@ -512,7 +528,7 @@ static int make_plan_r(const pfac_table *t, uint32_t k, int var, uint32_t masks,
     pl->unit_shift = SLICE_SHIFT;
     pl->unit_cap = SCAP;
     pl->queued = true;
-    if (!pl->kernel || !pl->kernel_emit)
+    if (!pl->kernel || !pl->kernel_emit || !pl->kernel_res)
         return set_error(PFAC_EINVAL, "pfac_match: no register-staged kernel for this table");
     return PFAC_OK;
 }
@@ -609,6 +625,11 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                                      : (t->match_density * SLICE > 8.0 ? (uint32_t)SLICE : SCAP));
     if (recs != (uint32_t)SCAP && recs != (uint32_t)SLICE)
         return set_error(PFAC_EINVAL, "pfac_match: records_per_slice %u (32 or 512)", recs);
+    const uint32_t resolver = opts ? opts->resolver : 0u;
+    if (resolver > 2) return set_error(PFAC_EINVAL, "pfac_match: resolver %u", resolver);
+    if (resolver == 2 && T.dag)
+        return set_error(PFAC_EINVAL, "pfac_match: a merged trie resolves its queues in the scan");
+    const bool defer = resolver != 1 && !T.dag;
 
     // ---- the register-staged kernel (8-bit symbols): on request, or by
     // default when the caller asks for nothing only the queued kernel has
@@ -627,6 +648,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                                  : (use_tuned && t->tuned_nw ? t->tuned_nw : (uint32_t)RNW);
         const int rc = make_plan_r(t, k, var, masks, gram, want, rnw, pl);
         pl->unit_cap = recs;
+        pl->defer = defer;
         if (rc == PFAC_OK || want_kind == SCAN_REGISTER) return rc;
         clear_error();
         memset(pl, 0, sizeof(*pl));
@@ -772,6 +794,10 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
         return set_error(PFAC_EINVAL, "pfac_match: %u warps do not fit next to the tables", nwant);
     pl->nw = nwant;
     pl->kind = SCAN_QUEUED;
+    // the resolver kernel takes the plain tries' queues (the merged trie's
+    // walk stays in its own instance)
+    pl->defer = defer;
+    pl->kernel_res = pl->defer ? resolve_kernel((int)T.W) : nullptr;
     const int kvar = T.dag ? (VAR_F | VAR_MERGED) : var;
     pl->kernel = scan_kernel_for(T.bps, kvar, 0, (int)nwant, (int)T.W);
     pl->kernel_emit = scan_kernel_for(T.bps, kvar, 1, (int)nwant, (int)T.W);
@@ -779,7 +805,7 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
     pl->unit_shift = SLICE_SHIFT;
     pl->unit_cap = recs;
     pl->queued = true;
-    if (!pl->kernel || !pl->kernel_emit)
+    if (!pl->kernel || !pl->kernel_emit || (pl->defer && !pl->kernel_res))
         return set_error(PFAC_EINVAL, "pfac_match: no kernel for this table");
     return PFAC_OK;
 }
@@ -980,6 +1006,12 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
     P.wait_limit_ns = opts && opts->test_wait_limit_us ? (uint64_t)opts->test_wait_limit_us * 1000
                                                        : WAIT_LIMIT_NS;
     P.withhold_unit = opts && opts->test_withhold_slice ? opts->test_withhold_slice - 1 : UNIT_NONE;
+    if (pl.defer) {
+        P.defer = (uint4 *)(W + L.defer);
+        P.defer_cap = L.defer_cap;
+        P.dbatch = (uint2 *)(W + L.dbatch);
+        P.dbatch_cap = L.dbatch_cap;
+    }
     const uint32_t nthreads = pl.queued ? pl.nw * 32 : NTHREADS;
     // units a CTA takes in one round: the register-staged kernel's warps
     // take two slices each
@@ -1004,6 +1036,16 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
         int emit = 0;
         void *args[] = {&P, &emit};
         e = cudaLaunchKernel(pl.kernel, dim3(grid), dim3(nthreads), args, pl.smem, st);
+    }
+    if (e == cudaSuccess && P.n_tiles && pl.defer) {
+        // the handed-over queues: prefix bitmap, counts and entries through
+        // L2 (one bitmap copy)
+        MatchParams P3 = P;
+        P3.rep_log2 = 0;
+        P3.tbl_e_words = 0;
+        P3.tbl_m_words = 0;
+        void *args[] = {&P3};
+        e = cudaLaunchKernel(pl.kernel_res, dim3(nsm * 4), dim3(RES_WARPS * 32), args, 0, st);
     }
     if (e == cudaSuccess && opts && opts->ev_scan_end)
         e = cudaEventRecord((cudaEvent_t)opts->ev_scan_end, st);

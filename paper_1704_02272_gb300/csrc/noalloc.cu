@@ -105,13 +105,16 @@ extern "C" int pfac_match_noalloc(const pfac_table *t, const uint8_t *d_input, u
     uint64_t need = 0;
     rc = pfac_workspace_bytes(t, n_bytes, n_segments, opts, &need);
     if (rc) return rc;
-    // a library choice of record space for every position (8 bytes of scratch
-    // per input byte) gives way to the smaller record space when only that fits
+    // library choices that take more scratch (a record per position, 8 bytes
+    // per input byte; the resolver kernel's buffer) give way to the smaller
+    // record space and the scan's own resolution when only those fit
     pfac_match_opts o32;
-    if (need > (uint64_t)PFAC_NOALLOC_SCRATCH_BYTES && !(opts && opts->records_per_slice)) {
+    if (need > (uint64_t)PFAC_NOALLOC_SCRATCH_BYTES &&
+        !(opts && opts->records_per_slice && opts->resolver)) {
         if (opts) o32 = *opts;
         else memset(&o32, 0, sizeof o32);
-        o32.records_per_slice = 32;
+        if (!o32.records_per_slice) o32.records_per_slice = 32;
+        if (!o32.resolver) o32.resolver = 1;
         uint64_t need32 = 0;
         if (pfac_workspace_bytes(t, n_bytes, n_segments, &o32, &need32) == PFAC_OK &&
             need32 <= (uint64_t)PFAC_NOALLOC_SCRATCH_BYTES) {

@@ -395,3 +395,34 @@ def test_dense_matches_one_pass():
                 keys = pfac.match(t, tt, sg, records_per_slice=recs)
                 torch.cuda.synchronize()
                 assert_same(keys_np(keys), ref, f"dense sigma {sigma} records {recs}")
+
+
+@pytest.mark.parametrize("seed,sigma,n,lo,hi,N,S,plants", [
+    (601, 4, 3000, 8, 40, 1 << 20, 1, 3000),     # DNA-like: queues of whole slices
+    (602, 4, 400, 2, 6, 600_000, 9, 500),        # short patterns: buffer full, partly in place
+    (603, 256, 2000, 2, 10, 1 << 20, 40, 2000),
+    (604, 20, 800, 1, 6, 400_003, 3, 800),
+])
+def test_resolver_kernel_same_keys(seed, sigma, n, lo, hi, N, S, plants):
+    # the scan kernel's own resolution (resolver=1) and the resolver kernel
+    # (resolver=2, with the in-place fallback when its buffer is full) give
+    # the oracle's keys through both scan kernels
+    w = workloads.tiny_case(seed, sigma, n, lo, hi, N, n_segments=S, n_plants=plants)
+    ref = oracle_keys(w)
+    text, seg = to_device(w)
+    ran = 0
+    with pfac.Table(w.patterns, w.sigma) as t:
+        for kern in (pfac.binding.KERNEL_QUEUED, pfac.binding.KERNEL_REGISTER):
+            for res in (1, 2):
+                for recs in (32, 512):
+                    opt = dict(scan_kernel=kern, resolver=res, records_per_slice=recs)
+                    try:
+                        pfac.plan(t, **opt)
+                    except pfac.PfacError as e:  # no register-staged kernel for this alphabet
+                        assert e.status == -1, str(e)
+                        continue
+                    keys = pfac.match(t, text, seg, **opt)
+                    torch.cuda.synchronize()
+                    assert_same(keys_np(keys), ref, f"{opt}")
+                    ran += 1
+    assert ran >= 4

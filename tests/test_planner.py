@@ -223,3 +223,16 @@ def test_default_prefix_depth_rule(seed, sigma, n, lo, hi):
     kcap = max([k for k in ents if 4 * ents[k] <= budget] or [kfloor])
     want = next((k for k in range(kfloor, kcap + 1) if ents[k] * 256 <= (1 << (k * bps))), kcap)
     assert info["prefix_depth"] == want, (ents, budget)
+
+
+def test_resolver_option_checked():
+    pats = workloads.uniform_patterns(np.random.RandomState(3), 100, 4, 4, 12)
+    with pfac.Table(pats, 4, host_only=True) as t:
+        for res in (0, 1, 2):
+            pfac.plan(t, resolver=res)
+        with pytest.raises(pfac.PfacError):
+            pfac.plan(t, resolver=3)
+    with pfac.Table(pats, 4, host_only=True, suffix_merge=True) as t:
+        pfac.plan(t, resolver=1)
+        with pytest.raises(pfac.PfacError):
+            pfac.plan(t, resolver=2)
