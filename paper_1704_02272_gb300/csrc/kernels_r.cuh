@@ -646,10 +646,15 @@ __global__ void __launch_bounds__(NW * 32, 1) k_scanr(const __grid_constant__ Ma
 // the prefix node's bitmap, counts and entries read through L2 (P has one
 // bitmap copy), and writes their records and counts as the scan kernel would
 // have.
+// The batches are chains of dependent L2 loads: occupancy (RES_CTAS CTAs of
+// RES_WARPS warps on every SM, at most 64 registers a thread) is what
+// hides them.
 constexpr int RES_WARPS = 8;
+constexpr int RES_CTAS = 4;
 
 template <int W>
-__global__ void __launch_bounds__(RES_WARPS * 32) k_resolve(const __grid_constant__ MatchParams P) {
+__global__ void __launch_bounds__(RES_WARPS * 32, RES_CTAS)
+    k_resolve(const __grid_constant__ MatchParams P) {
     __shared__ RWarpArea areas[RES_WARPS];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     RWarpArea &A = areas[warp];

@@ -1045,7 +1045,7 @@ extern "C" int pfac_match_async(const pfac_table *t, const uint8_t *d_input, uin
         P3.tbl_e_words = 0;
         P3.tbl_m_words = 0;
         void *args[] = {&P3};
-        e = cudaLaunchKernel(pl.kernel_res, dim3(nsm * 4), dim3(RES_WARPS * 32), args, 0, st);
+        e = cudaLaunchKernel(pl.kernel_res, dim3(nsm * RES_CTAS), dim3(RES_WARPS * 32), args, 0, st);
     }
     if (e == cudaSuccess && opts && opts->ev_scan_end)
         e = cudaEventRecord((cudaEvent_t)opts->ev_scan_end, st);
