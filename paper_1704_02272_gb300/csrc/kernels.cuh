@@ -48,6 +48,9 @@ enum { VAR_F = 1, VAR_FE = 2, VAR_DENSE = 4 };
 // kernel instances for merged tries (reduction step 2): VAR_F | VAR_MERGED;
 // the others leave the merged-trie slow path out
 constexpr int VAR_MERGED = 8;
+// the resolver kernel's instances: VAR_F | VAR_RES (fewer walks per lane, so
+// that more warps fit per SM)
+constexpr int VAR_RES = 16;
 
 struct WsHeader {
     int32_t status;

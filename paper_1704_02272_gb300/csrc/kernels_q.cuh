@@ -45,6 +45,10 @@ constexpr int QCAP = 128;                // queue entries per warp (and most sur
 constexpr int QU = QCAP / 32;            // queue entries per lane per batch
 // walks a lane advances together while resolving: fewer for 48-byte records
 __host__ __device__ constexpr int walks_per_lane(int W) { return W == 8 ? 2 : 4; }
+// walks per lane of one resolve pass: fewer in the resolver kernel
+__host__ __device__ constexpr int pass_walks(int W, int VAR) {
+    return (VAR & VAR_RES) ? (W == 8 ? 1 : 2) : walks_per_lane(W);
+}
 constexpr uint32_t ROOT_X = 0xFFFFFFFFu; // queue entry: walk from the root
 constexpr uint32_t DAG_PENDING = 0x80000000u;  // resolved entry: merged-trie walk still to run
 constexpr uint32_t LAST_FLAG = 0x80000000u;  // queue entry: the slice's last
@@ -236,7 +240,7 @@ __device__ __forceinline__ void resolve_pass(const MatchParams &P, QEntry *q, ui
                                              uint32_t e0, const uint32_t *Fs, const uint32_t *Cs,
                                              const uint32_t *Es, uint32_t *tail,
                                              uint32_t lane) {
-    constexpr int QU = walks_per_lane(W);
+    constexpr int QU = pass_walks(W, VAR);
     constexpr int LOCK_ROUNDS = 3;
     constexpr bool DAG = (VAR & VAR_MERGED) != 0;
     const uint32_t sigma = P.T.sigma, k = P.k, rep = P.rep_log2;
@@ -443,7 +447,7 @@ template <int W, int VAR>
 __device__ __forceinline__ void resolve_batch_inl(const MatchParams &P, QEntry *q, uint32_t n,
                                                   const uint32_t *Fs, const uint32_t *Cs,
                                                   const uint32_t *Es, uint32_t lane) {
-    constexpr uint32_t per = 32u * walks_per_lane(W);
+    constexpr uint32_t per = 32u * pass_walks(W, VAR);
     // the tail list lives behind the queue entries of this warp
     uint32_t *tail = reinterpret_cast<uint32_t *>(q + QCAP);
     for (uint32_t e0 = 0; e0 < n; e0 += per)

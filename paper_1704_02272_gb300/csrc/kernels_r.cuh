@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(RES_WARPS * 32, RES_CTAS)
             *reinterpret_cast<uint4 *>(&A.q[i]) = P.defer[chk(P, (uint64_t)d.x + i, P.defer_cap)];
         __syncwarp();
         uint32_t cu = UNIT_OVF, cc = 0;
-        flush_records_c<W, VAR_F>(P, A.q, d.y, P.F, P.C, nullptr, lane, cu, cc);
+        flush_records_c<W, VAR_F | VAR_RES>(P, A.q, d.y, P.F, P.C, nullptr, lane, cu, cc);
         __syncwarp();
     }
 }
