@@ -402,10 +402,13 @@ void pfac_match_host_release(void);
  *
  * Limits and rules:
  *   - the scratch an input needs grows with its size (about 0.55 bytes per
- *     input byte, pfac_workspace_bytes gives the exact figure); inputs that
- *     need more than PFAC_NOALLOC_SCRATCH_BYTES (roughly 58 MiB of input) are
- *     rejected with PFAC_EINVAL and a message naming both sizes, before any
- *     device work;
+ *     input byte, pfac_workspace_bytes gives the exact figure); where the
+ *     library's own choices (512 records per slice, the resolver kernel's
+ *     buffer) would not fit, the call takes 32 records per slice and the scan
+ *     kernel's own resolution instead (unless the caller set both); inputs
+ *     that need more than PFAC_NOALLOC_SCRATCH_BYTES even so (roughly 58 MiB
+ *     of input) are rejected with PFAC_EINVAL and a message naming both
+ *     sizes, before any device work;
  *   - the first call on a device looks up that device's copy of the array
  *     (cudaGetSymbolAddress, with the device current); make that first call
  *     before any stream capture.  The address is kept per device and per
