@@ -282,7 +282,8 @@ typedef struct {
     uint32_t warps_per_cta;  /* warps per CTA of the scan kernel (0: uncompressed) */
     uint32_t scan_kernel;    /* 1 = queued, 2 = register-staged, 3 = thread-serial */
     uint32_t records_per_slice; /* 32 or 512 (compressed layout) */
-    uint32_t reserved;
+    uint32_t resolver;       /* 1 = the scan kernel resolves its queues, 2 = the
+                                resolver kernel does (0: thread-serial) */
 } pfac_plan_info;
 int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts, pfac_plan_info *out);
 
@@ -451,6 +452,7 @@ typedef struct {
     uint32_t warps_per_cta;
     uint32_t scan_kernel;  /* 1 = queued, 2 = register-staged */
     uint32_t records_per_slice;
+    uint32_t resolver;     /* as pfac_match_opts.resolver (0: the library's) */
 } pfac_tune_result;
 
 int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,

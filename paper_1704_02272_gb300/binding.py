@@ -81,7 +81,8 @@ class TuneResult(ctypes.Structure):
                 ("scan_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
                 ("from_cache", ctypes.c_int), ("gram_filter", ctypes.c_uint32),
                 ("prefix_bytes", ctypes.c_uint32), ("warps_per_cta", ctypes.c_uint32),
-                ("scan_kernel", ctypes.c_uint32), ("records_per_slice", ctypes.c_uint32)]
+                ("scan_kernel", ctypes.c_uint32), ("records_per_slice", ctypes.c_uint32),
+                ("resolver", ctypes.c_uint32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -90,7 +91,7 @@ class PlanInfo(ctypes.Structure):
                 ("gram_filter", ctypes.c_uint32), ("gram_bits", ctypes.c_uint32),
                 ("smem_bytes", ctypes.c_uint32), ("prefix_bytes", ctypes.c_uint32),
                 ("warps_per_cta", ctypes.c_uint32), ("scan_kernel", ctypes.c_uint32),
-                ("records_per_slice", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("records_per_slice", ctypes.c_uint32), ("resolver", ctypes.c_uint32)]
 
 
 class ServerOpts(ctypes.Structure):

@@ -25,6 +25,7 @@ struct pfac_table {
     uint32_t tuned_nw = 0;
     uint32_t tuned_kernel = 0;
     uint32_t tuned_records = 0;
+    uint32_t tuned_resolver = 0;
     double match_density = 0.0;  // expected matches per position of uniform text
 };
 

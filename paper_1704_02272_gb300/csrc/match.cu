@@ -625,11 +625,17 @@ static int make_plan(const pfac_table *t, const pfac_match_opts *opts, Plan *pl)
                                      : (t->match_density * SLICE > 8.0 ? (uint32_t)SLICE : SCAP));
     if (recs != (uint32_t)SCAP && recs != (uint32_t)SLICE)
         return set_error(PFAC_EINVAL, "pfac_match: records_per_slice %u (32 or 512)", recs);
-    const uint32_t resolver = opts ? opts->resolver : 0u;
+    const uint32_t resolver = opts && opts->resolver
+                                  ? opts->resolver
+                                  : (use_tuned ? t->tuned_resolver : 0u);
     if (resolver > 2) return set_error(PFAC_EINVAL, "pfac_match: resolver %u", resolver);
     if (resolver == 2 && T.dag)
         return set_error(PFAC_EINVAL, "pfac_match: a merged trie resolves its queues in the scan");
-    const bool defer = resolver != 1 && !T.dag;
+    // by default the resolver kernel takes the queues where at least four
+    // windows per slice pass the prefix bitmap (uniform text): with fewer,
+    // its launch costs more than the scan saves
+    const bool defer = !T.dag && (resolver == 2 ||
+                                  (resolver == 0 && (double)ew * SLICE >= 4.0 * (double)ent));
 
     // ---- the register-staged kernel (8-bit symbols): on request, or by
     // default when the caller asks for nothing only the queued kernel has
@@ -908,6 +914,7 @@ extern "C" int pfac_match_plan(const pfac_table *t, const pfac_match_opts *opts,
     out->warps_per_cta = pl.nw;
     out->scan_kernel = (uint32_t)pl.kind;
     out->records_per_slice = pl.unit_cap;
+    out->resolver = pl.kind == SCAN_SERIAL ? 0u : (pl.defer ? 2u : 1u);
     return PFAC_OK;
 }
 

@@ -41,25 +41,26 @@ std::string cache_key(const pfac_table *t, uint64_t n_bytes, uint32_t n_segments
 }
 
 // A cache line: key, variant, depth, copies, masks, gram filter, prefix
-// bytes, warps per CTA, scan kernel, records per slice, time.  Lines without
-// the scan kernel (written before the register-staged kernel existed) name
-// the queued one; lines without the records leave them to the library.
+// bytes, warps per CTA, scan kernel, records per slice, resolver, time.
+// Lines without the scan kernel (written before the register-staged kernel
+// existed) name the queued one; lines without the records or the resolver
+// leave them to the library.
 bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_t *k,
                   uint32_t *c, uint32_t *mk, uint32_t *gf, uint32_t *pb, uint32_t *nw,
-                  uint32_t *kind, uint32_t *recs, float *ms) {
+                  uint32_t *kind, uint32_t *recs, uint32_t *resv, float *ms) {
     FILE *f = fopen(path, "r");
     if (!f) return false;
     char line[512];
     bool found = false;
     while (fgets(line, sizeof line, f)) {
-        // whitespace-separated tokens: the key, then 8 or 9 fields
-        char *tok[12], *save = nullptr;
+        // whitespace-separated tokens: the key, 7 to 10 fields, the time
+        char *tok[13], *save = nullptr;
         int nt = 0;
-        for (char *p = strtok_r(line, " \t\r\n", &save); p && nt < 12;
+        for (char *p = strtok_r(line, " \t\r\n", &save); p && nt < 13;
              p = strtok_r(nullptr, " \t\r\n", &save))
             tok[nt++] = p;
-        if (nt < 9 || nt > 11 || key != tok[0]) continue;
-        uint32_t u[9];
+        if (nt < 9 || nt > 12 || key != tok[0]) continue;
+        uint32_t u[10];
         bool ok = true;
         for (int i = 0; i < nt - 2; i++) {
             char *end = nullptr;
@@ -72,7 +73,8 @@ bool cache_lookup(const char *path, const std::string &key, uint32_t *v, uint32_
         if (!ok || !end || *end) continue;
         {
             const uint32_t q = nt >= 10 ? u[7] : 1u;
-            *recs = nt == 11 ? u[8] : 0u;
+            *recs = nt >= 11 ? u[8] : 0u;
+            *resv = nt == 12 ? u[9] : 0u;
             *v = u[0];
             *k = u[1];
             *c = u[2];
@@ -100,16 +102,19 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     memset(&res, 0, sizeof res);
     const std::string key = cache_key(t, n_bytes, n_segments);
     if (cache_path) {
-        uint32_t v, k, c, mk, gf, pb, nw, kind, rp;
+        uint32_t v, k, c, mk, gf, pb, nw, kind, rp, rsv;
         float ms;
-        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &nw, &kind, &rp, &ms) &&
+        if (cache_lookup(cache_path, key, &v, &k, &c, &mk, &gf, &pb, &nw, &kind, &rp, &rsv, &ms) &&
+            rsv <= 2 &&
             k >= t->kmin && k <= t->kmax && (gf != 2 || t->dev.g_len) &&
             (pb != 2 || t->dev.B[k])) {
             t->tuned_bytes = pb;
             t->tuned_nw = nw;
             t->tuned_kernel = kind;
             t->tuned_records = rp;
+            t->tuned_resolver = rsv;
             res.records_per_slice = rp;
+            res.resolver = rsv;
             res.prefix_bytes = pb;
             res.warps_per_cta = nw;
             res.scan_kernel = kind;
@@ -147,6 +152,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     t->tuned_nw = 0;
     t->tuned_kernel = 0;
     t->tuned_records = 0;
+    t->tuned_resolver = 0;
     if (!t->d_blob) return set_error(PFAC_EINVAL, "pfac_autotune: table was built host-only");
     {
         const int drc = check_table_device(t, cuda_stream, "pfac_autotune");
@@ -157,6 +163,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         uint32_t var, k, copies, masks, gram, bytes, nw, kernel;
         float ms;
         uint32_t recs = 0;  // records per slice (0: the library's choice)
+        uint32_t resolver = 0;  // who resolves the queues (0: the library's choice)
     };
     auto opts_of = [](const Cand &c) {
         pfac_match_opts o;
@@ -170,6 +177,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         o.warps_per_cta = c.nw;
         o.scan_kernel = c.kernel;
         o.records_per_slice = c.recs;
+        o.resolver = c.resolver;
         return o;
     };
     std::vector<Cand> cands;
@@ -278,6 +286,17 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
             if (time_cand(alt)) timed.push_back(alt);
         }
         clear_error();
+        // the best of those with the other resolution of the queues
+        Cand best1 = best0;
+        for (const Cand &c : timed)
+            if (c.var && c.ms < best1.ms) best1 = c;
+        o = opts_of(best1);
+        if (best1.var && pfac_match_plan(t, &o, &pi) == PFAC_OK && pi.resolver) {
+            Cand alt = best1;
+            alt.resolver = pi.resolver == 2 ? 1u : 2u;
+            if (time_cand(alt)) timed.push_back(alt);
+        }
+        clear_error();
     }
     int32_t h_st = 0;
     e = cudaMemcpyAsync(&h_st, d_st, 4, cudaMemcpyDeviceToHost, st);
@@ -307,6 +326,7 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
         t->tuned_nw = best.nw;
         t->tuned_kernel = best.kernel;
         t->tuned_records = best.recs;
+        t->tuned_resolver = best.resolver;
     }
     res.variant = best.var;
     res.prefix_depth = best.k;
@@ -317,13 +337,14 @@ extern "C" int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_
     res.warps_per_cta = best.nw;
     res.scan_kernel = best.kernel;
     res.records_per_slice = best.recs;
+    res.resolver = best.resolver;
     res.scan_ms = best.ms;
     if (cache_path && best.var) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s %u %u %u %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k,
+            fprintf(f, "%s %u %u %u %u %u %u %u %u %u %u %.6f\n", key.c_str(), best.var, best.k,
                     best.copies, best.masks, best.gram, best.bytes, best.nw, best.kernel,
-                    best.recs, best.ms);
+                    best.recs, best.resolver, best.ms);
             fclose(f);
         }
     }

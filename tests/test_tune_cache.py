@@ -60,3 +60,16 @@ def test_cached_line_without_a_plan_is_ignored(tmp_path, line):
         with pytest.raises(pfac.PfacError):
             pfac.autotune(t, text, seg, cache_path=str(path), stream=0)
         assert pfac.plan(t) == default
+
+
+def test_cached_resolver_is_applied(tmp_path):
+    # a line with the records per slice and the resolver (12 tokens)
+    w = workloads.config4(256, 1000, n_bytes=1 << 12)
+    with pfac.Table(w.patterns, w.sigma, host_only=True) as t:
+        text, seg = sample()
+        path = tmp_path / "tune.txt"
+        path.write_text(f"{cache_key(t, text.numel(), 1)} 1 2 1 1 2 1 16 1 32 1 0.5\n")
+        r = pfac.autotune(t, text, seg, cache_path=str(path), stream=0)
+        assert r["from_cache"] == 1 and r["resolver"] == 1 and r["records_per_slice"] == 32
+        p = pfac.plan(t)
+        assert (p["scan_kernel"], p["records_per_slice"], p["resolver"]) == (1, 32, 1)
