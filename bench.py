@@ -651,6 +651,11 @@ def run_ours(args):
         extra["serving"] = serving_levels(args, [100.0], 2.0, 30, 2000, verbose=False)[0]
 
     roofline = cell.pop("roofline")
+    # this library's launches per step: the five of every call, the resolver
+    # kernel where the plan hands queues to it, the segment pass for several
+    # segments
+    per_step = SCAN_KERNELS_PER_STEP + (1 if cell["scan_plan"].get("resolver") == 2 else 0) + \
+        (1 if S > 1 else 0)
     line = {
         "metric": METRIC,
         "value": round(value, 3), "unit": "Gbps", "n_gpus": world, "steps": K, "warmup": W,
@@ -673,8 +678,7 @@ def run_ours(args):
         "build_s": cell["build_s"],
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": (SCAN_KERNELS_PER_STEP + (1 if cell["scan_plan"].get("resolver") == 2 else 0)) * K
-                        + (K if S > 1 else 0),
+        "gpu_launches": per_step * K,
         "clocks": clk,
         "wall_s_timed": cell["wall_s_timed"],
     }
