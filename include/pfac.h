@@ -63,7 +63,10 @@ typedef enum {
     PFAC_ENOSPC = -5,   /* output capacity too small; count reported */
     PFAC_ECUDA = -6,    /* a CUDA runtime call failed */
     PFAC_ETIMEOUT = -7, /* a bounded device wait gave up */
-    PFAC_EDEVICE = -8   /* a device-side consistency check failed */
+    PFAC_EDEVICE = -8,  /* a device-side consistency check failed */
+    PFAC_EIO = -9,      /* a table file could not be opened, read or written */
+    PFAC_EFORMAT = -10  /* not a table file of this format, or its checksum or
+                           structure does not hold */
 } pfac_status;
 
 typedef enum {
@@ -501,6 +504,42 @@ void pfac_server_destroy(pfac_server *s);
 
 /* pfac_table_info - statistics of a built table (host call, no device work). */
 int pfac_table_info(const pfac_table *t, pfac_table_info_t *out);
+
+/*
+ * pfac_table_save / pfac_table_load - checkpoint and resume of a built
+ * table.  Library extension: the paper builds the compressed table once per
+ * pattern set on the host and then only reads it (Section 3.1); these calls
+ * let a restarted process (a serving loop, a second job) take the finished
+ * table from a file instead of building it again, and let a machine without
+ * a GPU build a table (PFAC_BUILD_HOST_ONLY) that a GPU machine loads.
+ *
+ * pfac_table_save writes t to path: a 48-byte header (magic "PFACTBL", the
+ * format version, the sizes of the library's table structures, the blob's
+ * bytes, a checksum), the table's description with every device pointer
+ * stored as an offset into the blob, then the blob as it sits on the device
+ * (read back with a synchronous copy from the table's device; host-only
+ * tables write the host copy they keep).  The file is written under a
+ * temporary name in the same directory and renamed over path, so a reader
+ * never sees half a file.  Tuned defaults (pfac_autotune) are saved with
+ * the table.  Errors: PFAC_EINVAL (NULL argument), PFAC_EIO, PFAC_ENOMEM,
+ * PFAC_ECUDA.
+ *
+ *   pfac_table_load reads such a file and uploads the blob to the current
+ *   device on cuda_stream (returning after the upload completed), or keeps
+ *   it on the host when flags holds PFAC_BUILD_HOST_ONLY (the only flag
+ *   accepted).  The result is the table that was saved: the same
+ *   pfac_table_info, the same keys from every match call.  Checks before
+ *   any allocation: the header, the checksum over description and blob
+ *   (FNV-1a over 64-bit words), every field's range and every section's
+ *   extent within the blob.  The contents of a section (child numbers,
+ *   entries) are not checked against each other: load only files that
+ *   pfac_table_save wrote.  The format holds little-endian integers and the
+ *   structure sizes of this library version; a file from another version is
+ *   PFAC_EFORMAT.  Errors: PFAC_EINVAL (NULL argument, unknown flag),
+ *   PFAC_EIO, PFAC_EFORMAT, PFAC_ENOMEM, PFAC_ECUDA.
+ */
+int pfac_table_save(const pfac_table *t, const char *path);
+int pfac_table_load(const char *path, uint32_t flags, void *cuda_stream, pfac_table **out);
 
 /* pfac_table_free - releases the table's host and device memory.  The caller
  * must make sure no device work that uses the table is still pending. */

@@ -25,7 +25,7 @@ VARIANT_DEFAULT, VARIANT_FILTER, VARIANT_DSMEM = 0, 1, 2  # DSMEM: entries in sh
 
 STATUS = {0: "PFAC_OK", -1: "PFAC_EINVAL", -2: "PFAC_EDUP", -3: "PFAC_ESYMBOL",
           -4: "PFAC_ENOMEM", -5: "PFAC_ENOSPC", -6: "PFAC_ECUDA", -7: "PFAC_ETIMEOUT",
-          -8: "PFAC_EDEVICE"}
+          -8: "PFAC_EDEVICE", -9: "PFAC_EIO", -10: "PFAC_EFORMAT"}
 
 
 class PfacError(RuntimeError):
@@ -155,6 +155,10 @@ def _load():
     lib.pfac_server_destroy.argtypes = [vp]
     lib.pfac_table_info.restype = ctypes.c_int
     lib.pfac_table_info.argtypes = [vp, ctypes.POINTER(TableInfo)]
+    lib.pfac_table_save.restype = ctypes.c_int
+    lib.pfac_table_save.argtypes = [vp, ctypes.c_char_p]
+    lib.pfac_table_load.restype = ctypes.c_int
+    lib.pfac_table_load.argtypes = [ctypes.c_char_p, u32, vp, ctypes.POINTER(vp)]
     lib.pfac_table_free.restype = None
     lib.pfac_table_free.argtypes = [vp]
     lib.pfac_status_str.restype = ctypes.c_char_p
@@ -238,6 +242,24 @@ class Table:
         self._h = h
         self.alphabet_size = alphabet_size
         self.layout = layout
+
+    @classmethod
+    def load(cls, path, stream=None, host_only: bool = False) -> "Table":
+        """pfac_table_load: the table a pfac_table_save wrote to path, uploaded
+        to the current device (or kept on the host with host_only)."""
+        h = ctypes.c_void_p()
+        st = 0 if host_only else _stream(stream)
+        _check(LIB.pfac_table_load(os.fsencode(path), BUILD_HOST_ONLY if host_only else 0,
+                                   ctypes.c_void_p(st), ctypes.byref(h)))
+        t = cls.__new__(cls)
+        t._h = h
+        i = t.info()
+        t.alphabet_size, t.layout = i["alphabet_size"], i["layout"]
+        return t
+
+    def save(self, path) -> None:
+        """pfac_table_save: writes the table (and its tuned defaults) to path."""
+        _check(LIB.pfac_table_save(self.handle, os.fsencode(path)))
 
     @property
     def handle(self):

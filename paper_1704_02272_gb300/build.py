@@ -32,7 +32,7 @@ def nvcc() -> str:
 
 def sources():
     srcs = ["builder.cpp", "tune.cpp", "serve.cpp", "host.cpp", "match.cu", "noalloc.cu",
-            "verify.cu", "resolve.cu", "scan_dense.cu"] + [f"scan_bps{i}.cu" for i in range(1, 9)] + \
+            "verify.cu", "resolve.cu", "scan_dense.cu", "table_io.cpp"] + [f"scan_bps{i}.cu" for i in range(1, 9)] + \
         [f"scan_r{b}_{g}.cu" for b in (8, 2) for g in ("g0_f", "g0_fe", "g1_f", "g1_fe", "d0", "d1")]
     return [os.path.join(CSRC, s) for s in srcs]
 

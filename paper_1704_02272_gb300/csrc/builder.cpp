@@ -822,7 +822,8 @@ extern "C" int pfac_build(const uint8_t *const *patterns, const uint32_t *length
             }
         }
         t->blob_bytes = blob;
-        uint8_t *B = (uint8_t *)t->d_blob;
+        if (host_only) t->h_blob = std::move(host);
+        uint8_t *B = host_only ? t->h_blob.data() : (uint8_t *)t->d_blob;
         DevTable &dv = t->dev;
         memset(&dv, 0, sizeof(dv));
         dv.sigma = sigma;
@@ -940,6 +941,8 @@ extern "C" const char *pfac_status_str(int s) {
         case PFAC_ECUDA: return "CUDA error";
         case PFAC_ETIMEOUT: return "device wait timed out";
         case PFAC_EDEVICE: return "device consistency check failed";
+        case PFAC_EIO: return "table file I/O failed";
+        case PFAC_EFORMAT: return "not a table file of this format";
         default: return "unknown status";
     }
 }
@@ -952,4 +955,4 @@ extern "C" int pfac_last_error(char *buf, size_t n) {
     return g_last_status;
 }
 
-extern "C" int pfac_version(void) { return 100; }
+extern "C" int pfac_version(void) { return 200; }

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/pfac.h"
 #include "table.h"
 
@@ -12,6 +14,9 @@ struct pfac_table {
     pfac::DevTable dev;
     void *d_blob = nullptr;
     uint64_t blob_bytes = 0;
+    // host-only tables keep their blob here (the DevTable's pointers point
+    // into it; no kernel reads them: every match call refuses such a table)
+    std::vector<uint8_t> h_blob;
     pfac_table_info_t info{};
     uint32_t kmin = 0, kmax = 0;  // prefix nodes exist for depths kmin..kmax
     int device = 0;
