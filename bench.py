@@ -697,7 +697,11 @@ def serving_levels(args, loads, seconds, n_min, n_max, verbose=True):
     each level runs `seconds` of arrivals (at least n_min, at most n_max
     batches).  Per level: p50/p99 latency (completion minus scheduled
     arrival), its parts (how late the load generator submitted, the wait for
-    admission, the time on the GPU) and the sustained throughput."""
+    admission, the host time of the admission's calls, the time on the GPU),
+    the results whose keys went through a staging copy instead of the result
+    arena, and the sustained throughput.  The load generator consumes each
+    result as it is polled (a view of the server's memory) and releases it at
+    once, as a client that keeps up does."""
     import gc
     import threading
     import torch
@@ -745,22 +749,28 @@ def serving_levels(args, loads, seconds, n_min, n_max, verbose=True):
 
             th = threading.Thread(target=submitter)
             th.start()
+            # a client that consumes each result as it comes: keep the
+            # stamps, release the request (its keys' block) at once
             done = {}
             while len(done) < n:
-                r = srv.poll()
+                r = srv.poll(copy=False)
                 if r is None:
                     time.sleep(0.0002)
                     continue
+                r["n_keys"] = r.pop("keys").size
+                srv.release(r["id"])
                 done[r["id"]] = r
             th.join()
-            lat, wait_adm, service = [], [], []
+            lat, wait_adm, service, issue = [], [], [], []
+            staged = 0  # results whose keys went through a staging copy
             for rid, at in zip(ids, sched):
                 r = done[rid]
                 assert r["status"] == 0
                 lat.append(r["t_done"] - at)
                 wait_adm.append(r["t_admit"] - r["t_submit"])
                 service.append(r["t_done"] - r["t_admit"])
-                srv.release(rid)
+                issue.append(r["t_issued"] - r["t_admit"])
+                staged += 0 if r["in_arena"] or not r["n_keys"] else 1
             gc.enable()
             t_end = max(done[i]["t_done"] for i in ids)
             ms = lambda xs, q: round(1e3 * float(np.percentile(xs, q)), 3)
@@ -768,7 +778,8 @@ def serving_levels(args, loads, seconds, n_min, n_max, verbose=True):
                     "sustained_gbps": round(8.0 * sum(sizes) / (t_end - start) / 1e9, 3),
                     "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
                     "p99_submit_late_ms": ms(late, 99), "p99_admission_wait_ms": ms(wait_adm, 99),
-                    "p99_on_gpu_ms": ms(service, 99),
+                    "p99_on_gpu_ms": ms(service, 99), "p99_issue_ms": ms(issue, 99),
+                    "max_issue_ms": round(1e3 * max(issue), 3), "staged_results": staged,
                     "requests": n, "mean_request_bytes": int(mean_bytes),
                     "slots": args.serve_slots}
             out.append(line)

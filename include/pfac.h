@@ -474,8 +474,14 @@ int pfac_autotune(pfac_table *t, const uint8_t *d_sample, uint64_t n_bytes,
  * admitted requests run concurrently on their streams.  pfac_server_wait
  * blocks until a request is done (timeout_s <= 0: no limit), pfac_server_poll
  * returns the next completed request (1 when none), and the result's keys
- * stay valid until pfac_server_release.  Times are seconds on a monotonic
- * clock (submit, admission, completion).
+ * stay valid until pfac_server_release.  Keys land straight from the device
+ * in a pinned host arena of host_bytes and are handed out in place; release
+ * returns the block, so results released promptly keep the arena free
+ * (when it is full, keys go through a staging copy into memory of their
+ * own).  Times are seconds on a monotonic
+ * clock: submit, admission (a slot and memory taken), issued (the host calls
+ * of the admission returned), counted (the dispatcher saw the first phase
+ * complete), completion.
  */
 typedef struct pfac_server pfac_server;
 typedef struct {
@@ -483,15 +489,18 @@ typedef struct {
     uint32_t reserved0;
     uint64_t device_bytes;      /* pool for in-flight requests; 0 = 1 GiB */
     uint64_t max_request_bytes; /* largest input accepted; 0 = device_bytes / 4 */
-    uint64_t reserved[4];
+    uint64_t host_bytes;        /* pinned result arena; 0 = 256 MiB */
+    uint64_t reserved[3];
 } pfac_server_opts;
 typedef struct {
     uint64_t id;
     int32_t status;             /* PFAC_OK or the request's error */
-    int32_t reserved0;
+    int32_t in_arena;           /* 1: keys lie in the result arena */
     uint64_t n_keys;
     const uint64_t *keys;       /* host memory owned by the server */
     double t_submit, t_admit, t_done;
+    double t_issued;            /* admission's copies and match enqueued */
+    double t_counted;           /* the dispatcher saw the count (phase 1 done) */
 } pfac_result;
 
 int pfac_server_create(const pfac_table *t, const pfac_server_opts *opts, pfac_server **out);

@@ -97,14 +97,15 @@ class PlanInfo(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64), ("max_request_bytes", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint64 * 4)]
+                ("host_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 3)]
 
 
 class ResultC(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("n_keys", ctypes.c_uint64),
+                ("in_arena", ctypes.c_int32), ("n_keys", ctypes.c_uint64),
                 ("keys", ctypes.POINTER(ctypes.c_uint64)), ("t_submit", ctypes.c_double),
-                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("t_issued", ctypes.c_double), ("t_counted", ctypes.c_double)]
 
 
 def _load():
@@ -471,9 +472,10 @@ class Server:
     passed to submit() are kept alive here until release()."""
 
     def __init__(self, table: Table, n_slots: int = 4, device_bytes: int = 1 << 30,
-                 max_request_bytes: int = 0):
+                 max_request_bytes: int = 0, host_bytes: int = 0):
         o = ServerOpts()
         o.n_slots, o.device_bytes, o.max_request_bytes = n_slots, device_bytes, max_request_bytes
+        o.host_bytes = host_bytes
         h = ctypes.c_void_p()
         _check(LIB.pfac_server_create(table.handle, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -500,25 +502,33 @@ class Server:
         return rid.value
 
     @staticmethod
-    def _result(r: ResultC) -> dict:
+    def _result(r: ResultC, copy: bool = True) -> dict:
+        """The result as a dict; keys copied out, or with copy=False a view of
+        the server's memory that is valid until release()."""
         import numpy as np
-        keys = np.ctypeslib.as_array(r.keys, shape=(r.n_keys,)).copy() if r.n_keys else \
-            np.zeros(0, np.uint64)
-        return {"id": r.id, "status": r.status, "keys": keys, "t_submit": r.t_submit,
-                "t_admit": r.t_admit, "t_done": r.t_done}
+        if r.n_keys:
+            keys = np.ctypeslib.as_array(r.keys, shape=(r.n_keys,))
+            if copy:
+                keys = keys.copy()
+        else:
+            keys = np.zeros(0, np.uint64)
+        return {"id": r.id, "status": r.status, "keys": keys, "in_arena": bool(r.in_arena),
+                "t_submit": r.t_submit,
+                "t_admit": r.t_admit, "t_done": r.t_done, "t_issued": r.t_issued,
+                "t_counted": r.t_counted}
 
-    def wait(self, rid: int, timeout: float = 0.0) -> dict:
+    def wait(self, rid: int, timeout: float = 0.0, copy: bool = True) -> dict:
         r = ResultC()
         _check(LIB.pfac_server_wait(self._h, rid, timeout, ctypes.byref(r)))
-        return self._result(r)
+        return self._result(r, copy)
 
-    def poll(self):
+    def poll(self, copy: bool = True):
         r = ResultC()
         rc = LIB.pfac_server_poll(self._h, ctypes.byref(r))
         if rc == 1:
             return None
         _check(rc)
-        return self._result(r)
+        return self._result(r, copy)
 
     def release(self, rid: int):
         _check(LIB.pfac_server_release(self._h, rid))

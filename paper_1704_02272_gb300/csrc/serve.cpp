@@ -11,7 +11,13 @@
 // H2D of its input, pfac_match_async, D2H of its count; then D2H of its keys
 // (in the rare case the first estimate was too small, re-matched into a
 // buffer of exactly its count first, asynchronously on its slot with its own
-// status check).  Latency is stamped at submit, admission and completion.
+// status check).  The keys land in a block of a pinned result arena, taken
+// when the count is known and handed out in place until the request is
+// released, so the dispatcher neither allocates nor copies host memory per
+// request (fresh host pages cost milliseconds while the process grows); when
+// the arena is full they land in the slot's staging buffer and are copied
+// into the request's own vector.  Latency is stamped at submit, admission,
+// issue, count and completion.
 //
 // Threads: submitters, pollers and waiters share one lock over the request
 // queue and the completed list; the dispatcher owns the slots and the pool
@@ -89,9 +95,11 @@ struct Request {
     uint64_t n;
     const uint64_t *h_seg;
     uint32_t nseg;
-    double t_submit = 0, t_admit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0, t_issued = 0, t_counted = 0;
     int status = PFAC_OK;
-    std::vector<uint64_t> keys;
+    std::vector<uint64_t> keys;  // keys outside the arena
+    bool in_arena = false;       // keys at arena_off of the result arena
+    uint64_t arena_off = 0, n_arena = 0;
     bool done = false;
 };
 
@@ -119,6 +127,8 @@ struct pfac_server {
     int device = 0;
     uint8_t *d_pool = nullptr;
     Pool pool;
+    uint8_t *h_arena = nullptr;  // pinned result arena
+    Pool hpool;                  // its blocks (under mu: release runs on callers' threads)
     std::vector<Slot> slots;
     uint64_t max_req = 0;
     std::mutex mu;
@@ -186,6 +196,7 @@ bool admit(pfac_server *s, Slot &sl, Request *r) {
         sl.phase = 3;  // complete with an error once the stream drains
         cudaEventRecord(sl.ev, sl.stream);
     }
+    r->t_issued = now_s();
     return true;
 }
 
@@ -227,12 +238,26 @@ Block block_of(pfac_server *s, const Slot &sl, const Request *r) {
     return b;
 }
 
-// Phase 1 done with more keys than the output buffer or the pinned staging
-// holds: grow the staging, match again into a buffer of exactly cnt keys
-// (from the pool when it has room), copy count, status and keys back; the
-// slot moves to phase 4.  Returns false on failure (status set).
-bool rematch(pfac_server *s, Slot &sl, Request *r, uint64_t cnt) {
-    if (cnt > sl.h_cap) {
+// Host destination of a request's cnt keys: a block of the result arena when
+// it has room (recorded in the request), else nullptr (the slot's staging).
+uint64_t *arena_block(pfac_server *s, Request *r, uint64_t cnt) {
+    if (!cnt || !s->h_arena) return nullptr;
+    std::lock_guard<std::mutex> lk(s->mu);
+    uint64_t off = 0;
+    if (!s->hpool.alloc(8 * cnt, &off)) return nullptr;
+    r->in_arena = true;
+    r->arena_off = off;
+    r->n_arena = cnt;
+    return (uint64_t *)(s->h_arena + off);
+}
+
+// Phase 1 done with more keys than the output buffer holds: match again into
+// a buffer of exactly cnt keys (from the pool when it has room), copy count,
+// status and keys back to dst (the arena block) or to the slot's staging,
+// grown first when too small; the slot moves to phase 4.  Returns false on
+// failure (status set).
+bool rematch(pfac_server *s, Slot &sl, Request *r, uint64_t cnt, uint64_t *dst) {
+    if (!dst && cnt > sl.h_cap) {
         cudaStreamSynchronize(sl.stream);
         cudaFreeHost(sl.h_keys);
         sl.h_keys = nullptr;
@@ -261,7 +286,8 @@ bool rematch(pfac_server *s, Slot &sl, Request *r, uint64_t cnt) {
     if (rc == PFAC_OK)
         e = cudaMemcpyAsync(sl.h_small, b.small, 16, cudaMemcpyDeviceToHost, sl.stream);
     if (rc == PFAC_OK && e == cudaSuccess)
-        e = cudaMemcpyAsync(sl.h_keys, sl.d_big, 8 * cnt, cudaMemcpyDeviceToHost, sl.stream);
+        e = cudaMemcpyAsync(dst ? dst : sl.h_keys, sl.d_big, 8 * cnt, cudaMemcpyDeviceToHost,
+                            sl.stream);
     if (rc == PFAC_OK && e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
     if (rc != PFAC_OK || e != cudaSuccess) {
         cudaGetLastError();
@@ -312,6 +338,7 @@ void dispatcher(pfac_server *s) {
                 continue;
             }
             if (sl.phase == 1) {
+                r->t_counted = now_s();
                 const uint64_t cnt = sl.h_small[0];
                 const int32_t st = (int32_t)(uint32_t)sl.h_small[1];
                 if (st != PFAC_OK) {
@@ -320,14 +347,15 @@ void dispatcher(pfac_server *s) {
                     continue;
                 }
                 sl.count = cnt;
-                if (cnt > sl.cap || cnt > sl.h_cap) {
-                    if (!rematch(s, sl, r, cnt)) finish(s, sl);
+                uint64_t *dst = arena_block(s, r, cnt);
+                if (cnt > sl.cap || (!dst && cnt > sl.h_cap)) {
+                    if (!rematch(s, sl, r, cnt, dst)) finish(s, sl);
                     continue;
                 }
                 cudaError_t e = cudaSuccess;
                 if (cnt)
-                    e = cudaMemcpyAsync(sl.h_keys, sl.d_out, 8 * cnt, cudaMemcpyDeviceToHost,
-                                        sl.stream);
+                    e = cudaMemcpyAsync(dst ? dst : sl.h_keys, sl.d_out, 8 * cnt,
+                                        cudaMemcpyDeviceToHost, sl.stream);
                 if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
                 if (e != cudaSuccess) {
                     r->status = PFAC_ECUDA;
@@ -339,7 +367,7 @@ void dispatcher(pfac_server *s) {
                 const int32_t st = (int32_t)(uint32_t)sl.h_small[1];
                 if (sl.phase == 4 && (st != PFAC_OK || sl.h_small[0] != sl.count))
                     r->status = st != PFAC_OK ? st : PFAC_EDEVICE;
-                else
+                else if (!r->in_arena)
                     r->keys.assign(sl.h_keys, sl.h_keys + sl.count);
                 finish(s, sl);
             }
@@ -383,6 +411,16 @@ extern "C" int pfac_server_create(const pfac_table *t, const pfac_server_opts *o
                          (unsigned long long)pool, cudaGetErrorString(e));
     }
     s->pool.init(s->d_pool, pool);
+    const uint64_t hbytes = opt.host_bytes ? opt.host_bytes : (256ull << 20);
+    e = cudaHostAlloc((void **)&s->h_arena, hbytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->d_pool);
+        delete s;
+        return set_error(PFAC_ENOMEM, "pfac_server_create: result arena of %llu bytes: %s",
+                         (unsigned long long)hbytes, cudaGetErrorString(e));
+    }
+    s->hpool.init(s->h_arena, hbytes);
     s->slots.resize(n_slots);
     for (Slot &sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
@@ -435,14 +473,22 @@ extern "C" int pfac_server_submit(pfac_server *s, const uint8_t *h_input, uint64
     return PFAC_OK;
 }
 
-static void fill(const Request *r, pfac_result *res) {
+static void fill(const pfac_server *s, const Request *r, pfac_result *res) {
     res->id = r->id;
     res->status = r->status;
-    res->n_keys = r->keys.size();
-    res->keys = r->keys.data();
+    res->in_arena = r->in_arena ? 1 : 0;
+    if (r->in_arena) {
+        res->n_keys = r->status == PFAC_OK ? r->n_arena : 0;
+        res->keys = (const uint64_t *)(s->h_arena + r->arena_off);
+    } else {
+        res->n_keys = r->keys.size();
+        res->keys = r->keys.data();
+    }
     res->t_submit = r->t_submit;
     res->t_admit = r->t_admit;
     res->t_done = r->t_done;
+    res->t_issued = r->t_issued;
+    res->t_counted = r->t_counted;
 }
 
 extern "C" int pfac_server_wait(pfac_server *s, uint64_t id, double timeout_s,
@@ -459,7 +505,7 @@ extern "C" int pfac_server_wait(pfac_server *s, uint64_t id, double timeout_s,
         if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout && !r->done)
             return set_error(PFAC_ETIMEOUT, "pfac_server_wait: request %llu not done",
                              (unsigned long long)id);
-    fill(r, res);
+    fill(s, r, res);
     return PFAC_OK;
 }
 
@@ -471,7 +517,7 @@ extern "C" int pfac_server_poll(pfac_server *s, pfac_result *res) {
         s->completed.pop_front();
         auto it = s->reqs.find(id);
         if (it == s->reqs.end()) continue;  // already released
-        fill(it->second, res);
+        fill(s, it->second, res);
         return PFAC_OK;
     }
     return 1;
@@ -483,7 +529,9 @@ extern "C" int pfac_server_release(pfac_server *s, uint64_t id) {
     auto it = s->reqs.find(id);
     if (it == s->reqs.end() || !it->second->done)
         return set_error(PFAC_EINVAL, "pfac_server_release: unknown or unfinished request");
-    delete it->second;
+    Request *r = it->second;
+    if (r->in_arena) s->hpool.release(r->arena_off, 8 * r->n_arena);
+    delete r;
     s->reqs.erase(it);
     return PFAC_OK;
 }
@@ -504,6 +552,7 @@ extern "C" void pfac_server_destroy(pfac_server *s) {
         if (sl.h_keys) cudaFreeHost(sl.h_keys);
     }
     if (s->d_pool) cudaFree(s->d_pool);
+    if (s->h_arena) cudaFreeHost(s->h_arena);
     for (auto &kv : s->reqs) delete kv.second;  // pending requests are in reqs too
     delete s;
 }

@@ -36,13 +36,19 @@ def alone(table, text, seg):
     return keys_np(k)
 
 
-def test_results_same_alone_and_in_the_mix(serving_setup):
+# result arenas: the default (every result's keys land in it) and one of
+# 64 KiB (most results go through the slots' staging copy instead)
+ARENAS = [0, 1 << 16]
+
+
+@pytest.mark.parametrize("host_bytes", ARENAS, ids=["arena", "small-arena"])
+def test_results_same_alone_and_in_the_mix(serving_setup, host_bytes):
     pats, reqs, table = serving_setup
     ref = [alone(table, t, s) for t, s in reqs]
     # a pool that holds only a few requests at a time forces admission waits
     biggest = max(t.size for t, _ in reqs)
     with pfac.Server(table, n_slots=4, device_bytes=6 * biggest + (64 << 20),
-                     max_request_bytes=biggest) as srv:
+                     max_request_bytes=biggest, host_bytes=host_bytes) as srv:
         ids = [srv.submit(t, s) for t, s in reqs]
         got = [srv.wait(i, timeout=120) for i in ids]
         for i in ids:
@@ -50,7 +56,7 @@ def test_results_same_alone_and_in_the_mix(serving_setup):
     for k, (g, r) in enumerate(zip(got, ref)):
         assert g["status"] == 0
         assert_same(g["keys"], r, f"request {k}")
-        assert g["t_submit"] <= g["t_admit"] <= g["t_done"]
+        assert g["t_submit"] <= g["t_admit"] <= g["t_issued"] <= g["t_counted"] <= g["t_done"]
     # later requests waited for earlier ones to free memory or slots
     assert max(g["t_admit"] - g["t_submit"] for g in got) > 0
     for k in (0, 7, 35):
@@ -102,7 +108,8 @@ def test_request_larger_than_pool_rejected(serving_setup):
         assert ei.value.status == -4
 
 
-def test_requests_with_more_keys_than_their_first_buffer():
+@pytest.mark.parametrize("host_bytes", ARENAS, ids=["arena", "small-arena"])
+def test_requests_with_more_keys_than_their_first_buffer(host_bytes):
     # requests whose matches outnumber the server's first key estimate (one
     # key per 8 input bytes) take the re-match path: a buffer of exactly
     # their count, matched again on their slot with its status checked; they
@@ -123,7 +130,7 @@ def test_requests_with_more_keys_than_their_first_buffer():
         reqs.append((text, seg))
     with pfac.Table(pats, 256) as table:
         with pfac.Server(table, n_slots=3, device_bytes=64 << 20,
-                         max_request_bytes=1 << 20) as srv:
+                         max_request_bytes=1 << 20, host_bytes=host_bytes) as srv:
             ids = [srv.submit(t, s) for t, s in reqs]
             got = [srv.wait(i, timeout=120) for i in ids]
             for i in ids:
