@@ -52,11 +52,19 @@ MEASURED_TRAFFIC = {
     "dna": [(310759680, "d100e0d9e6ba3865",
              {"variant": 1, "prefix_depth": 10, "bitmap_copies": 1, "child_masks": 1,
               "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 16, "scan_kernel": 1,
-              "records_per_slice": 512, "resolver": 2})],
+              "records_per_slice": 512, "resolver": 2}),
+            (311110912, "d100e0d9e6ba3865",
+             {"variant": 1, "prefix_depth": 10, "bitmap_copies": 1, "child_masks": 1,
+              "gram_filter": 1, "prefix_bytes": 1, "warps_per_cta": 16, "scan_kernel": 1,
+              "records_per_slice": 32, "resolver": 2})],
     "sweep-256-1000": [(550563584, "d100e0d9e6ba3865",
                         {"variant": 1, "prefix_depth": 2, "bitmap_copies": 1, "child_masks": 1,
                          "gram_filter": 2, "prefix_bytes": 1, "warps_per_cta": 16,
-                         "scan_kernel": 2, "records_per_slice": 32, "resolver": 2})],
+                         "scan_kernel": 2, "records_per_slice": 32, "resolver": 2}),
+                       (553913344, "d100e0d9e6ba3865",
+                        {"variant": 2, "prefix_depth": 2, "bitmap_copies": 1, "child_masks": 2,
+                         "gram_filter": 2, "prefix_bytes": 1, "warps_per_cta": 16,
+                         "scan_kernel": 2, "records_per_slice": 32, "resolver": 1})],
 }
 KERNEL_SOURCES = ["kernels_q.cuh", "kernels_r.cuh", "kernels.cuh", "table.h"]
 TUNE_SAMPLE = 128 << 20
@@ -254,7 +262,7 @@ def user_options(args):
                      ("bitmap_copies", args.copies), ("child_masks", args.masks),
                      ("gram_filter", args.gram), ("prefix_bytes", args.bytes),
                      ("warps_per_cta", args.warps), ("scan_kernel", args.kernel),
-                     ("records_per_slice", args.records)):
+                     ("records_per_slice", args.records), ("resolver", args.resolver)):
         if val:
             user_opt[key] = val
     return user_opt
@@ -827,6 +835,8 @@ def main():
     ap.add_argument("--bytes", type=int, default=0, help="prefix bytes first stage: 1 off, 2 on")
     ap.add_argument("--warps", type=int, default=0, help="scan-kernel warps per CTA: 16 or 24")
     ap.add_argument("--records", type=int, default=0, help="records per slice: 32 or 512")
+    ap.add_argument("--resolver", type=int, default=0,
+                    help="queues of survivors: 1 resolved by the scan, 2 by the resolver kernel")
     ap.add_argument("--kernel", type=int, default=0,
                     help="scan kernel: 1 queued (input staged in shared memory), 2 register-staged "
                          "(alphabets of 129-256 symbols)")
