@@ -638,8 +638,9 @@ def run_ours(args):
     ctx["dense"].close()
     del ctx, text, seg, keys, host_in, host_out
 
-    # the cell the 50%-of-HBM target is judged on: alphabet 256, 1,000
-    # patterns, 512 MiB (timed the same way, on rank 0's GPU only)
+    # the alphabet-256 cell (1,000 patterns, 512 MiB), where a scan over few
+    # survivors should come closest to the HBM bound (timed the same way, on
+    # rank 0's GPU only)
     extra = {}
     if not args.no_sweep_cell and args.workload != "sweep-256-1000" and world == 1:
         wc = load_workload("sweep-256-1000", 0)
