@@ -147,3 +147,32 @@ def test_bad_arguments(tmp_path):
     assert h.pfac_table_load(None, pfac.binding.BUILD_HOST_ONLY, None, ctypes.byref(out)) == EINVAL
     assert h.pfac_table_save(None, os.fsencode(p)) == EINVAL
 
+
+
+# every alphabet size class the builder distinguishes (record formats, packed
+# shifts, bits per symbol), in both layouts, over sets of patterns of 1 to 12
+# symbols (many of them prefixes of others)
+SIGMAS = [1, 2, 3, 4, 5, 8, 9, 16, 17, 32, 33, 64, 128, 129, 200, 256]
+
+
+@pytest.mark.parametrize("sigma", SIGMAS)
+def test_round_trip_every_alphabet_class(tmp_path, sigma):
+    w = workloads.tiny_case(900 + sigma, sigma, 150, 1, 12, 64)
+    for kw in ({}, {"layout": pfac.LAYOUT_DENSE}):
+        with pfac.Table(w.patterns, sigma, host_only=True, **kw) as t:
+            t.save(tmp_path / "a.pfac")
+            info = t.info()
+        with pfac.Table.load(tmp_path / "a.pfac", host_only=True) as u:
+            assert u.info() == info
+            u.save(tmp_path / "b.pfac")
+        assert (tmp_path / "a.pfac").read_bytes() == (tmp_path / "b.pfac").read_bytes()
+
+
+def test_misaligned_section_is_refused(tmp_path):
+    with host_table(20, 300) as t:
+        t.save(tmp_path / "good.pfac")
+    src = (tmp_path / "good.pfac").read_bytes()
+    # the records' offset (the first pointer of the description) moved off
+    # its 4-byte alignment, checksum made valid again
+    assert "section offset" in refused(damaged(tmp_path, src, HEADER + 48, struct.pack("<Q", 2), True),
+                                       EFORMAT)
